@@ -1,0 +1,165 @@
+"""IMEX multi-rate SDC, Algorithms 1 and 2 taken literally (oracle; test infrastructure only).
+
+Problem interface (any object with):
+    mass           (N,) diagonal of M (lumped)
+    fI(T)          the slow, linear, implicit term f^I(T)
+    g(t)           the slow source g(t)
+    fE(T, t)       the fast explicit term f^E(T, t)
+    solve(dtau, rhs, x0) -> (x, iters)   solves  mass * x - dtau * fI(x) = rhs
+
+One macro step [t_n, t_n + dt] with standard nodes tau_m = t_n + dt c_m and
+embedded nodes tau_{m,p} (see oracle.weights):
+
+Algorithm 1 (predictor), for m = 1..M:
+    solve  M T*_m = M T_{m-1} + dtau_m (f^I(T*_m) + g(tau_m))
+    f*_m = f^I(T*_m) + g(tau_m)
+    T_{m,0} = T_{m-1};  for p = 1..P:
+        M T_{m,p} = M T_{m,p-1} + dt_{m,p} (f*_m + f^E(T_{m,p-1}, tau_{m,p-1}))
+    T_m = T_{m,P}
+
+Algorithm 2 (sweep k -> k+1): build I_{m-1}^m (Eq. standard_quad) and
+I_{m,p-1}^p (Eq. embedded_quad) from iterate k; T_0 = T(t_n); for m = 1..M:
+    solve  M T*_m = M T^{k+1}_{m-1} + dtau_m (f^I(T*_m) - f^I(T^k_m)) + I_{m-1}^m
+    f*_m = f^I(T*_m) - f^I(T^k_m)
+    T_{m,0} = T^{k+1}_{m-1};  for p = 1..P:
+        M T_{m,p} = M T_{m,p-1} + dt_{m,p} f*_m
+                    + dt_{m,p} (f^E(T^{k+1}_{m,p-1}, tau_{m,p-1}) - f^E(T^k_{m,p-1}, tau_{m,p-1}))
+                    + I_{m,p-1}^p
+    T^{k+1}_m = T^{k+1}_{m,P}
+
+Full vectors are kept at every embedded node; nothing is specialised to the
+location of the contact, so the fast library path (which runs the P substeps
+only on contact DOFs) is checked against this plain form.
+
+Residual (Eq. residual, with the sum index read as j, i.e. sum_{j<=m} I_{j-1}^j):
+    r^k = max_m || M T^k_m - M T(t_n) - sum_{j=1}^m I_{j-1}^j ||_inf
+computed from iterate k (and its own quadrature).
+
+Readings: g is evaluated at tau_m in the predictor (Algorithm 1 includes it
+in f*); the explicit Euler step uses f^E at the left embedded node
+tau_{m,p-1}; quadratures use f^E at tau_{m,q}, q = 1..P. A zero-length
+interval (Lobatto, m = 1) is run as written: its solve returns T_{m-1} and
+its substeps have zero length.
+
+Parity: pinned by tests/test_oracle_stepper.py (order min(M, w, k+1) on the
+scalar IMEX equation, convergence of the sweeps to the directly solved
+collocation system, equality with implicit Euler / implicit SDC when f^E = 0,
+conservation of total heat) and tests/test_oracle_bruteforce.py (matrix
+exponential of a <= 200-DOF machine).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+class StepResult:
+    def __init__(self):
+        self.residuals = []
+        self.cg_iters = []
+        self.T_std = None
+        self.T_emb = None
+
+
+def _quadratures(prob, T_std, T_emb, tau, tau_emb, W, dt):
+    """F^I_j, f^E at embedded nodes and the integrals I_{m-1}^m, I_{m,p-1}^p of one iterate."""
+    M, P = W["M"], W["P"]
+    FI = [prob.fI(T_std[j + 1]) + prob.g(tau[j + 1]) for j in range(M)]
+    FE = [[prob.fE(T_emb[m][q], tau_emb[m][q]) for q in range(P + 1)] for m in range(M)]
+    I_std = []
+    I_emb = []
+    for m in range(M):
+        acc = np.zeros_like(T_std[0])
+        for j in range(M):
+            acc = acc + dt * W["S"][m, j] * FI[j]
+        for q in range(P):
+            acc = acc + dt * W["Shat"][m, q] * FE[m][q + 1]
+        I_std.append(acc)
+        row = []
+        for p in range(P):
+            acc = np.zeros_like(T_std[0])
+            for j in range(M):
+                acc = acc + dt * W["Stil"][m, p, j] * FI[j]
+            for q in range(P):
+                acc = acc + dt * W["Semb"][m, p, q] * FE[m][q + 1]
+            row.append(acc)
+        I_emb.append(row)
+    return FI, FE, I_std, I_emb
+
+
+def _residual(prob, T_n, T_std, I_std):
+    M = len(I_std)
+    cum = np.zeros_like(T_n)
+    r = 0.0
+    for m in range(M):
+        cum = cum + I_std[m]
+        res = prob.mass * T_std[m + 1] - prob.mass * T_n - cum
+        r = max(r, float(np.max(np.abs(res))))
+    return r
+
+
+def mrsdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False, keep_nodes=False):
+    """One macro step; returns (T(t_n + dt), StepResult)."""
+    M, P = W["M"], W["P"]
+    c, emb = W["c"], W["emb"]
+    tau = [t_n + dt * c[m] for m in range(M + 1)]          # tau[0] = t_n
+    tau_emb = [[t_n + dt * emb[m][p] for p in range(P + 1)] for m in range(M)]
+    mass = prob.mass
+    res = StepResult()
+
+    # ---------------- Algorithm 1: predictor ----------------
+    T_std = [T_n.copy()] + [None] * M
+    T_emb = [[None] * (P + 1) for _ in range(M)]
+    for m in range(M):
+        dtau = tau[m + 1] - tau[m]
+        rhs = mass * T_std[m] + dtau * prob.g(tau[m + 1])
+        Tstar, it = prob.solve(dtau, rhs, T_std[m])
+        res.cg_iters.append(it)
+        fstar = prob.fI(Tstar) + prob.g(tau[m + 1])
+        T_emb[m][0] = T_std[m].copy()
+        for p in range(1, P + 1):
+            dtp = tau_emb[m][p] - tau_emb[m][p - 1]
+            incr = dtp * (fstar + prob.fE(T_emb[m][p - 1], tau_emb[m][p - 1]))
+            T_emb[m][p] = T_emb[m][p - 1] + incr / mass
+        T_std[m + 1] = T_emb[m][P]
+
+    # ---------------- Algorithm 2: sweeps ----------------
+    for k in range(sweeps):
+        FI, FE, I_std, I_emb = _quadratures(prob, T_std, T_emb, tau, tau_emb, W, dt)
+        if want_residuals:
+            res.residuals.append(_residual(prob, T_n, T_std, I_std))
+        new_std = [T_n.copy()] + [None] * M
+        new_emb = [[None] * (P + 1) for _ in range(M)]
+        for m in range(M):
+            dtau = tau[m + 1] - tau[m]
+            fI_old = FI[m] - prob.g(tau[m + 1])            # f^I(T^k_m)
+            rhs = mass * new_std[m] - dtau * fI_old + I_std[m]
+            Tstar, it = prob.solve(dtau, rhs, T_std[m + 1])
+            res.cg_iters.append(it)
+            fstar = prob.fI(Tstar) - fI_old
+            new_emb[m][0] = new_std[m].copy()
+            for p in range(1, P + 1):
+                dtp = tau_emb[m][p] - tau_emb[m][p - 1]
+                fe_new = prob.fE(new_emb[m][p - 1], tau_emb[m][p - 1])
+                fe_old = FE[m][p - 1]                       # f^E(T^k_{m,p-1}, tau_{m,p-1})
+                incr = dtp * fstar + dtp * (fe_new - fe_old) + I_emb[m][p - 1]
+                new_emb[m][p] = new_emb[m][p - 1] + incr / mass
+            new_std[m + 1] = new_emb[m][P]
+        T_std, T_emb = new_std, new_emb
+
+    if want_residuals:
+        _, _, I_std, _ = _quadratures(prob, T_std, T_emb, tau, tau_emb, W, dt)
+        res.residuals.append(_residual(prob, T_n, T_std, I_std))
+    if keep_nodes:
+        res.T_std, res.T_emb = T_std, T_emb
+    return T_std[M].copy(), res
+
+
+def run(prob, T0, t0, dt, W, sweeps, n_steps, callback=None):
+    """n_steps macro steps from (T0, t0); t_n = t0 + n dt (no accumulated sum)."""
+    T = np.array(T0, dtype=np.float64, copy=True)
+    for n in range(n_steps):
+        T, r = mrsdc_step(prob, T, t0 + n * dt, dt, W, sweeps)
+        if callback is not None:
+            callback(n, T, r)
+    return T
