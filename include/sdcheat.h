@@ -1,0 +1,221 @@
+/*
+ * sdcheat.h -- C ABI of the GB300 IMEX multi-rate SDC heat solver.
+ *
+ * The library advances the fully coupled transient FEM heat equation of a
+ * fixed stand and a stock sliding on it (Sec. 2 of Naumann, Ruprecht,
+ * Wensch, arXiv:1707.03581) with the implicit-explicit multi-rate spectral
+ * deferred correction method of Sec. 3 (Algorithm 1 = predictor,
+ * Algorithm 2 = correction sweep):
+ *
+ *   M dT/dt = f^I(T) + f^E(T, t) + g,          (Eq. ivp)
+ *   f^I(T)  = (A + B_env) T = -K T              slow, implicit (diffusion + Robin)
+ *   g       = b_env                             slow source (environment)
+ *   f^E     = M_B(t) T + C_B(t) T + b(t)        fast, explicit (contact + friction)
+ *
+ * All compute runs in CUDA kernels for sm_103a; this header carries no
+ * C++ or PyTorch types. Conventions shared by every call:
+ *
+ *  - Every call returns an sdc_status. On error the context stays valid and
+ *    sdc_last_error() describes the failure. Nothing is partially applied
+ *    unless stated.
+ *  - Host arrays passed in are read during the call and copied; the caller
+ *    keeps ownership. Device arrays the library creates are owned by the
+ *    context and freed by sdc_destroy().
+ *  - A context is not thread safe; use one context per host thread/stream.
+ *  - DOF numbering: stand nodes 0..n_stand-1, then stock nodes.
+ *  - Units: SI (m, s, W, J, K or degC consistently).
+ */
+#ifndef SDCHEAT_H
+#define SDCHEAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdc_ctx sdc_ctx;
+
+typedef enum {
+    SDC_OK = 0,
+    SDC_ERR_ARG = -1,            /* invalid argument (sizes, ids, geometry)            */
+    SDC_ERR_OOM = -2,            /* a device allocation failed                         */
+    SDC_ERR_CUDA = -3,           /* a CUDA runtime call failed                         */
+    SDC_ERR_NOT_CONVERGED = -4,  /* a CG solve hit cg_max_iter before cg_rtol          */
+    SDC_ERR_TIMEOUT = -5,        /* a bounded device wait gave up                      */
+    SDC_ERR_STATE = -6           /* call out of order (e.g. step before assemble)      */
+} sdc_status;
+
+/* Standard quadrature nodes of one macro step (Sec. 3, "Single-rate SDC").
+ * EQUI_NOLEFT: tau_m = t_n + m dt / M (the paper's choice);
+ * RADAU_RIGHT: Radau IIA points (right end included);
+ * LOBATTO: Gauss-Lobatto points (both ends; the zero-length first interval is
+ * skipped, which leaves every result unchanged). */
+typedef enum { SDC_NODES_EQUI_NOLEFT = 0, SDC_NODES_RADAU_RIGHT = 1, SDC_NODES_LOBATTO = 2 } sdc_nodes;
+
+/* Arithmetic of the implicit solves. FP64: FP64 SpMV/CG throughout.
+ * MIXED_FP32: FP64 iterative refinement around an FP32 SpMV/CG on the
+ * correction; the state, right-hand sides, residuals, f^I/f^E evaluations
+ * and quadratures stay FP64. */
+typedef enum { SDC_FP64 = 0, SDC_MIXED_FP32 = 1 } sdc_precision;
+
+#define SDC_MAX_SWEEPS 15
+
+/* Diagnostics of one macro step. */
+typedef struct {
+    double t;                               /* simulated time after the step                  */
+    int32_t sweeps;                         /* correction sweeps run (K)                      */
+    int32_t n_solves;                       /* implicit solves in the step                    */
+    int32_t cg_iters_total;                 /* CG iterations over all solves (inner for MIXED) */
+    int32_t cg_iters_max;                   /* largest iteration count of one solve           */
+    int32_t refinements_total;              /* outer refinement passes (MIXED only)           */
+    int32_t status;                         /* sdc_status of the device-side checks           */
+    double residual[SDC_MAX_SWEEPS + 1];    /* r^k, k = 0..K (Eq. residual), if enabled; else -1 */
+    double heat_stand;                      /* sum_i m_i T_i over stand DOFs [J]              */
+    double heat_stock;                      /* sum_i m_i T_i over stock DOFs [J]              */
+} sdc_step_report;
+
+/* Heat ledger (all FP64). */
+typedef struct {
+    double stored_stand;    /* sum_i m_i T_i, stand [J, relative to 0 degC]          */
+    double stored_stock;    /* same, stock                                            */
+    double friction_in;     /* int q(t) |Gamma_R| dt accumulated since set_temperature [J] */
+    double t;               /* simulated time                                          */
+} sdc_heat;
+
+/* Device allocator hook: alloc(bytes, user) returns a device pointer or NULL;
+ * free(ptr, user) releases it. Allocations happen only inside sdc_assemble,
+ * sdc_set_scheme and the first sdc_step after either. */
+typedef void* (*sdc_alloc_fn)(size_t bytes, void* user);
+typedef void (*sdc_free_fn)(void* ptr, void* user);
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). *out is set on success. */
+sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream);
+
+/* Free every device and host resource of the context (NULL is a no-op). */
+void sdc_destroy(sdc_ctx* ctx);
+
+/* Text of the last error of this context (valid until the next call). */
+const char* sdc_last_error(const sdc_ctx* ctx);
+
+/* Route device allocations through alloc/free (e.g. a framework's caching
+ * allocator). Must be called before sdc_assemble; NULL restores cudaMalloc. */
+sdc_status sdc_set_allocator(sdc_ctx* ctx, sdc_alloc_fn alloc, sdc_free_fn free_fn, void* user);
+
+/* ---------------------------------------------------------------- problem */
+
+/* Mesh and material of one body (Sec. 2, Eq. heat-diffusion; the weak form
+ * Eq. femContFix / femContMov). body: 0 = fixed stand, 1 = moving stock.
+ * xyz: n_nodes x 3 row-major coordinates [m]. hex8: n_hex x 8 node ids
+ * (0-based, per body), bottom face counter-clockwise then top face.
+ * k_per_hex: n_hex conductivities [W/(m K)] or NULL for uniform k.
+ * rho [kg/m^3], c [J/(kg K)]. SDC_ERR_ARG on bad ids or inverted elements
+ * (detected in sdc_assemble). */
+sdc_status sdc_set_body(sdc_ctx* ctx, int body, const double* xyz, int64_t n_nodes,
+                        const int64_t* hex8, int64_t n_hex, const double* k_per_hex,
+                        double k, double rho, double c);
+
+/* Robin faces of one body (Sec. 2: environment / cooling / floor exchange,
+ * B_env and b_env after Eq. femDiscr): n_faces x 4 node ids going around
+ * each bilinear face; heat transfer coefficient h [W/(m^2 K)], T_env. */
+sdc_status sdc_set_robin(sdc_ctx* ctx, int body, const int64_t* quad4, int64_t n_faces,
+                         double h, double T_env);
+
+/* Contact between the stand's rail (stand_quads, per-body ids) and the stock
+ * (stock_quads, per-body ids in the stock's reference position); Sec. 2,
+ * Gamma_R(t), M_B, C_B (Eq. defCB) and b_X(t). Faces must be axis-aligned
+ * rectangles in one common plane. The rail is insulated where it is not
+ * covered. h_c: exchange coefficient alpha [W/(m^2 K)]; q0_peak: peak
+ * friction flux [W/m^2], of which each body receives half. */
+sdc_status sdc_set_contact(sdc_ctx* ctx, const int64_t* stand_quads, int64_t n_sq,
+                           const int64_t* stock_quads, int64_t n_kq, double h_c, double q0_peak);
+
+/* Rigid stock motion (the motion law of Sec. 5): displacement
+ * d(t) = dir * (z0 + amp sin(2 pi t / period)), dir in the contact plane;
+ * friction flux q(t) = q0_peak |cos(2 pi t / period)|. period = +inf gives a
+ * resting stock with constant flux q0_peak. */
+sdc_status sdc_set_motion(sdc_ctx* ctx, const double dir[3], double z0, double amp, double period);
+
+/* Assemble K = -(A + B_env), the lumped mass m (row sums, Sec. 2) and
+ * g = b_env for both bodies, build the contact tables and upload everything.
+ * Allocates device memory. SDC_ERR_STATE if a body or the contact is missing. */
+sdc_status sdc_assemble(sdc_ctx* ctx);
+
+/* Time-stepping scheme (Sec. 3): node family, M standard nodes, P embedded
+ * substeps per interval, K correction sweeps (<= SDC_MAX_SWEEPS), embedded
+ * interpolation window (0 = min(M, P); P = the paper's literal weights),
+ * macro step dt [s], CG relative tolerance ||r||_2 <= cg_rtol ||b||_2 and
+ * iteration cap, precision of the implicit solves. */
+sdc_status sdc_set_scheme(sdc_ctx* ctx, sdc_nodes nodes, int M, int P, int sweeps, int window,
+                          double dt, double cg_rtol, int cg_max_iter, sdc_precision precision);
+
+/* Enable (1) or disable (0) the FP64 SDC residual r^k of Eq. residual after
+ * the predictor and every sweep (costs extra passes). */
+sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
+
+/* Initial state: T (host or device pointer of n_dof doubles) or, if T is
+ * NULL, the uniform value T_uniform; simulated time t0. */
+sdc_status sdc_set_temperature(sdc_ctx* ctx, const double* T, double T_uniform, double t0);
+
+/* ---------------------------------------------------------------- stepping */
+
+/* One macro step t_n -> t_n + dt: Algorithm 1 then K x Algorithm 2, as one
+ * CUDA graph launch on the context's stream. If rep is non-NULL the call
+ * waits for the step and fills *rep (and returns SDC_ERR_NOT_CONVERGED if a
+ * solve hit its cap); if rep is NULL the step is only enqueued and device
+ * errors surface at the next synchronising call. */
+sdc_status sdc_step(sdc_ctx* ctx, sdc_step_report* rep);
+
+/* Enqueue n_steps macro steps back to back, then wait once; *last (if not
+ * NULL) receives the report of the final step. */
+sdc_status sdc_run_horizon(sdc_ctx* ctx, int64_t n_steps, sdc_step_report* last);
+
+/* Wait for all enqueued work; returns the accumulated device status. */
+sdc_status sdc_synchronize(sdc_ctx* ctx);
+
+/* ---------------------------------------------------------------- results */
+
+/* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
+sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,
+                         int64_t* n_contact);
+
+/* Copy T(t_n) into out (host or device pointer, n == n_dof doubles). Waits. */
+sdc_status sdc_get_temperature(sdc_ctx* ctx, double* out, int64_t n);
+
+/* Borrowed device pointer to T(t_n); valid until the next step or destroy. */
+sdc_status sdc_get_temperature_device(const sdc_ctx* ctx, const double** dptr);
+
+/* Heat ledger after the last step (waits). */
+sdc_status sdc_get_heat_totals(sdc_ctx* ctx, sdc_heat* out);
+
+/* Copy the assembled system to host arrays: row_ptr (n_dof+1), col (nnz),
+ * val (nnz) of K in CSR with sorted columns, mass (n_dof), genv (n_dof).
+ * Any pointer may be NULL to skip it. */
+sdc_status sdc_get_system(const sdc_ctx* ctx, int64_t* row_ptr, int64_t* col, double* val,
+                          double* mass, double* genv);
+
+/* ---------------------------------------------------------------- components
+ * Single operations of the step on caller-owned device buffers of n_dof
+ * doubles, run on the context's stream (asynchronous unless stated). */
+
+/* y = m .* x + dtau K x (the implicit-stage operator of Algorithms 1 and 2). */
+sdc_status sdc_apply_operator(sdc_ctx* ctx, double dtau, const double* x_dev, double* y_dev);
+
+/* Solve (diag(m) + dtau K) x = b with Jacobi-PCG in the scheme's precision;
+ * x_dev holds the initial guess on entry. Waits; *iters receives the
+ * iteration count (may be NULL). */
+sdc_status sdc_solve(sdc_ctx* ctx, double dtau, const double* b_dev, double* x_dev, int32_t* iters);
+
+/* f^E(T, t) on all DOFs (zero away from the contact): Sec. 2, the contact
+ * and friction terms of Eq. femContFix / femContMov. */
+sdc_status sdc_contact_flux(sdc_ctx* ctx, const double* T_dev, double t, double* fE_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDCHEAT_H */

@@ -1,0 +1,980 @@
+// C ABI of the GB300 IMEX multi-rate SDC heat solver: context, device
+// memory, CUDA-graph construction of one macro step, and the entry points
+// declared in sdcheat.h.
+//
+// One macro step (Algorithm 1 followed by K x Algorithm 2 of Sec. 3) is one
+// CUDA graph. Each implicit solve is a conditional WHILE node whose body is
+// one CG iteration; the last reduction of the iteration clears the
+// condition once ||r|| <= rtol ||b|| or the iteration cap is hit, so a whole
+// macro step runs without host round trips.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace sdc;
+
+struct sdc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    sdc_alloc_fn alloc = nullptr;
+    sdc_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    std::vector<void*> pool_asm, pool_scheme;
+
+    // inputs
+    BodyInput body[2];
+    bool contact_set = false;
+    std::vector<int64_t> cq_fix, cq_mov;
+    double h_c = 0, q0 = 0;
+    bool motion_set = false;
+    double dir[3] = {0, 0, 1}, z0 = 0, amp = 0, period = 1;
+
+    // assembled system
+    bool assembled = false;
+    int64_t n = 0, n_fix = 0, nnz = 0;
+    HostCSR K;                      // concatenated, global column ids
+    std::vector<double> mass_h, genv_h;
+    EllDev A;
+    double *d_mass = nullptr, *d_minv = nullptr, *d_diagK = nullptr, *d_genv = nullptr;
+    ContactHost ch;
+    ContactDev C;
+    double* Tn = nullptr;
+    StepState* st = nullptr;
+    StepState* st_host = nullptr;   // pinned
+    CgState* cgs = nullptr;
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    double *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Y = nullptr, *D = nullptr;
+    CouplingOp E1{};                // one slot, for sdc_contact_flux
+    double* Ti1 = nullptr;
+    int max_blocks = 0;
+
+    // scheme
+    bool scheme_set = false;
+    Weights W;
+    int K_sweeps = 0;
+    double dt = 1.0, rtol = 1e-12;
+    int max_iter = 2000;
+    int precision = SDC_FP64;
+    int residuals = 0;
+    std::vector<int> nondeg;        // 1-based standard nodes m whose interval has positive length
+    bool temp_set = false;
+
+    // per-scheme device buffers
+    std::vector<double*> Tstd;      // M+1, Tstd[0] = Tn
+    double* FI[2][MAX_M] = {{nullptr}};
+    double* fe[2] = {nullptr, nullptr};
+    double* ihat[2] = {nullptr, nullptr};
+    double *Ta = nullptr, *Tb = nullptr, *fst = nullptr;
+    CouplingOp E{};
+    double *w_Stil = nullptr, *w_Semb = nullptr, *w_Shat = nullptr, *w_emb = nullptr, *w_slot = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ready = false;
+};
+
+namespace {
+
+void* dalloc(sdc_ctx* c, std::vector<void*>& pool, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->user);
+        if (!p) throw ApiError(SDC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw ApiError(SDC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+    }
+    pool.push_back(p);
+    return p;
+}
+
+template <class T>
+T* dalloc_n(sdc_ctx* c, std::vector<void*>& pool, size_t count) {
+    return static_cast<T*>(dalloc(c, pool, count * sizeof(T)));
+}
+
+template <class T>
+T* upload(sdc_ctx* c, std::vector<void*>& pool, const std::vector<T>& v) {
+    T* d = dalloc_n<T>(c, pool, v.size());
+    if (!v.empty()) SDC_CUDA_TRY(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return d;
+}
+
+void free_pool(sdc_ctx* c, std::vector<void*>& pool) {
+    if (pool.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (void* p : pool) {
+        if (c->alloc) c->free_fn(p, c->user);
+        else cudaFree(p);
+    }
+    pool.clear();
+}
+
+void drop_graph(sdc_ctx* c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->graph_ready = false;
+}
+
+unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Appends nodes to a graph in a single dependency chain.
+struct Chain {
+    cudaGraph_t g;
+    cudaGraphNode_t last = nullptr;
+    explicit Chain(cudaGraph_t gg) : g(gg) {}
+
+    template <typename... KArgs>
+    void kernel(void (*f)(KArgs...), unsigned grid, unsigned block, KArgs... args) {
+        void* params[] = {(void*)&args...};
+        cudaKernelNodeParams p{};
+        p.func = (void*)f;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = 0;
+        p.kernelParams = params;
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        last = nd;
+    }
+    void copy(void* dst, const void* src, size_t bytes) {
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddMemcpyNode1D(&nd, g, last ? &last : nullptr, last ? 1 : 0, dst, src, bytes,
+                                              cudaMemcpyDeviceToDevice));
+        last = nd;
+    }
+    // WHILE node driven by handle h; returns the body graph.
+    cudaGraph_t while_node(cudaGraphConditionalHandle h) {
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddNode(&nd, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np));
+        last = nd;
+        return np.conditional.phGraph_out[0];
+    }
+};
+
+CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter) {
+    CgArgs a{};
+    a.A = c->A;
+    a.mass = c->d_mass;
+    a.diagK = c->d_diagK;
+    a.dtau = dtau;
+    a.n = c->n;
+    a.X = c->X;
+    a.R = c->R;
+    a.Z = c->Z;
+    a.P = c->P;
+    a.Y = c->Y;
+    a.D = c->D;
+    a.cg = c->cgs;
+    a.partials = c->partials;
+    a.counter = c->counter;
+    a.iters_out = &c->st->cg_iters[solve_idx];
+    a.status = &c->st->status;
+    a.max_iter = max_iter;
+    a.rtol2 = rtol * rtol;
+    a.handle = 0;
+    return a;
+}
+
+// init kernel, then WHILE { spmv, update, p-update }
+void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
+    cudaGraphConditionalHandle h;
+    SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, ch.g, 1u, cudaGraphCondAssignDefault));
+    a.handle = (unsigned long long)h;
+    const unsigned nb = blocks_for(c->n, RED_BLOCK);
+    ch.kernel(k_cg_init, nb, RED_BLOCK, a, r);
+    Chain body(ch.while_node(h));
+    body.kernel(k_cg_spmv, nb, RED_BLOCK, a);
+    body.kernel(k_cg_update, nb, RED_BLOCK, a);
+    body.kernel(k_cg_pupdate, nb, RED_BLOCK, a);
+}
+
+void require(bool ok, sdc_status code, const char* msg) {
+    if (!ok) throw ApiError(code, msg);
+}
+
+void build_ell(sdc_ctx* c) {
+    const int64_t n = c->n;
+    const int64_t ns = (n + SLICE - 1) / SLICE;
+    std::vector<int64_t> sp(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t w = 0;
+        for (int64_t r = s * SLICE; r < std::min(n, (s + 1) * SLICE); ++r)
+            w = std::max(w, c->K.row_ptr[r + 1] - c->K.row_ptr[r]);
+        sp[s + 1] = sp[s] + w * SLICE;
+    }
+    std::vector<int32_t> col(sp[ns]);
+    std::vector<double> val(sp[ns], 0.0);
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t w = (sp[s + 1] - sp[s]) / SLICE;
+        for (int lane = 0; lane < SLICE; ++lane) {
+            const int64_t r = s * SLICE + lane;
+            const int64_t len = r < n ? c->K.row_ptr[r + 1] - c->K.row_ptr[r] : 0;
+            for (int64_t k = 0; k < w; ++k) {
+                const int64_t o = sp[s] + k * SLICE + lane;
+                if (k < len) {
+                    col[o] = c->K.col[c->K.row_ptr[r] + k];
+                    val[o] = c->K.val[c->K.row_ptr[r] + k];
+                } else {
+                    col[o] = (int32_t)std::min<int64_t>(r, n - 1);
+                    val[o] = 0.0;
+                }
+            }
+        }
+    }
+    c->A.n = n;
+    c->A.n_slices = ns;
+    c->A.slice_ptr = upload(c, c->pool_asm, sp);
+    c->A.col = upload(c, c->pool_asm, col);
+    c->A.val = upload(c, c->pool_asm, val);
+    std::vector<float> v32(val.begin(), val.end());
+    c->A.val32 = upload(c, c->pool_asm, v32);
+}
+
+void do_assemble(sdc_ctx* c) {
+    require(c->body[0].set && c->body[1].set, SDC_ERR_STATE, "both bodies must be set before sdc_assemble");
+    require(c->contact_set, SDC_ERR_STATE, "sdc_set_contact must precede sdc_assemble");
+    require(c->motion_set, SDC_ERR_STATE, "sdc_set_motion must precede sdc_assemble");
+    drop_graph(c);
+    free_pool(c, c->pool_scheme);
+    free_pool(c, c->pool_asm);
+    c->assembled = false;
+    c->temp_set = false;
+
+    HostCSR K0, K1;
+    std::vector<double> m0, m1, g0, g1;
+    assemble_body(c->body[0], K0, m0, g0);
+    assemble_body(c->body[1], K1, m1, g1);
+    const int64_t nf = K0.n, nm = K1.n;
+    c->n_fix = nf;
+    c->n = nf + nm;
+    require(c->n < (int64_t)INT32_MAX, SDC_ERR_ARG, "too many DOFs");
+    c->K.n = c->n;
+    c->K.row_ptr.assign(c->n + 1, 0);
+    c->K.col.resize(K0.col.size() + K1.col.size());
+    c->K.val.resize(K0.val.size() + K1.val.size());
+    std::copy(K0.row_ptr.begin(), K0.row_ptr.end(), c->K.row_ptr.begin());
+    for (int64_t i = 1; i <= nm; ++i) c->K.row_ptr[nf + i] = K0.row_ptr[nf] + K1.row_ptr[i];
+    std::copy(K0.col.begin(), K0.col.end(), c->K.col.begin());
+    for (size_t k = 0; k < K1.col.size(); ++k) c->K.col[K0.col.size() + k] = K1.col[k] + (int32_t)nf;
+    std::copy(K0.val.begin(), K0.val.end(), c->K.val.begin());
+    std::copy(K1.val.begin(), K1.val.end(), c->K.val.begin() + K0.val.size());
+    c->nnz = (int64_t)c->K.col.size();
+    c->mass_h = m0;
+    c->mass_h.insert(c->mass_h.end(), m1.begin(), m1.end());
+    c->genv_h = g0;
+    c->genv_h.insert(c->genv_h.end(), g1.begin(), g1.end());
+    std::vector<double> diag(c->n, 0.0), minv(c->n);
+    for (int64_t i = 0; i < c->n; ++i) {
+        for (int64_t k = c->K.row_ptr[i]; k < c->K.row_ptr[i + 1]; ++k)
+            if (c->K.col[k] == i) diag[i] = c->K.val[k];
+        require(c->mass_h[i] > 0.0, SDC_ERR_ARG, "node with zero lumped mass (unused node?)");
+        minv[i] = 1.0 / c->mass_h[i];
+    }
+
+    c->ch = build_contact(c->body[0], c->body[1], c->cq_fix, c->cq_mov, c->dir);
+
+    SDC_CUDA_TRY(cudaSetDevice(c->device));
+    build_ell(c);
+    c->d_mass = upload(c, c->pool_asm, c->mass_h);
+    c->d_minv = upload(c, c->pool_asm, minv);
+    c->d_diagK = upload(c, c->pool_asm, diag);
+    c->d_genv = upload(c, c->pool_asm, c->genv_h);
+
+    // contact tables
+    ContactHost& H = c->ch;
+    ContactDev& C = c->C;
+    C = ContactDev{};
+    C.n_iface = (int)H.dof.size();
+    C.n_iface_fix = H.n_iface_fix;
+    C.nq_fix = H.nq_fix;
+    C.nq_mov = H.nq_mov;
+    C.dof = upload(c, c->pool_asm, H.dof);
+    std::vector<double> mI(H.dof.size());
+    for (size_t a = 0; a < H.dof.size(); ++a) mI[a] = c->mass_h[H.dof[a]];
+    C.mass = upload(c, c->pool_asm, mI);
+    C.inc_ptr = upload(c, c->pool_asm, H.inc_ptr);
+    C.inc_quad = upload(c, c->pool_asm, H.inc_quad);
+    C.inc_code = upload(c, c->pool_asm, H.inc_code);
+    C.rect = reinterpret_cast<const Rect4*>(upload(c, c->pool_asm, H.rect));
+    C.qnode = reinterpret_cast<const int4*>(upload(c, c->pool_asm, H.qnode));
+    auto bins = [&](const BinsHost& b) {
+        BinsDev d;
+        d.ou = b.ou;
+        d.ov = b.ov;
+        d.bu = b.bu;
+        d.bv = b.bv;
+        d.nu = b.nu;
+        d.nv = b.nv;
+        d.ptr = upload(c, c->pool_asm, b.ptr);
+        d.item = upload(c, c->pool_asm, b.item);
+        return d;
+    };
+    C.bins_fix = bins(H.bins_fix);
+    C.bins_mov = bins(H.bins_mov);
+    C.dir_u = H.dir_u;
+    C.dir_v = H.dir_v;
+    C.z0 = c->z0;
+    C.amp = c->amp;
+    C.period = c->period;
+    C.q0 = c->q0;
+    C.h_c = c->h_c;
+    C.pos = upload(c, c->pool_asm, H.pos);
+
+    // state and CG work vectors
+    const size_t N = (size_t)c->n;
+    c->Tn = dalloc_n<double>(c, c->pool_asm, N);
+    c->X = dalloc_n<double>(c, c->pool_asm, N);
+    c->R = dalloc_n<double>(c, c->pool_asm, N);
+    c->Z = dalloc_n<double>(c, c->pool_asm, N);
+    c->P = dalloc_n<double>(c, c->pool_asm, N);
+    c->Y = dalloc_n<double>(c, c->pool_asm, N);
+    c->D = dalloc_n<double>(c, c->pool_asm, N);
+    c->st = dalloc_n<StepState>(c, c->pool_asm, 1);
+    c->cgs = dalloc_n<CgState>(c, c->pool_asm, 1);
+    c->max_blocks = (int)blocks_for(c->n, RED_BLOCK) + 1;
+    c->partials = dalloc_n<double>(c, c->pool_asm, (size_t)4 * c->max_blocks);
+    c->counter = dalloc_n<unsigned int>(c, c->pool_asm, 4);
+    SDC_CUDA_TRY(cudaMemsetAsync(c->counter, 0, 4 * sizeof(unsigned int), c->stream));
+    SDC_CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->stream));
+    const size_t NI = (size_t)C.n_iface;
+    c->E1.cnt = dalloc_n<int32_t>(c, c->pool_asm, NI);
+    c->E1.idx = dalloc_n<int32_t>(c, c->pool_asm, NI * MAXE);
+    c->E1.coef = dalloc_n<double>(c, c->pool_asm, NI * MAXE);
+    c->E1.cst = dalloc_n<double>(c, c->pool_asm, NI);
+    c->Ti1 = dalloc_n<double>(c, c->pool_asm, NI);
+    SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->assembled = true;
+}
+
+void alloc_scheme_buffers(sdc_ctx* c) {
+    free_pool(c, c->pool_scheme);
+    const Weights& W = c->W;
+    const int M = W.M, P = W.P;
+    const size_t N = (size_t)c->n, NI = (size_t)c->C.n_iface;
+    const int n_int = (int)c->nondeg.size();
+    c->Tstd.assign(M + 1, nullptr);
+    c->Tstd[0] = c->Tn;
+    for (int m = 1; m <= M; ++m) {
+        const bool degenerate = std::find(c->nondeg.begin(), c->nondeg.end(), m) == c->nondeg.end();
+        c->Tstd[m] = degenerate ? c->Tstd[m - 1] : dalloc_n<double>(c, c->pool_scheme, N);
+    }
+    for (int s = 0; s < 2; ++s)
+        for (int j = 0; j < M; ++j) {
+            const bool degenerate = std::find(c->nondeg.begin(), c->nondeg.end(), j + 1) == c->nondeg.end();
+            if (s == 1 && degenerate) c->FI[1][j] = c->FI[0][j];  // T_j = T_n: same in every iterate
+            else c->FI[s][j] = dalloc_n<double>(c, c->pool_scheme, N);
+        }
+    for (int s = 0; s < 2; ++s) {
+        c->fe[s] = dalloc_n<double>(c, c->pool_scheme, (size_t)n_int * (P + 1) * NI);
+        c->ihat[s] = dalloc_n<double>(c, c->pool_scheme, (size_t)n_int * NI);
+        SDC_CUDA_TRY(cudaMemsetAsync(c->ihat[s], 0, (size_t)n_int * NI * sizeof(double), c->stream));
+    }
+    c->Ta = dalloc_n<double>(c, c->pool_scheme, NI);
+    c->Tb = dalloc_n<double>(c, c->pool_scheme, NI);
+    c->fst = dalloc_n<double>(c, c->pool_scheme, NI);
+    const size_t slots = (size_t)n_int * (P + 1);
+    c->E.cnt = dalloc_n<int32_t>(c, c->pool_scheme, slots * NI);
+    c->E.idx = dalloc_n<int32_t>(c, c->pool_scheme, slots * MAXE * NI);
+    c->E.coef = dalloc_n<double>(c, c->pool_scheme, slots * MAXE * NI);
+    c->E.cst = dalloc_n<double>(c, c->pool_scheme, slots * NI);
+    // dt-scaled weights
+    std::vector<double> Stil(W.Stil), Semb(W.Semb), Shat(W.Shat), slot_pos(slots);
+    for (double& v : Stil) v *= c->dt;
+    for (double& v : Semb) v *= c->dt;
+    for (double& v : Shat) v *= c->dt;
+    for (int ii = 0; ii < n_int; ++ii)
+        for (int q = 0; q <= P; ++q) slot_pos[(size_t)ii * (P + 1) + q] = W.emb[(size_t)(c->nondeg[ii] - 1) * (P + 1) + q];
+    c->w_Stil = upload(c, c->pool_scheme, Stil);
+    c->w_Semb = upload(c, c->pool_scheme, Semb);
+    c->w_Shat = upload(c, c->pool_scheme, Shat);
+    c->w_emb = upload(c, c->pool_scheme, W.emb);
+    c->w_slot = upload(c, c->pool_scheme, slot_pos);
+    SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+}
+
+void build_step_graph(sdc_ctx* c) {
+    drop_graph(c);
+    alloc_scheme_buffers(c);
+    const Weights& W = c->W;
+    const int M = W.M, P = W.P, K = c->K_sweeps;
+    const int NI = c->C.n_iface;
+    const int n_int = (int)c->nondeg.size();
+    const double dt = c->dt;
+    const unsigned nb = blocks_for(c->n, RED_BLOCK);
+    SDC_CUDA_TRY(cudaGraphCreate(&c->graph, 0));
+    Chain ch(c->graph);
+
+    // geometry of f^E at every embedded node of the step (independent of T)
+    GeomArgs ga{};
+    ga.C = c->C;
+    ga.E = c->E;
+    ga.slot_pos = c->w_slot;
+    ga.st = c->st;
+    ga.use_fixed = 0;
+    ga.n_slots = n_int * (P + 1);
+    ga.status = &c->st->status;
+    ch.kernel(k_iface_geom, blocks_for((int64_t)NI * ga.n_slots, 128), 128u, ga);
+
+    // F^I at a standard node that coincides with t_n (Lobatto)
+    for (int j = 1; j <= M; ++j)
+        if (std::find(c->nondeg.begin(), c->nondeg.end(), j) == c->nondeg.end())
+            ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->FI[0][j - 1]);
+
+    auto sdt_row = [&](int m, double* out) {
+        for (int j = 0; j < MAX_M; ++j) out[j] = j < M ? dt * W.S[(size_t)(m - 1) * M + j] : 0.0;
+    };
+    int solve = 0;
+    auto iface_args = [&](int ii, int m, int mode, int set_old, int set_new) {
+        IfaceArgs ia{};
+        ia.C = c->C;
+        ia.A = c->A;
+        ia.g = c->d_genv;
+        ia.mode = mode;
+        ia.first = ii == 0;
+        ia.P = P;
+        ia.dt = dt;
+        ia.st = c->st;
+        ia.emb = c->w_emb + (size_t)(m - 1) * (P + 1);
+        ia.Tprev = c->Tstd[m - 1];
+        ia.Tout = c->Tstd[m];
+        ia.X = c->X;
+        ia.FIm = c->FI[set_old][m - 1];
+        for (int j = 0; j < M; ++j) ia.FI[j] = c->FI[set_old][j];
+        ia.nFI = M;
+        ia.Stil = c->w_Stil + (size_t)(m - 1) * P * M;
+        ia.Semb = c->w_Semb + (size_t)(m - 1) * P * P;
+        ia.Shat = c->w_Shat + (size_t)(m - 1) * P;
+        ia.E = c->E;
+        ia.slot0 = ii * (P + 1);
+        ia.fe_old = c->fe[set_old] + (size_t)ii * (P + 1) * NI;
+        ia.fe_new = c->fe[set_new] + (size_t)ii * (P + 1) * NI;
+        ia.fe_prev_end = ii > 0 ? c->fe[set_new] + ((size_t)(ii - 1) * (P + 1) + P) * NI : nullptr;
+        ia.ihat_new = c->ihat[set_new] + (size_t)ii * NI;
+        ia.Ta = c->Ta;
+        ia.Tb = c->Tb;
+        ia.fstar = c->fst;
+        return ia;
+    };
+    auto residual = [&](int set, int k) {
+        ResidualArgs ra{};
+        ra.mass = c->d_mass;
+        ra.Tn = c->Tn;
+        for (int m = 1; m <= M; ++m) {
+            ra.Tm[m - 1] = c->Tstd[m];
+            ra.FI[m - 1] = c->FI[set][m - 1];
+            for (int j = 0; j < M; ++j) ra.Sdt[m - 1][j] = dt * W.S[(size_t)(m - 1) * M + j];
+            auto it = std::find(c->nondeg.begin(), c->nondeg.end(), m);
+            ra.ihat[m - 1] = it == c->nondeg.end() ? nullptr
+                                                   : c->ihat[set] + (size_t)(it - c->nondeg.begin()) * NI;
+        }
+        ra.pos = c->C.pos;
+        ra.M = M;
+        ra.n = c->n;
+        ra.partials = c->partials;
+        ra.counter = c->counter;
+        ra.out = &c->st->residual[k];
+        ch.kernel(k_residual, nb, (unsigned)RED_BLOCK, ra);
+    };
+
+    // ---- Algorithm 1 (predictor)
+    for (int ii = 0; ii < n_int; ++ii) {
+        const int m = c->nondeg[ii];
+        const double dtau = dt * (W.c[m] - W.c[m - 1]);
+        RhsArgs r{};
+        r.mode = RHS_PRED;
+        r.Tprev = c->Tstd[m - 1];
+        r.g = c->d_genv;
+        r.x0 = c->Tstd[m - 1];
+        r.pos = c->C.pos;
+        add_solve(c, ch, cg_args(c, dtau, solve++, c->rtol, c->max_iter), r);
+        BulkArgs b{};
+        b.A = c->A;
+        b.minv = c->d_minv;
+        b.g = c->d_genv;
+        b.X = c->X;
+        b.Tprev = c->Tstd[m - 1];
+        b.Tout = c->Tstd[m];
+        b.dtau = dtau;
+        b.mode = RHS_PRED;
+        b.n = c->n;
+        ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
+        ch.kernel(k_iface_loop, (unsigned)IFACE_CLUSTER, (unsigned)IFACE_THREADS, iface_args(ii, m, RHS_PRED, 0, 0));
+        ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m], c->FI[0][m - 1]);
+    }
+    // ---- Algorithm 2 (sweeps)
+    for (int k = 1; k <= K; ++k) {
+        const int so = (k - 1) & 1, sn = k & 1;
+        if (c->residuals) residual(so, k - 1);
+        for (int ii = 0; ii < n_int; ++ii) {
+            const int m = c->nondeg[ii];
+            const double dtau = dt * (W.c[m] - W.c[m - 1]);
+            RhsArgs r{};
+            r.mode = RHS_SWEEP;
+            r.Tprev = c->Tstd[m - 1];
+            r.g = c->d_genv;
+            r.FIm = c->FI[so][m - 1];
+            for (int j = 0; j < M; ++j) r.FI[j] = c->FI[so][j];
+            sdt_row(m, r.Sdt);
+            r.nFI = M;
+            r.ihat = c->ihat[so] + (size_t)ii * NI;
+            r.pos = c->C.pos;
+            r.x0 = c->Tstd[m];
+            add_solve(c, ch, cg_args(c, dtau, solve++, c->rtol, c->max_iter), r);
+            BulkArgs b{};
+            b.A = c->A;
+            b.minv = c->d_minv;
+            b.g = c->d_genv;
+            b.X = c->X;
+            b.Tprev = c->Tstd[m - 1];
+            b.Tout = c->Tstd[m];
+            b.FIm = c->FI[so][m - 1];
+            for (int j = 0; j < M; ++j) b.FI[j] = c->FI[so][j];
+            sdt_row(m, b.Sdt);
+            b.nFI = M;
+            b.dtau = dtau;
+            b.mode = RHS_SWEEP;
+            b.n = c->n;
+            ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
+            ch.kernel(k_iface_loop, (unsigned)IFACE_CLUSTER, (unsigned)IFACE_THREADS,
+                      iface_args(ii, m, RHS_SWEEP, so, sn));
+            if (k < K || c->residuals)
+                ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m],
+                          c->FI[sn][m - 1]);
+        }
+    }
+    if (c->residuals) residual(K & 1, K);
+    ch.copy(c->Tn, c->Tstd[M], (size_t)c->n * sizeof(double));
+    ch.kernel(k_heat, nb, (unsigned)RED_BLOCK, (const double*)c->d_mass, (const double*)c->Tn, (int64_t)c->n,
+              (int64_t)c->n_fix, c->partials, c->counter, &c->st->heat[0]);
+    ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], n_int, NI);
+    SDC_CUDA_TRY(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->graph_ready = true;
+}
+
+sdc_status fail(sdc_ctx* c, sdc_status code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <class F>
+sdc_status guarded(sdc_ctx* c, F&& f) {
+    if (!c) return SDC_ERR_ARG;
+    try {
+        f();
+        return SDC_OK;
+    } catch (const ApiError& e) {
+        return fail(c, e.code, e.what);
+    } catch (const CudaError& e) {
+        cudaGetLastError();
+        return fail(c, e.code == cudaErrorMemoryAllocation ? SDC_ERR_OOM : SDC_ERR_CUDA, e.what);
+    } catch (const std::bad_alloc&) {
+        return fail(c, SDC_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(c, SDC_ERR_ARG, e.what());
+    }
+}
+
+void fill_report(sdc_ctx* c, sdc_step_report* rep) {
+    const StepState& s = *c->st_host;
+    std::memset(rep, 0, sizeof(*rep));
+    rep->t = s.t0 + (double)s.n_done * s.dt;
+    rep->sweeps = c->K_sweeps;
+    const int n_solves = (int)c->nondeg.size() * (c->K_sweeps + 1);
+    rep->n_solves = n_solves;
+    for (int i = 0; i < n_solves; ++i) {
+        rep->cg_iters_total += s.cg_iters[i];
+        rep->cg_iters_max = std::max(rep->cg_iters_max, s.cg_iters[i]);
+        rep->refinements_total += s.refinements[i];
+    }
+    rep->status = s.status;
+    for (int k = 0; k <= SDC_MAX_SWEEPS; ++k) rep->residual[k] = (c->residuals && k <= c->K_sweeps) ? s.residual[k] : -1.0;
+    rep->heat_stand = s.heat[0];
+    rep->heat_stock = s.heat[1];
+}
+
+sdc_status read_state(sdc_ctx* c, sdc_step_report* rep) {
+    SDC_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream));
+    SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (rep) fill_report(c, rep);
+    const int s = c->st_host->status;
+    if (s != 0) {
+        SDC_CUDA_TRY(cudaMemsetAsync(&c->st->status, 0, sizeof(int), c->stream));
+        if (s == SDC_ERR_NOT_CONVERGED) throw ApiError(SDC_ERR_NOT_CONVERGED, "a CG solve reached cg_max_iter");
+        if (s == SDC_ERR_ARG) throw ApiError(SDC_ERR_ARG, "contact operator has more than 32 entries per DOF");
+        throw ApiError((sdc_status)s, "device reported an error");
+    }
+    return SDC_OK;
+}
+
+void ensure_ready(sdc_ctx* c) {
+    require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+    require(c->scheme_set, SDC_ERR_STATE, "call sdc_set_scheme first");
+    require(c->temp_set, SDC_ERR_STATE, "call sdc_set_temperature first");
+    if (!c->graph_ready) build_step_graph(c);
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream) {
+    if (!out) return SDC_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return SDC_ERR_CUDA;
+    }
+    sdc_ctx* c = new (std::nothrow) sdc_ctx();
+    if (!c) return SDC_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaMallocHost((void**)&c->st_host, sizeof(StepState)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SDC_ERR_CUDA;
+    }
+    std::memset(c->st_host, 0, sizeof(StepState));
+    *out = c;
+    return SDC_OK;
+}
+
+void sdc_destroy(sdc_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    drop_graph(c);
+    free_pool(c, c->pool_scheme);
+    free_pool(c, c->pool_asm);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    delete c;
+}
+
+const char* sdc_last_error(const sdc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sdc_status sdc_set_allocator(sdc_ctx* c, sdc_alloc_fn alloc, sdc_free_fn free_fn, void* user) {
+    return guarded(c, [&] {
+        require(!c->assembled, SDC_ERR_STATE, "allocator must be set before sdc_assemble");
+        require((alloc == nullptr) == (free_fn == nullptr), SDC_ERR_ARG, "give both alloc and free, or neither");
+        c->alloc = alloc;
+        c->free_fn = free_fn;
+        c->user = user;
+    });
+}
+
+sdc_status sdc_set_body(sdc_ctx* c, int body, const double* xyz, int64_t n_nodes, const int64_t* hex8, int64_t n_hex,
+                        const double* k_per_hex, double k, double rho, double cc) {
+    return guarded(c, [&] {
+        require(body == 0 || body == 1, SDC_ERR_ARG, "body must be 0 (stand) or 1 (stock)");
+        require(xyz && hex8 && n_nodes > 0 && n_hex > 0, SDC_ERR_ARG, "empty mesh");
+        require(rho > 0 && cc > 0, SDC_ERR_ARG, "rho and c must be positive");
+        require(k_per_hex || k > 0, SDC_ERR_ARG, "conductivity must be positive");
+        BodyInput& b = c->body[body];
+        b.xyz.assign(xyz, xyz + 3 * n_nodes);
+        b.hex8.assign(hex8, hex8 + 8 * n_hex);
+        if (k_per_hex) {
+            b.k_hex.assign(k_per_hex, k_per_hex + n_hex);
+            for (double v : b.k_hex) require(v > 0, SDC_ERR_ARG, "conductivity must be positive");
+        } else {
+            b.k_hex.clear();
+        }
+        b.k = k;
+        b.rho = rho;
+        b.c = cc;
+        b.set = true;
+        c->assembled = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_robin(sdc_ctx* c, int body, const int64_t* quad4, int64_t n_faces, double h, double T_env) {
+    return guarded(c, [&] {
+        require(body == 0 || body == 1, SDC_ERR_ARG, "body must be 0 or 1");
+        require(n_faces >= 0 && (n_faces == 0 || quad4), SDC_ERR_ARG, "bad face list");
+        require(h >= 0, SDC_ERR_ARG, "h must be >= 0");
+        BodyInput& b = c->body[body];
+        b.robin.assign(quad4, quad4 + 4 * n_faces);
+        b.h = h;
+        b.T_env = T_env;
+        c->assembled = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_contact(sdc_ctx* c, const int64_t* sq, int64_t n_sq, const int64_t* kq, int64_t n_kq, double h_c,
+                           double q0_peak) {
+    return guarded(c, [&] {
+        require(sq && kq && n_sq > 0 && n_kq > 0, SDC_ERR_ARG, "empty contact face list");
+        require(h_c >= 0 && q0_peak >= 0, SDC_ERR_ARG, "h_c and q0 must be >= 0");
+        c->cq_fix.assign(sq, sq + 4 * n_sq);
+        c->cq_mov.assign(kq, kq + 4 * n_kq);
+        c->h_c = h_c;
+        c->q0 = q0_peak;
+        c->contact_set = true;
+        c->assembled = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_motion(sdc_ctx* c, const double dir[3], double z0, double amp, double period) {
+    return guarded(c, [&] {
+        require(dir != nullptr, SDC_ERR_ARG, "dir is NULL");
+        require(period > 0, SDC_ERR_ARG, "period must be > 0 (inf for a resting stock)");
+        const double nrm = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        require(nrm > 0 && std::isfinite(nrm), SDC_ERR_ARG, "bad motion direction");
+        for (int i = 0; i < 3; ++i) c->dir[i] = dir[i];
+        c->z0 = z0;
+        c->amp = amp;
+        c->period = period;
+        c->motion_set = true;
+        if (c->assembled) {
+            c->C.z0 = z0;
+            c->C.amp = amp;
+            c->C.period = period;
+            require(std::fabs(dir[c->ch.normal]) <= 1e-12, SDC_ERR_ARG, "motion direction leaves the contact plane");
+            c->C.dir_u = dir[c->ch.u];
+            c->C.dir_v = dir[c->ch.v];
+            c->graph_ready = false;
+        }
+    });
+}
+
+sdc_status sdc_assemble(sdc_ctx* c) {
+    return guarded(c, [&] { do_assemble(c); });
+}
+
+sdc_status sdc_set_scheme(sdc_ctx* c, sdc_nodes nodes, int M, int P, int sweeps, int window, double dt, double cg_rtol,
+                          int cg_max_iter, sdc_precision precision) {
+    return guarded(c, [&] {
+        require(nodes == SDC_NODES_EQUI_NOLEFT || nodes == SDC_NODES_RADAU_RIGHT || nodes == SDC_NODES_LOBATTO,
+                SDC_ERR_ARG, "unknown node family");
+        require(M >= 1 && M <= MAX_M, SDC_ERR_ARG, "M out of range [1, 16]");
+        require(P >= 1 && P <= MAX_P, SDC_ERR_ARG, "P out of range [1, 64]");
+        require(sweeps >= 0 && sweeps <= SDC_MAX_SWEEPS, SDC_ERR_ARG, "sweeps out of range [0, 15]");
+        require(window >= 0 && window <= P, SDC_ERR_ARG, "window out of range [0, P]");
+        require(dt > 0 && std::isfinite(dt), SDC_ERR_ARG, "dt must be positive");
+        require(cg_rtol > 0 && cg_rtol < 1, SDC_ERR_ARG, "cg_rtol must be in (0, 1)");
+        require(cg_max_iter >= 1, SDC_ERR_ARG, "cg_max_iter must be >= 1");
+        require(precision == SDC_FP64, SDC_ERR_ARG, "only SDC_FP64 is available in this build");
+        require(!(nodes == SDC_NODES_LOBATTO && M < 2), SDC_ERR_ARG, "Lobatto needs M >= 2");
+        c->W = make_weights(nodes, M, P, window);
+        c->K_sweeps = sweeps;
+        c->dt = dt;
+        c->rtol = cg_rtol;
+        c->max_iter = cg_max_iter;
+        c->precision = precision;
+        c->nondeg.clear();
+        for (int m = 1; m <= M; ++m)
+            if (c->W.c[m] > c->W.c[m - 1]) c->nondeg.push_back(m);
+        c->scheme_set = true;
+        c->graph_ready = false;
+        if (c->assembled) {
+            c->st_host->dt = dt;
+            SDC_CUDA_TRY(cudaMemcpyAsync(&c->st->dt, &c->st_host->dt, sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream));
+            SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
+    });
+}
+
+sdc_status sdc_set_diagnostics(sdc_ctx* c, int residuals) {
+    return guarded(c, [&] {
+        c->residuals = residuals ? 1 : 0;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_temperature(sdc_ctx* c, const double* T, double T_uniform, double t0) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        if (T) {
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->Tn, T, (size_t)c->n * sizeof(double), cudaMemcpyDefault, c->stream));
+        } else {
+            std::vector<double> v((size_t)c->n, T_uniform);
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->Tn, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
+        StepState* h = c->st_host;
+        std::memset(h, 0, sizeof(StepState));
+        h->t0 = t0;
+        h->dt = c->scheme_set ? c->dt : 1.0;
+        SDC_CUDA_TRY(cudaMemcpyAsync(c->st, h, sizeof(StepState), cudaMemcpyHostToDevice, c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        c->temp_set = true;
+    });
+}
+
+sdc_status sdc_step(sdc_ctx* c, sdc_step_report* rep) {
+    return guarded(c, [&] {
+        ensure_ready(c);
+        SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
+        if (rep) read_state(c, rep);
+    });
+}
+
+sdc_status sdc_run_horizon(sdc_ctx* c, int64_t n_steps, sdc_step_report* last) {
+    return guarded(c, [&] {
+        require(n_steps >= 0, SDC_ERR_ARG, "n_steps must be >= 0");
+        ensure_ready(c);
+        for (int64_t i = 0; i < n_steps; ++i) SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
+        read_state(c, last);
+    });
+}
+
+sdc_status sdc_synchronize(sdc_ctx* c) {
+    return guarded(c, [&] {
+        if (c->assembled) read_state(c, nullptr);
+        else SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+}
+
+sdc_status sdc_get_sizes(const sdc_ctx* cc, int64_t* n_dof, int64_t* n_stand, int64_t* nnz, int64_t* n_contact) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        if (n_dof) *n_dof = c->n;
+        if (n_stand) *n_stand = c->n_fix;
+        if (nnz) *nnz = c->nnz;
+        if (n_contact) *n_contact = c->C.n_iface;
+    });
+}
+
+sdc_status sdc_get_temperature(sdc_ctx* c, double* out, int64_t n) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(out && n == c->n, SDC_ERR_ARG, "out must hold n_dof doubles");
+        SDC_CUDA_TRY(cudaMemcpyAsync(out, c->Tn, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+}
+
+sdc_status sdc_get_temperature_device(const sdc_ctx* cc, const double** dptr) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(dptr != nullptr, SDC_ERR_ARG, "dptr is NULL");
+        *dptr = c->Tn;
+    });
+}
+
+sdc_status sdc_get_heat_totals(sdc_ctx* c, sdc_heat* out) {
+    return guarded(c, [&] {
+        require(c->assembled && c->temp_set, SDC_ERR_STATE, "no state yet");
+        require(out != nullptr, SDC_ERR_ARG, "out is NULL");
+        read_state(c, nullptr);
+        const StepState& s = *c->st_host;
+        if (s.n_done == 0) {
+            // no step taken yet: compute the stored heat on the host side of the copy
+            std::vector<double> T((size_t)c->n);
+            SDC_CUDA_TRY(cudaMemcpy(T.data(), c->Tn, T.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            double h0 = 0, h1 = 0;
+            for (int64_t i = 0; i < c->n; ++i) (i < c->n_fix ? h0 : h1) += c->mass_h[i] * T[i];
+            out->stored_stand = h0;
+            out->stored_stock = h1;
+        } else {
+            out->stored_stand = s.heat[0];
+            out->stored_stock = s.heat[1];
+        }
+        out->friction_in = s.friction_in;
+        out->t = s.t0 + (double)s.n_done * s.dt;
+    });
+}
+
+sdc_status sdc_get_system(const sdc_ctx* cc, int64_t* row_ptr, int64_t* col, double* val, double* mass, double* genv) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        if (row_ptr) std::copy(c->K.row_ptr.begin(), c->K.row_ptr.end(), row_ptr);
+        if (col)
+            for (size_t k = 0; k < c->K.col.size(); ++k) col[k] = c->K.col[k];
+        if (val) std::copy(c->K.val.begin(), c->K.val.end(), val);
+        if (mass) std::copy(c->mass_h.begin(), c->mass_h.end(), mass);
+        if (genv) std::copy(c->genv_h.begin(), c->genv_h.end(), genv);
+    });
+}
+
+sdc_status sdc_apply_operator(sdc_ctx* c, double dtau, const double* x, double* y) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(x && y, SDC_ERR_ARG, "null buffer");
+        k_apply_operator<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->A, c->d_mass, dtau, x, y);
+        SDC_CUDA_TRY(cudaGetLastError());
+    });
+}
+
+sdc_status sdc_solve(sdc_ctx* c, double dtau, const double* b, double* x, int32_t* iters) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(b && x, SDC_ERR_ARG, "null buffer");
+        require(dtau >= 0, SDC_ERR_ARG, "dtau must be >= 0");
+        const double rtol = c->scheme_set ? c->rtol : 1e-12;
+        const int max_iter = c->scheme_set ? c->max_iter : 2000;
+        cudaGraph_t g;
+        SDC_CUDA_TRY(cudaGraphCreate(&g, 0));
+        std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> guard(g, &cudaGraphDestroy);
+        Chain ch(g);
+        RhsArgs r{};
+        r.mode = RHS_GIVEN;
+        r.b_in = b;
+        r.x0 = x;
+        r.pos = c->C.pos;
+        add_solve(c, ch, cg_args(c, dtau, 0, rtol, max_iter), r);
+        ch.copy(x, c->X, (size_t)c->n * sizeof(double));
+        cudaGraphExec_t ex;
+        SDC_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+        cudaError_t e = cudaGraphLaunch(ex, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(ex);
+        SDC_CUDA_TRY(e);
+        int it = 0;
+        SDC_CUDA_TRY(cudaMemcpy(&it, &c->st->cg_iters[0], sizeof(int), cudaMemcpyDeviceToHost));
+        if (iters) *iters = it;
+        read_state(c, nullptr);
+    });
+}
+
+sdc_status sdc_contact_flux(sdc_ctx* c, const double* T, double t, double* fE) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(T && fE, SDC_ERR_ARG, "null buffer");
+        GeomArgs ga{};
+        ga.C = c->C;
+        ga.E = c->E1;
+        ga.slot_pos = nullptr;
+        ga.st = c->st;
+        ga.t_fixed = t;
+        ga.use_fixed = 1;
+        ga.n_slots = 1;
+        ga.status = &c->st->status;
+        const int NI = c->C.n_iface;
+        SDC_CUDA_TRY(cudaMemsetAsync(fE, 0, (size_t)c->n * sizeof(double), c->stream));
+        k_iface_geom<<<blocks_for(NI, 128), 128, 0, c->stream>>>(ga);
+        k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 0);
+        k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 1);
+        SDC_CUDA_TRY(cudaGetLastError());
+        read_state(c, nullptr);
+    });
+}
+
+}  // extern "C"

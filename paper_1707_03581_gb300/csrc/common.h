@@ -1,0 +1,168 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sdcheat.h"
+
+namespace sdc {
+
+constexpr int SLICE = 32;       // rows per SELL slice (one warp)
+constexpr int MAX_M = 16;       // standard nodes
+constexpr int MAX_P = 64;       // embedded substeps per interval
+constexpr int MAX_SOLVES = (SDC_MAX_SWEEPS + 1) * MAX_M;
+constexpr int RED_BLOCK = 256;  // threads of the reduction kernels
+
+// ----------------------------------------------------------------- host data
+
+struct BodyInput {
+    bool set = false;
+    std::vector<double> xyz;      // n_nodes x 3
+    std::vector<int64_t> hex8;    // n_hex x 8
+    std::vector<double> k_hex;    // n_hex (empty = uniform)
+    double k = 0, rho = 0, c = 0;
+    std::vector<int64_t> robin;   // n_faces x 4
+    double h = 0, T_env = 0;
+    int64_t n_nodes() const { return (int64_t)xyz.size() / 3; }
+    int64_t n_hex() const { return (int64_t)hex8.size() / 8; }
+};
+
+struct HostCSR {
+    int64_t n = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+};
+
+struct Weights {
+    int kind = 0, M = 0, P = 0, w = 0;
+    std::vector<double> c;      // M+1, c[0] = 0
+    std::vector<double> emb;    // M x (P+1)
+    std::vector<double> S;      // M x M
+    std::vector<double> Shat;   // M x P
+    std::vector<double> Stil;   // M x P x M
+    std::vector<double> Semb;   // M x P x P
+};
+
+Weights make_weights(int kind, int M, int P, int window);
+int window_start(int p, int P, int w);
+
+// Assemble K = -(A + B_env) (CSR, sorted columns), lumped mass and b_env of one body.
+void assemble_body(const BodyInput& b, HostCSR& K, std::vector<double>& mass, std::vector<double>& genv);
+
+struct BinsHost {
+    double ou = 0, ov = 0, bu = 1, bv = 1;
+    int nu = 0, nv = 0;
+    std::vector<int32_t> ptr, item;
+};
+
+// Contact tables built on the host (see ContactDev for the meaning).
+struct ContactHost {
+    int normal = 1, u = 0, v = 2;
+    int n_iface_fix = 0;
+    std::vector<int32_t> dof;
+    std::vector<int32_t> inc_ptr, inc_quad, inc_code;
+    std::vector<double> rect;      // 4 per quad
+    std::vector<int32_t> qnode;    // 4 per quad, by corner code
+    int nq_fix = 0, nq_mov = 0;
+    BinsHost bins_fix, bins_mov;
+    double dir_u = 0, dir_v = 0;
+    std::vector<int32_t> pos;      // n_dof
+};
+
+ContactHost build_contact(const BodyInput& stand, const BodyInput& stock, const std::vector<int64_t>& stand_quads,
+                          const std::vector<int64_t>& stock_quads, const double dir[3]);
+
+// ----------------------------------------------------------------- device data
+
+// Sliced ELL, slice height 32: entry (slice s, k, lane) at slice_ptr[s] + 32 k + lane.
+struct EllDev {
+    int64_t n = 0;
+    int64_t n_slices = 0;
+    const int64_t* slice_ptr = nullptr;
+    const int32_t* col = nullptr;
+    const double* val = nullptr;
+    const float* val32 = nullptr;
+};
+
+// Axis-aligned rectangle in the contact plane: x = lo_u, y = lo_v, z = hi_u, w = hi_v.
+struct Rect4 {
+    double x, y, z, w;
+};
+
+struct BinsDev {
+    double ou = 0, ov = 0, bu = 1, bv = 1;   // origin and bin size
+    int nu = 0, nv = 0;
+    const int32_t* ptr = nullptr;           // nu*nv + 1
+    const int32_t* item = nullptr;          // quad ids, stand quads or stock quads
+};
+
+// Contact tables. Interface DOFs: stand rail nodes first, then stock contact nodes.
+struct ContactDev {
+    int n_iface = 0;
+    int n_iface_fix = 0;
+    int nq_fix = 0, nq_mov = 0;            // quads: stand 0..nq_fix-1, stock nq_fix..
+    const int32_t* dof = nullptr;          // n_iface global DOF ids
+    const double* mass = nullptr;          // n_iface lumped masses
+    const int32_t* inc_ptr = nullptr;      // n_iface + 1
+    const int32_t* inc_quad = nullptr;     // incident quad ids
+    const int32_t* inc_code = nullptr;     // corner code of the node in that quad
+    const Rect4* rect = nullptr;           // stock quads in reference position
+    const int4* qnode = nullptr;           // interface-local node at corner codes 0..3
+    BinsDev bins_fix, bins_mov;
+    double dir_u = 0, dir_v = 0;           // in-plane components of the motion direction
+    double z0 = 0, amp = 0, period = 0;
+    double q0 = 0, h_c = 0;
+    const int32_t* pos = nullptr;          // n_dof: interface-local index or -1
+};
+
+// Scalars of one CG solve (device).
+struct CgState {
+    double rz, alpha, beta, bb, rr, pAp;
+    int iter;
+    int done;
+};
+
+// Per-step device state.
+struct StepState {
+    double t0;                 // time origin
+    double dt;
+    long long n_done;          // macro steps completed since set_temperature
+    int status;                // sticky sdc_status
+    int pad;
+    int cg_iters[MAX_SOLVES];
+    int refinements[MAX_SOLVES];
+    double residual[SDC_MAX_SWEEPS + 1];
+    double heat[2];
+    double friction_in;
+    double rmax_partial_dummy;
+};
+
+// ----------------------------------------------------------------- helpers
+
+#define SDC_CUDA_TRY(expr)                                                             \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess) throw ::sdc::CudaError(_e, #expr, __FILE__, __LINE__);   \
+    } while (0)
+
+struct CudaError {
+    cudaError_t code;
+    std::string what;
+    CudaError(cudaError_t c, const char* expr, const char* file, int line)
+        : code(c),
+          what(std::string(cudaGetErrorString(c)) + " in " + expr + " (" + file + ":" + std::to_string(line) + ")") {}
+};
+
+struct ApiError {
+    sdc_status code;
+    std::string what;
+    ApiError(sdc_status c, std::string w) : code(c), what(std::move(w)) {}
+};
+
+}  // namespace sdc

@@ -1,0 +1,525 @@
+// CUDA kernels of the IMEX multi-rate SDC step (sm_103a).
+//
+// Memory-bound work (sliced-ELL SpMV, CG vector updates, right-hand sides)
+// runs one row per thread with the slice layout giving coalesced loads of
+// values and column ids; reductions finish in the last block to arrive
+// (fixed-order combination, no floating-point atomics, so results are
+// reproducible run to run). The contact substep loop runs on one
+// thread-block cluster synchronised with hardware cluster barriers.
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sdc {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// sum_k K[row, k] x[k] over the sliced-ELL row (padding entries carry 0).
+__device__ __forceinline__ double ell_row(const EllDev& A, int64_t row, const double* __restrict__ x) {
+    const int64_t s = row >> 5;
+    const int lane = (int)(row & 31);
+    const int64_t b = A.slice_ptr[s], e = A.slice_ptr[s + 1];
+    double acc = 0.0;
+#pragma unroll 4
+    for (int64_t k = b + lane; k < e; k += SLICE) acc = fma(__ldg(A.val + k), __ldg(x + __ldg(A.col + k)), acc);
+    return acc;
+}
+
+// Block-reduce NQ values, publish per-block partials, and let the last block
+// to finish combine them in a fixed order into out[0..NQ). Returns true in
+// every thread of that last block, after out[] is written.
+template <int NQ, bool MAX>
+__device__ bool reduce_last(double (&v)[NQ], double* partials, unsigned int* counter, double* out) {
+    __shared__ double sh[NQ][32];
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = MAX ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q][warp] = v[q];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = lane < nw ? sh[q][lane] : (MAX ? -1.0 : 0.0);
+            t = MAX ? warp_max(t) : warp_sum(t);
+            if (lane == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = t;
+        }
+        if (lane == 0) {
+            __threadfence();
+            const unsigned int prev = atomicAdd(counter, 1u);
+            am_last = (prev == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double t = MAX ? -1.0 : 0.0;
+        for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+            const double p = __ldcg(partials + (size_t)q * gridDim.x + i);
+            t = MAX ? fmax(t, p) : t + p;
+        }
+        v[q] = MAX ? warp_max(t) : warp_sum(t);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q][warp] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = MAX ? -1.0 : 0.0;
+            for (int w = 0; w < nw; ++w) t = MAX ? fmax(t, sh[q][w]) : t + sh[q][w];
+            out[q] = t;
+        }
+        *counter = 0u;
+    }
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------------------ operator
+
+// y = m .* x + dtau K x
+__global__ void k_apply_operator(EllDev A, const double* __restrict__ mass, double dtau,
+                                 const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.n) y[i] = fma(dtau, ell_row(A, i, x), mass[i] * x[i]);
+}
+
+// F = -K T + g   (f^I(T) + g of Eq. ivp)
+__global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.n) F[i] = g[i] - ell_row(A, i, T);
+}
+
+// ------------------------------------------------------------------ Jacobi-PCG
+
+// Right-hand side of the implicit stage (Algorithm 1: m T_{m-1} + dtau g;
+// Algorithm 2: m T^{k+1}_{m-1} - dtau f^I(T^k_m) + I_{m-1}^m), the initial
+// residual r = b - (m x0 + dtau K x0), z = D r, p = z, and the scalars.
+__global__ void k_cg_init(CgArgs a, RhsArgs r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (i < a.n) {
+        const double m = a.mass[i];
+        double b;
+        if (r.mode == RHS_GIVEN) {
+            b = r.b_in[i];
+        } else if (r.mode == RHS_PRED) {
+            b = m * r.Tprev[i] + a.dtau * r.g[i];
+        } else {
+            double I = 0.0;
+            for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
+            const int pa = r.pos[i];
+            if (pa >= 0) I += r.ihat[pa];
+            b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
+        }
+        const double x0 = r.x0[i];
+        const double Ax = fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
+        const double res = b - Ax;
+        const double d = 1.0 / (m + a.dtau * a.diagK[i]);
+        const double z = res * d;
+        a.X[i] = x0;
+        a.R[i] = res;
+        a.D[i] = d;
+        a.Z[i] = z;
+        a.P[i] = z;
+        v[0] = res * z;
+        v[1] = b * b;
+        v[2] = res * res;
+    }
+    double out[3];
+    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        a.cg->rz = out[0];
+        a.cg->bb = out[1];
+        a.cg->rr = out[2];
+        a.cg->iter = 0;
+        a.cg->beta = 0.0;
+        *a.iters_out = 0;
+        const bool conv = out[2] <= a.rtol2 * out[1];
+        a.cg->done = conv ? 1 : 0;
+        if (conv && a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
+    }
+}
+
+// y = m .* p + dtau K p; alpha = (r, z) / (p, y)
+__global__ void k_cg_spmv(CgArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (i < a.n) {
+        const double p = a.P[i];
+        const double y = fma(a.dtau, ell_row(a.A, i, a.P), a.mass[i] * p);
+        a.Y[i] = y;
+        v[0] = p * y;
+    }
+    double out[1];
+    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        a.cg->pAp = out[0];
+        a.cg->alpha = a.cg->rz / out[0];
+    }
+}
+
+// x += alpha p; r -= alpha y; z = D r; beta = (r, z)_new / (r, z)_old; stop test
+__global__ void k_cg_update(CgArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double alpha = a.cg->alpha;
+    double v[2] = {0.0, 0.0};
+    if (i < a.n) {
+        const double p = a.P[i];
+        a.X[i] = fma(alpha, p, a.X[i]);
+        const double res = fma(-alpha, a.Y[i], a.R[i]);
+        a.R[i] = res;
+        const double z = res * a.D[i];
+        a.Z[i] = z;
+        v[0] = res * z;
+        v[1] = res * res;
+    }
+    double out[2];
+    if (reduce_last<2, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        CgState* s = a.cg;
+        s->beta = out[0] / s->rz;
+        s->rz = out[0];
+        s->rr = out[1];
+        s->iter += 1;
+        *a.iters_out = s->iter;
+        const bool conv = out[1] <= a.rtol2 * s->bb;
+        if (conv || s->iter >= a.max_iter) {
+            s->done = 1;
+            if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
+            if (a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
+        }
+    }
+}
+
+// p = z + beta p
+__global__ void k_cg_pupdate(CgArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double beta = a.cg->beta;
+    if (i < a.n) a.P[i] = fma(beta, a.P[i], a.Z[i]);
+}
+
+// ------------------------------------------------------------------ endpoint
+
+// f*_m = f^I(T*) + g (Algorithm 1) or f^I(T*) - f^I(T^k_m) (Algorithm 2), and
+// the endpoint T_{m,P} of every DOF off the contact, where f^E vanishes and
+// the P explicit substeps add up exactly to
+//   m T_{m,P} = m T_{m-1} + dtau f*_m + sum_j dt s_{m,j} F^I_j
+// (sum_p stil_{m,p,j} = s_{m,j}). Contact rows are overwritten by the
+// substep loop that follows.
+__global__ void k_bulk_endpoint(BulkArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double KX = ell_row(a.A, i, a.X);
+    double incr;
+    if (a.mode == RHS_PRED) {
+        incr = a.dtau * (a.g[i] - KX);
+    } else {
+        const double fstar = -KX - (a.FIm[i] - a.g[i]);
+        double I = 0.0;
+        for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
+        incr = fma(a.dtau, fstar, I);
+    }
+    a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
+}
+
+// ------------------------------------------------------------------ contact geometry
+
+__device__ __forceinline__ void motion_at(const ContactDev& C, double tau, double& du, double& dv, double& q) {
+    const double ph = 2.0 * 3.14159265358979323846 * tau / C.period;
+    const double s = __dadd_rn(C.z0, __dmul_rn(C.amp, sin(ph)));
+    du = C.dir_u * s;
+    dv = C.dir_v * s;
+    q = C.q0 * fabs(cos(ph));
+}
+
+__device__ __forceinline__ double corner_phi(int code, const Rect4& r, double pu, double pv) {
+    const double wu = r.z - r.x, wv = r.w - r.y;
+    const double fu = (code & 1) ? (pu - r.x) / wu : (r.z - pu) / wu;
+    const double fv = (code & 2) ? (pv - r.y) / wv : (r.w - pv) / wv;
+    return fu * fv;
+}
+
+__device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, int node, double c, bool& overflow) {
+    for (int k = 0; k < n; ++k)
+        if (idx[k] == node) {
+            coef[k] += c;
+            return;
+        }
+    if (n < MAXE) {
+        idx[n] = node;
+        coef[n] = c;
+        ++n;
+    } else {
+        overflow = true;
+    }
+}
+
+// Coupling operator of Sec. 2 at one substep time, row by row:
+//   f^E_a = sum over faces Q containing a, faces R of the other body
+//           overlapping Q, and the 2x2 Gauss points of the overlap of
+//           w phi^Q_a (h_c (T_R - T_Q) + q/2),
+// stored as a constant plus coefficients on contact DOFs.
+__global__ void k_iface_geom(GeomArgs g) {
+    const ContactDev& C = g.C;
+    const int NI = C.n_iface;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)NI * g.n_slots) return;
+    const int s = (int)(gid / NI), a = (int)(gid % NI);
+    double tau;
+    if (g.use_fixed) {
+        tau = g.t_fixed;
+    } else {
+        const double tn = __dadd_rn(g.st->t0, __dmul_rn((double)g.st->n_done, g.st->dt));
+        tau = __dadd_rn(tn, __dmul_rn(g.st->dt, g.slot_pos[s]));
+    }
+    double du, dv, q;
+    motion_at(C, tau, du, dv, q);
+    const bool stock = a >= C.n_iface_fix;
+    const double h_c = C.h_c;
+    const double gp = 0.57735026918962576451;  // 1/sqrt(3)
+
+    int32_t idx[MAXE];
+    double coef[MAXE];
+    int n = 0;
+    bool overflow = false;
+    double cst = 0.0;
+    const BinsDev& B = stock ? C.bins_fix : C.bins_mov;
+    for (int e = C.inc_ptr[a]; e < C.inc_ptr[a + 1]; ++e) {
+        const int Qf = C.inc_quad[e];
+        const int code = C.inc_code[e];
+        Rect4 Q = C.rect[Qf];
+        if (stock) {
+            Q.x += du; Q.z += du; Q.y += dv; Q.w += dv;
+        }
+        const int4 qn = C.qnode[Qf];
+        // query rectangle in the partner body's frame (stock partners are in reference position)
+        const double su = stock ? 0.0 : du, sv = stock ? 0.0 : dv;
+        const double lo_u = Q.x - su, lo_v = Q.y - sv, hi_u = Q.z - su, hi_v = Q.w - sv;
+        int iu0 = (int)floor((lo_u - B.bu - B.ou) / B.bu) - 1, iu1 = (int)floor((hi_u - B.ou) / B.bu) + 1;
+        int iv0 = (int)floor((lo_v - B.bv - B.ov) / B.bv) - 1, iv1 = (int)floor((hi_v - B.ov) / B.bv) + 1;
+        iu0 = max(iu0, 0); iv0 = max(iv0, 0);
+        iu1 = min(iu1, B.nu - 1); iv1 = min(iv1, B.nv - 1);
+        for (int iv = iv0; iv <= iv1; ++iv)
+            for (int iu = iu0; iu <= iu1; ++iu) {
+                const int bin = iv * B.nu + iu;
+                for (int t = B.ptr[bin]; t < B.ptr[bin + 1]; ++t) {
+                    const int Rf = B.item[t];
+                    Rect4 R = C.rect[Rf];
+                    if (!stock) {
+                        R.x += du; R.z += du; R.y += dv; R.w += dv;
+                    }
+                    const double ua = fmax(Q.x, R.x), ub = fmin(Q.z, R.z);
+                    const double va = fmax(Q.y, R.y), vb = fmin(Q.w, R.w);
+                    if (!(ub > ua && vb > va)) continue;
+                    const int4 rn = C.qnode[Rf];
+                    const double cu = 0.5 * (ua + ub), cv = 0.5 * (va + vb);
+                    const double hu = 0.5 * (ub - ua), hv = 0.5 * (vb - va);
+                    const double w = hu * hv;
+                    for (int gq = 0; gq < 4; ++gq) {
+                        const double pu = cu + ((gq & 1) ? gp : -gp) * hu;
+                        const double pv = cv + ((gq & 2) ? gp : -gp) * hv;
+                        const double pq[4] = {corner_phi(0, Q, pu, pv), corner_phi(1, Q, pu, pv),
+                                              corner_phi(2, Q, pu, pv), corner_phi(3, Q, pu, pv)};
+                        const double pr[4] = {corner_phi(0, R, pu, pv), corner_phi(1, R, pu, pv),
+                                              corner_phi(2, R, pu, pv), corner_phi(3, R, pu, pv)};
+                        const double wa = w * pq[code];
+                        cst += wa * 0.5 * q;
+                        const double wh = wa * h_c;
+                        add_entry(idx, coef, n, qn.x, -wh * pq[0], overflow);
+                        add_entry(idx, coef, n, qn.y, -wh * pq[1], overflow);
+                        add_entry(idx, coef, n, qn.z, -wh * pq[2], overflow);
+                        add_entry(idx, coef, n, qn.w, -wh * pq[3], overflow);
+                        add_entry(idx, coef, n, rn.x, wh * pr[0], overflow);
+                        add_entry(idx, coef, n, rn.y, wh * pr[1], overflow);
+                        add_entry(idx, coef, n, rn.z, wh * pr[2], overflow);
+                        add_entry(idx, coef, n, rn.w, wh * pr[3], overflow);
+                    }
+                }
+            }
+    }
+    if (overflow) atomicExch(g.status, (int)SDC_ERR_ARG);
+    const size_t so = (size_t)s * NI + a;
+    g.E.cnt[so] = n;
+    g.E.cst[so] = cst;
+    for (int k = 0; k < n; ++k) {
+        const size_t o = ((size_t)s * MAXE + k) * NI + a;
+        g.E.idx[o] = idx[k];
+        g.E.coef[o] = coef[k];
+    }
+}
+
+__device__ __forceinline__ double apply_coupling(const CouplingOp& E, int slot, int NI, int a, const double* T) {
+    const size_t so = (size_t)slot * NI + a;
+    const int n = E.cnt[so];
+    double acc = E.cst[so];
+    for (int k = 0; k < n; ++k) {
+        const size_t o = ((size_t)slot * MAXE + k) * NI + a;
+        acc = fma(__ldg(E.coef + o), __ldcg(T + __ldg(E.idx + o)), acc);
+    }
+    return acc;
+}
+
+// f^E(T, tau) on all DOFs for one precomputed slot (zero elsewhere is set by the caller).
+__global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* __restrict__ T,
+                                double* __restrict__ Ti, double* __restrict__ out, int phase) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= C.n_iface) return;
+    if (phase == 0) {
+        Ti[a] = T[C.dof[a]];
+    } else {
+        out[C.dof[a]] = apply_coupling(E, slot, C.n_iface, a, Ti);
+    }
+}
+
+// ------------------------------------------------------------------ substep loop
+
+// The P explicit substeps of one interval on the contact DOFs, on one
+// cluster of IFACE_CLUSTER CTAs (Algorithm 1 / Algorithm 2 inner loops):
+//   predictor: m T_{m,p} = m T_{m,p-1} + dt_p (f*_m + f^E(T_{m,p-1}, tau_{m,p-1}))
+//   sweep:     m T_{m,p} = m T_{m,p-1} + dt_p f*_m
+//                          + dt_p (f^E(T^{k+1}_{m,p-1}) - f^E(T^k_{m,p-1})) + I_{m,p-1}^p
+// with I_{m,p-1}^p = sum_j dt stil_{m,p,j} F^I_j + sum_q dt s_{m,p,q} f^E(T^k_{m,q}).
+// Every f^E of the current iterate is stored for the next sweep, together
+// with ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m).
+__global__ void __cluster_dims__(IFACE_CLUSTER, 1, 1) __launch_bounds__(IFACE_THREADS)
+    k_iface_loop(IfaceArgs a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const ContactDev& C = a.C;
+    const int NI = C.n_iface;
+    const int stride = IFACE_CLUSTER * IFACE_THREADS;
+    const int tid0 = (int)(cluster.block_rank() * IFACE_THREADS + threadIdx.x);
+    const int P = a.P;
+    const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+
+    // load T_{m,0} = T_{m-1} and f*_m on the contact DOFs
+    for (int i = tid0; i < NI; i += stride) {
+        const int row = C.dof[i];
+        a.Ta[i] = a.Tprev[row];
+        const double KX = ell_row(a.A, row, a.X);
+        a.fstar[i] = (a.mode == RHS_PRED) ? (a.g[row] - KX) : (-KX - (a.FIm[row] - a.g[row]));
+    }
+    cluster.sync();
+    // f^E at tau_{m,0}
+    for (int i = tid0; i < NI; i += stride) {
+        double f0;
+        if (a.first) {
+            f0 = (a.mode == RHS_PRED) ? apply_coupling(a.E, a.slot0, NI, i, a.Ta) : a.fe_old[i];
+        } else {
+            f0 = a.fe_prev_end[i];
+        }
+        a.fe_new[i] = f0;
+    }
+    double* Tc = a.Ta;
+    double* Tn = a.Tb;
+    for (int p = 1; p <= P; ++p) {
+        const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
+        for (int i = tid0; i < NI; i += stride) {
+            const double fe_cur = a.fe_new[(size_t)(p - 1) * NI + i];
+            double incr;
+            if (a.mode == RHS_PRED) {
+                incr = dtp * (a.fstar[i] + fe_cur);
+            } else {
+                const int row = C.dof[i];
+                double I = 0.0;
+                for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
+                for (int q = 1; q <= P; ++q) {
+                    const double wq = a.Semb[(size_t)(p - 1) * P + (q - 1)];
+                    if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)q * NI + i], I);
+                }
+                incr = dtp * a.fstar[i] + dtp * (fe_cur - a.fe_old[(size_t)(p - 1) * NI + i]) + I;
+            }
+            Tn[i] = Tc[i] + incr / C.mass[i];
+        }
+        cluster.sync();
+        for (int i = tid0; i < NI; i += stride)
+            a.fe_new[(size_t)p * NI + i] = apply_coupling(a.E, a.slot0 + p, NI, i, Tn);
+        double* t = Tc;
+        Tc = Tn;
+        Tn = t;
+    }
+    for (int i = tid0; i < NI; i += stride) {
+        a.Tout[C.dof[i]] = Tc[i];
+        double ih = 0.0;
+        for (int q = 1; q <= P; ++q) ih = fma(a.Shat[q - 1], a.fe_new[(size_t)q * NI + i], ih);
+        a.ihat_new[i] = ih;
+    }
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+// r^k = max_m || m T_m - m T_n - sum_{j<=m} I_{j-1}^j ||_inf (Eq. residual)
+__global__ void k_residual(ResidualArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (i < a.n) {
+        const double m = a.mass[i];
+        const double tn = a.Tn[i];
+        const int pa = a.pos[i];
+        double cum = 0.0, r = 0.0;
+        for (int mm = 0; mm < a.M; ++mm) {
+            double I = 0.0;
+            for (int j = 0; j < a.M; ++j) I = fma(a.Sdt[mm][j], a.FI[j][i], I);
+            if (pa >= 0 && a.ihat[mm]) I += a.ihat[mm][pa];
+            cum += I;
+            r = fmax(r, fabs(m * a.Tm[mm][i] - m * tn - cum));
+        }
+        v[0] = r;
+    }
+    double out[1];
+    if (reduce_last<1, true>(v, a.partials, a.counter, out) && threadIdx.x == 0) *a.out = out[0];
+}
+
+// heat[0] = sum over stand rows of m T, heat[1] = stock rows
+__global__ void k_heat(const double* __restrict__ mass, const double* __restrict__ T, int64_t n, int64_t n_fix,
+                       double* partials, unsigned int* counter, double* heat) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (i < n) {
+        const double h = mass[i] * T[i];
+        if (i < n_fix) v[0] = h; else v[1] = h;
+    }
+    double out[2];
+    if (reduce_last<2, false>(v, partials, counter, out) && threadIdx.x == 0) {
+        heat[0] = out[0];
+        heat[1] = out[1];
+    }
+}
+
+// friction energy of the step: sum over intervals and contact DOFs of ihat
+// (exchange terms cancel between the bodies); then advance the step counter.
+__global__ void k_step_end(StepState* st, const double* ihat, int n_int, int NI) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int m = 0; m < n_int; ++m)
+        for (int i = threadIdx.x; i < NI; i += blockDim.x) acc += ihat[(size_t)m * NI + i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        st->friction_in += t;
+        st->n_done += 1;
+    }
+}
+
+}  // namespace sdc

@@ -1,0 +1,146 @@
+// Kernel argument blocks and launch entry points (device side of the stepper).
+#pragma once
+
+#include "common.h"
+
+namespace sdc {
+
+constexpr int MAXE = 32;            // coupling entries per contact DOF and substep time
+constexpr int IFACE_CLUSTER = 8;    // CTAs of the substep-loop cluster
+constexpr int IFACE_THREADS = 512;  // threads per CTA of that cluster
+
+enum RhsMode { RHS_GIVEN = 0, RHS_PRED = 1, RHS_SWEEP = 2 };
+
+// One Jacobi-PCG solve of (diag(m) + dtau K) x = b.
+struct CgArgs {
+    EllDev A;
+    const double* mass;
+    const double* diagK;
+    double dtau;
+    int64_t n;
+    double *X, *R, *Z, *P, *Y, *D;   // iterate, residual, preconditioned residual, direction, A p, 1/diag
+    CgState* cg;
+    double* partials;
+    unsigned int* counter;
+    int* iters_out;                 // iteration count of this solve
+    int* status;                    // sticky status word
+    int max_iter;
+    double rtol2;
+    unsigned long long handle;      // cudaGraphConditionalHandle of the enclosing while node
+};
+
+// Right-hand side of the implicit stage.
+struct RhsArgs {
+    int mode;
+    const double* b_in;             // RHS_GIVEN
+    const double* Tprev;            // T_{m-1} of the current iterate
+    const double* g;                // b_env
+    const double* FIm;              // F^I(T^k_m) (sweep)
+    const double* FI[MAX_M];        // F^I(T^k_j), j = 1..M (sweep)
+    double Sdt[MAX_M];              // dt s_{m,j}
+    int nFI;
+    const double* ihat;             // sum_q dt shat_{m,q} f^E(T^k_{m,q}) on contact DOFs (sweep)
+    const int32_t* pos;             // DOF -> contact index or -1
+    const double* x0;               // initial guess
+};
+
+// Bulk endpoint update after the solve (see k_bulk_endpoint).
+struct BulkArgs {
+    EllDev A;
+    const double* minv;
+    const double* g;
+    const double* X;                // T*
+    const double* Tprev;
+    double* Tout;
+    const double* FIm;
+    const double* FI[MAX_M];
+    double Sdt[MAX_M];
+    int nFI;
+    double dtau;
+    int mode;
+    int64_t n;
+};
+
+// Precomputed coupling operator f^E(T, tau_s)_a = cst[s][a] + sum_k coef[s][k][a] T_I[idx[s][k][a]].
+struct CouplingOp {
+    int32_t* cnt;     // [slots][NI]
+    int32_t* idx;     // [slots][MAXE][NI]
+    double* coef;     // [slots][MAXE][NI]
+    double* cst;      // [slots][NI]
+};
+
+struct GeomArgs {
+    ContactDev C;
+    CouplingOp E;
+    const double* slot_pos;   // unit-step position of each slot (tau = t_n + dt pos)
+    const StepState* st;      // t_n = st->t0 + st->n_done * dt
+    double t_fixed;           // used instead of t_n + dt pos when use_fixed
+    int use_fixed;
+    int n_slots;
+    int* status;
+};
+
+// Substep loop of one interval (Algorithm 1 or 2, interface DOFs only).
+struct IfaceArgs {
+    ContactDev C;
+    EllDev A;
+    const double* g;
+    int mode;                       // RHS_PRED or RHS_SWEEP
+    int first;                      // first non-degenerate interval of the step
+    int P;
+    double dt;
+    const StepState* st;
+    const double* emb;              // P+1 unit-step positions of this interval's embedded nodes
+    const double* Tprev;
+    double* Tout;
+    const double* X;                // T*
+    const double* FIm;
+    const double* FI[MAX_M];
+    int nFI;
+    const double* Stil;             // [P][nFI] dt stil_{m,p,j}
+    const double* Semb;             // [P][P]  dt s_{m,p,q}
+    const double* Shat;             // [P]     dt shat_{m,q}
+    CouplingOp E;                   // slots of this interval start at slot0
+    int slot0;
+    const double* fe_old;           // [(P+1)][NI] previous iterate (sweep)
+    double* fe_new;                 // [(P+1)][NI]
+    const double* fe_prev_end;      // [NI] this iterate's f^E at the end of the previous interval
+    double* ihat_new;               // [NI]
+    double* Ta;                     // work [NI]
+    double* Tb;                     // work [NI]
+    double* fstar;                  // work [NI]
+};
+
+struct ResidualArgs {
+    const double* mass;
+    const double* Tn;
+    const double* Tm[MAX_M];        // T^k_m, m = 1..M
+    const double* FI[MAX_M];
+    double Sdt[MAX_M][MAX_M];
+    const double* ihat[MAX_M];      // per interval, NI values (NULL for a zero-length interval)
+    const int32_t* pos;
+    int M;
+    int64_t n;
+    double* partials;
+    unsigned int* counter;
+    double* out;
+};
+
+// kernels (defined in kernels.cu)
+__global__ void k_apply_operator(EllDev A, const double* mass, double dtau, const double* x, double* y);
+__global__ void k_fi(EllDev A, const double* g, const double* T, double* F);
+__global__ void k_cg_init(CgArgs a, RhsArgs r);
+__global__ void k_cg_spmv(CgArgs a);
+__global__ void k_cg_update(CgArgs a);
+__global__ void k_cg_pupdate(CgArgs a);
+__global__ void k_bulk_endpoint(BulkArgs a);
+__global__ void k_iface_geom(GeomArgs g);
+__global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,
+                                int phase);
+__global__ void k_iface_loop(IfaceArgs a);
+__global__ void k_residual(ResidualArgs a);
+__global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,
+                       unsigned int* counter, double* heat);
+__global__ void k_step_end(StepState* st, const double* ihat, int n_int, int NI);
+
+}  // namespace sdc

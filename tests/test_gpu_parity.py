@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 path rel-L2 <= 1e-10 per macro step on the temperature
+(the stated bar), plus the stricter rel-L2 of the rise T - T0 <= 1e-8, since
+the 20 degC offset makes the first metric lenient. Component checks use
+1e-12..1e-13 (rounding-order differences of FP64 sums only).
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import contact as ct
+from oracle.machine import MachineProblem
+from oracle.mrsdc import mrsdc_step
+from oracle.weights import mrsdc_weights
+from synth import machine_config, tiny_machine
+from synth.machines import with_scheme
+
+pytestmark = pytest.mark.gpu
+
+REL_T = 1e-10
+REL_RISE = 1e-8
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def _solver(mach, **kw):
+    from paper_1707_03581_gb300 import Solver
+
+    s = Solver(0)
+    s.set_machine(mach, **kw)
+    return s
+
+
+def _compare(got, ref, T0, tag):
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    d = np.linalg.norm(ref - T0)
+    rise = np.linalg.norm(got - ref) / d if d > 0 else np.linalg.norm(got - ref)
+    assert rel <= REL_T, (tag, rel)
+    assert rise <= REL_RISE, (tag, rise)
+    return rel, rise
+
+
+def test_assembled_system_matches_oracle(torch):
+    mach = machine_config(0)
+    s = _solver(mach)
+    prob = MachineProblem(mach)
+    rp, col, val, mass, genv = s.system()
+    K = sp.csr_matrix((val, col, rp), shape=(s.n, s.n))
+    diff = abs(K - prob.K)
+    assert diff.max() <= 1e-13 * abs(prob.K).max()
+    np.testing.assert_allclose(mass, prob.mass, rtol=1e-14)
+    np.testing.assert_allclose(genv, prob.genv, rtol=1e-13, atol=1e-13 * abs(prob.genv).max())
+    assert s.n_stand == mach.stand.mesh.n_nodes and s.nnz == prob.K.nnz
+
+
+def test_operator_solve_and_contact_components(torch):
+    mach = machine_config(0)
+    s = _solver(mach)
+    prob = MachineProblem(mach)
+    rng = np.random.default_rng(11)
+    x = 20.0 + rng.standard_normal(s.n)
+    for dtau in (0.0, 0.5, 0.123):
+        y = s.apply_operator(dtau, x).cpu().numpy()
+        ref = prob.mass * x + dtau * (prob.K @ x)
+        assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+    b = prob.mass * (20.0 + rng.standard_normal(s.n))
+    xs, it = s.solve(0.5, b, np.full(s.n, 20.0))
+    A = (sp.diags(prob.mass) + 0.5 * prob.K).toarray()
+    xd = np.linalg.solve(A, b)
+    assert it > 0
+    assert np.abs(xs.cpu().numpy() - xd).max() <= 1e-10 * np.abs(xd).max()
+    T = 20.0 + rng.standard_normal(s.n)
+    for t in (0.0, 0.37, 1.0, 1.5, 7.31):
+        fe = s.contact_flux(T, t).cpu().numpy()
+        ref = prob.fE(T, t)
+        assert np.abs(fe - ref).max() <= 1e-12 * np.abs(ref).max(), t
+
+
+def _run_parity(mach, n_steps, residuals=False, T0=None):
+    s = _solver(mach, residuals=residuals, T0=T0)
+    prob = MachineProblem(mach)
+    sc = mach.scheme
+    W = mrsdc_weights(sc.nodes, sc.M, sc.P, sc.window)
+    T = np.full(prob.n, mach.T0) if T0 is None else np.array(T0, dtype=np.float64)
+    start = T.copy()
+    worst = (0.0, 0.0)
+    for n in range(n_steps):
+        rep = s.step(report=True)
+        T, r = mrsdc_step(prob, T, mach.t0 + n * sc.dt, sc.dt, W, sc.sweeps, want_residuals=residuals)
+        got = s.temperature()
+        rel, rise = _compare(got, T, start, f"step {n}")
+        worst = (max(worst[0], rel), max(worst[1], rise))
+        assert rep["status"] == 0
+        if residuals:
+            scale = max(r.residuals[0], 1e-300)
+            np.testing.assert_allclose(rep["residual"], r.residuals, rtol=1e-6, atol=1e-9 * scale)
+        h = s.heat_totals()
+        hs, hk = prob.heat(got)
+        assert abs(h["stored_stand"] - hs) <= 1e-12 * abs(hs)
+        assert abs(h["stored_stock"] - hk) <= 1e-12 * abs(hk)
+    s.close()
+    return worst
+
+
+def test_config0_full_horizon_lobatto(torch):
+    # 8x8x20 + 4x4x6, Lobatto M=3, 3 sweeps, P=20, dt = 1 s, 60 macro steps
+    mach = machine_config(0)
+    _run_parity(mach, 60)
+
+
+@pytest.mark.parametrize("nodes,M,P,K,window", [("radau_right", 4, 8, 4, 0), ("equi_noleft", 3, 2, 2, 2),
+                                                 ("equi_noleft", 5, 8, 3, 8), ("lobatto", 2, 1, 1, 0),
+                                                 ("radau_right", 1, 5, 0, 0), ("lobatto", 4, 40, 2, 0)])
+def test_schemes_on_tiny_machine_with_residuals(torch, nodes, M, P, K, window):
+    mach = with_scheme(tiny_machine(z0=0.37, amp=0.21, period=1.7), nodes=nodes, M=M, P=P, sweeps=K,
+                       window=window, dt=0.8)
+    rng = np.random.default_rng(5)
+    T0 = 20.0 + rng.standard_normal(mach.n_dof)
+    _run_parity(mach, 4, residuals=True, T0=T0)
+
+
+def test_resting_stock_and_insulated_conservation(torch):
+    mach = tiny_machine(z0=0.37, amp=0.25, period=np.inf, q0=0.0)
+    mach.stand.h = 0.0
+    mach.stock.h = 0.0
+    rng = np.random.default_rng(9)
+    T0 = 20.0 + 3.0 * rng.standard_normal(mach.n_dof)
+    s = _solver(mach, T0=T0)
+    h0 = s.heat_totals()
+    Q0 = h0["stored_stand"] + h0["stored_stock"]
+    for _ in range(5):
+        s.step(report=True)
+    h1 = s.heat_totals()
+    Q1 = h1["stored_stand"] + h1["stored_stock"]
+    assert abs(Q1 - Q0) <= 1e-12 * abs(Q0)
+    assert abs(h1["friction_in"]) <= 1e-12
+
+
+def test_friction_energy_ledger(torch):
+    # resting stock, constant flux: friction energy per step = q0 * area * dt
+    mach = tiny_machine(z0=0.37, amp=0.25, period=np.inf, q0=2.0e4)
+    s = _solver(mach)
+    for _ in range(3):
+        s.step(report=True)
+    h = s.heat_totals()
+    assert abs(h["friction_in"] - 3 * 2.0e4 * 0.06 * 1.0) <= 1e-9 * 3 * 2.0e4 * 0.06
+
+
+def test_deterministic_and_horizon_equals_steps(torch):
+    mach = machine_config(0)
+    a = _solver(mach)
+    for _ in range(4):
+        a.step(report=False)
+    a.synchronize()
+    Ta = a.temperature()
+    b = _solver(mach)
+    rep = b.run_horizon(4)
+    Tb = b.temperature()
+    assert np.array_equal(Ta, Tb)
+    assert abs(rep["t"] - 4.0) < 1e-12
+
+
+def test_config1_two_macro_steps(torch):
+    # 48x48x120 + 24x24x36 (313,646 DOF), seeded stroke: the benchmark workload
+    mach = machine_config(1)
+    _run_parity(mach, 2)
+
+
+def test_errors_are_reported_not_fatal(torch):
+    from paper_1707_03581_gb300 import Solver
+    from paper_1707_03581_gb300.binding import SdcError
+
+    s = Solver(0)
+    with pytest.raises(SdcError) as e:
+        s.step()
+    assert "SDC_ERR_STATE" in str(e.value)
+    mach = machine_config(0)
+    bad = mach.stand.mesh.hex8.copy()
+    bad[0, 0] = 10 ** 9
+    s.set_body(0, mach.stand.mesh.xyz, bad, 50.0, 7850.0, 460.0)
+    s.set_body(1, mach.stock.mesh.xyz, mach.stock.mesh.hex8, 50.0, 7850.0, 460.0)
+    s.set_contact(mach.stand_contact, mach.stock_contact, 2000.0, 5e4)
+    s.set_motion((0, 0, 1), 0.35, 0.25, 2.0)
+    with pytest.raises(SdcError) as e:
+        s.assemble()
+    assert "SDC_ERR_ARG" in str(e.value)
+    # a cap of one CG iteration cannot reach 1e-12: the step reports it
+    s2 = _solver(with_scheme(machine_config(0), cg_max_iter=1))
+    rng = np.random.default_rng(0)
+    s2.set_temperature(20.0 + rng.standard_normal(s2.n))
+    with pytest.raises(SdcError) as e:
+        s2.step(report=True)
+    assert "NOT_CONVERGED" in str(e.value)
+    # the context stays usable
+    s2.set_scheme("lobatto", 3, 20, 3, 0, 1.0, 1e-12, 2000)
+    s2.set_temperature(None, 20.0, 0.0)
+    s2.step(report=True)
