@@ -19,7 +19,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <stdexcept>
+#include <utility>
 #include <vector>
 
 #include "common.h"
@@ -124,10 +127,22 @@ std::vector<ld> standard_nodes_ld(int kind, int M) {
 
 // int_a^b prod_{i != j} (s - x_i) / (x_j - x_i) ds, exactly for the degree.
 static ld lagrange_integral(const std::vector<ld>& x, int j, ld a, ld b) {
-    int deg = (int)x.size() - 1;
-    int ng = deg / 2 + 1;
+    static std::mutex mu;
+    static std::map<int, std::pair<std::vector<ld>, std::vector<ld>>> rules;
+    const int deg = (int)x.size() - 1;
+    const int ng = std::max(deg / 2 + 1, 1);
     std::vector<ld> gx, gw;
-    gauss_legendre(std::max(ng, 1), gx, gw);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = rules.find(ng);
+        if (it == rules.end()) {
+            gauss_legendre(ng, gx, gw);
+            rules[ng] = {gx, gw};
+        } else {
+            gx = it->second.first;
+            gw = it->second.second;
+        }
+    }
     ld half = 0.5L * (b - a), mid = 0.5L * (a + b), acc = 0.0L;
     for (size_t g = 0; g < gx.size(); ++g) {
         ld s = mid + half * gx[g];
