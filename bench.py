@@ -1,0 +1,299 @@
+"""Benchmark: IMEX multi-rate SDC macro steps of the coupled stand/stock heat problem.
+
+Workload (default): the 48x48x120 stand + 24x24x36 stock machine (313,646
+DOF, seeded stroke), Lobatto M=3, 3 sweeps, P=20 embedded substeps, dt = 1 s,
+CG to rel 1e-12. One "step" = one macro step (Algorithm 1 + 3 x Algorithm 2).
+
+  value  = DOF x substeps per second (N_dof x M' x P per macro step)
+  eta    = simulated seconds per wall second (look-ahead factor)
+
+Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
+on the solver's stream, with L2 flushed (256 MiB write) between steps
+outside the timed intervals; barrier + synchronize around the region; the
+maximum over ranks. `e2e` repeats the run through the public API with the
+state coming from and going back to pinned host memory every step.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "look-ahead η & DOF·substeps/s, mixed vs FP64 at rel-L2≤1e-6; p99 latency"
+UNIT = "DOF·substeps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(config_idx):
+    from synth import machine_config
+
+    m = machine_config(config_idx)
+    s = m.scheme
+    n_int = s.M - 1 if s.nodes == "lobatto" else s.M
+    desc = (f"{m.name}: {m.stand.mesh.n[0]}x{m.stand.mesh.n[1]}x{m.stand.mesh.n[2]} stand + "
+            f"{m.stock.mesh.n[0]}x{m.stock.mesh.n[1]}x{m.stock.mesh.n[2]} stock ({m.n_dof} DOF), "
+            f"{s.nodes} M={s.M}, {s.sweeps} sweeps, P={s.P}, dt={s.dt} s, CG rtol {s.cg_rtol:g}")
+    return m, n_int, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_baseline(config_idx, steps):
+    """Time the CPU oracle (single-threaded numpy/scipy) in a fresh process."""
+    code = (
+        "import os, sys, time, json, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from synth import machine_config\n"
+        "from oracle.machine import MachineProblem\n"
+        "from oracle.mrsdc import mrsdc_step\n"
+        "from oracle.weights import mrsdc_weights\n"
+        f"m = machine_config({config_idx}); s = m.scheme\n"
+        "prob = MachineProblem(m)\n"
+        "W = mrsdc_weights(s.nodes, s.M, s.P, s.window)\n"
+        "T = np.full(prob.n, m.T0)\n"
+        "t = time.perf_counter()\n"
+        f"for n in range({steps}):\n"
+        "    T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)\n"
+        "el = time.perf_counter() - t\n"
+        "print(json.dumps({'seconds': el, 'n': prob.n}))\n"
+    )
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank, world):
+    m, n_int, desc = _workload(args.config)
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 3))
+    res = _oracle_baseline(args.config, steps)
+    units = res["n"] * n_int * m.scheme.P * steps
+    value = units / res["seconds"]
+    ms = res["seconds"] / steps * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": "fp64", "l2": "n/a (CPU)"},
+            "eta": steps * m.scheme.dt / res["seconds"],
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {steps} macro steps of the workload, single-threaded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1707_03581_gb300 import Solver
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    m, n_int, desc = _workload(args.config)
+    s = Solver(local)
+    s.set_machine(m, precision=args.precision)
+    P = m.scheme.P
+    units_per_step = s.n * n_int * P
+    stream = s.stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            s.step(report=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        launches, cg_iters = 0, 0
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+                s.step(report=False)
+                ends[k].record(stream)
+                s.synchronize()
+            torch.cuda.synchronize()
+        ms_steps = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        total_ms = float(sum(ms_steps))
+    # launches and CG work of one step, from a reported step after the timed region
+    rep = s.step(report=True)
+    launches = rep["kernel_launches"] * args.steps
+    cg_iters = rep["cg_iters_total"]
+
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+
+    # end-to-end through the public API: host state in, host state out, every step
+    pin_in = torch.empty(s.n, dtype=torch.float64).pin_memory()
+    pin_out = torch.empty(s.n, dtype=torch.float64).pin_memory()
+    pin_in.copy_(torch.from_numpy(s.temperature()))
+    t_sim = m.t0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s.set_temperature(pin_in.numpy(), t0=t_sim)
+        s.step(report=False)
+        s.temperature(out=pin_out)
+        t_sim += m.scheme.dt
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # dominant kernel (CG SpMV + dot), timed live on the solver's stream
+    dtau = m.scheme.dt * (0.5 if m.scheme.nodes == "lobatto" else 1.0 / m.scheme.M)
+    kt = s.time_cg_kernels(dtau, reps=50)
+    peak, peak_kind = _peaks()
+    spmv_bytes = 12 * s.nnz + 24 * s.n
+    achieved = spmv_bytes / (kt["spmv"] * 1e-3) / 1e9
+
+    if rank != 0:
+        return
+    value = units_per_step * args.steps * world / (t_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "eta": args.steps * m.scheme.dt / (t_max * 1e-3),
+        "cg_iters_per_step": cg_iters,
+        "e2e": {"value": units_per_step * args.steps * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * s.n, "d2h_bytes_per_step": 8 * s.n,
+                "eta": args.steps * m.scheme.dt / e2e_s},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_cg_spmv (FP64 sliced-ELL SpMV + <p, y>)",
+                     "algorithmic_bytes": spmv_bytes, "ms_per_launch": kt["spmv"],
+                     "peak_kind": peak_kind},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            res = _oracle_baseline(args.config, 1)
+            v = res["n"] * n_int * P / res["seconds"]
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "one macro step of the same workload, single-threaded numpy/scipy"}
+        except Exception as e:  # reported, not fatal
+            line["cpu_baseline"] = {"error": str(e)[:200]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

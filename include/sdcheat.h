@@ -71,6 +71,7 @@ typedef struct {
     int32_t cg_iters_max;                   /* largest iteration count of one solve           */
     int32_t refinements_total;              /* outer refinement passes (MIXED only)           */
     int32_t status;                         /* sdc_status of the device-side checks           */
+    int32_t kernel_launches;                /* CUDA kernels the step executed                 */
     double residual[SDC_MAX_SWEEPS + 1];    /* r^k, k = 0..K (Eq. residual), if enabled; else -1 */
     double heat_stand;                      /* sum_i m_i T_i over stand DOFs [J]              */
     double heat_stock;                      /* sum_i m_i T_i over stock DOFs [J]              */
@@ -213,6 +214,13 @@ sdc_status sdc_solve(sdc_ctx* ctx, double dtau, const double* b_dev, double* x_d
 /* f^E(T, t) on all DOFs (zero away from the contact): Sec. 2, the contact
  * and friction terms of Eq. femContFix / femContMov. */
 sdc_status sdc_contact_flux(sdc_ctx* ctx, const double* T_dev, double t, double* fE_dev);
+
+/* Measurement aid: run the three kernels of one FP64 CG iteration
+ * (SpMV + dot, update + dots, direction update) `reps` times each, outside
+ * any graph, on the context's stream, on the work vectors of the last solve,
+ * and return their average device times in ms_out[0..2] (CUDA events).
+ * The values of the work vectors are overwritten. Waits. */
+sdc_status sdc_time_cg_kernels(sdc_ctx* ctx, double dtau, int reps, float* ms_out);
 
 #ifdef __cplusplus
 }

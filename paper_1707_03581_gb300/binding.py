@@ -32,7 +32,7 @@ _vp = C.c_void_p
 class StepReport(C.Structure):
     _fields_ = [("t", C.c_double), ("sweeps", C.c_int32), ("n_solves", C.c_int32),
                 ("cg_iters_total", C.c_int32), ("cg_iters_max", C.c_int32),
-                ("refinements_total", C.c_int32), ("status", C.c_int32),
+                ("refinements_total", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int32),
                 ("residual", C.c_double * (MAX_SWEEPS + 1)),
                 ("heat_stand", C.c_double), ("heat_stock", C.c_double)]
 
@@ -40,6 +40,7 @@ class StepReport(C.Structure):
         return {"t": self.t, "sweeps": self.sweeps, "n_solves": self.n_solves,
                 "cg_iters_total": self.cg_iters_total, "cg_iters_max": self.cg_iters_max,
                 "refinements_total": self.refinements_total, "status": self.status,
+                "kernel_launches": self.kernel_launches,
                 "residual": [r for r in self.residual[: self.sweeps + 1]],
                 "heat_stand": self.heat_stand, "heat_stock": self.heat_stock}
 
@@ -78,6 +79,7 @@ _SIGS = {
     "sdc_apply_operator": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
+    "sdc_time_cg_kernels": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_float)]),
 }
 
 _LIB = None
@@ -306,6 +308,12 @@ class Solver:
         it = C.c_int32()
         self._call("sdc_solve", dtau, _vp(b.data_ptr()), _vp(x.data_ptr()), C.byref(it))
         return x, it.value
+
+    def time_cg_kernels(self, dtau, reps=20):
+        """Average device ms of the CG SpMV, update and direction kernels (see sdc_time_cg_kernels)."""
+        out = (C.c_float * 3)()
+        self._call("sdc_time_cg_kernels", dtau, int(reps), out)
+        return {"spmv": out[0], "update": out[1], "pupdate": out[2]}
 
     def contact_flux(self, T, t):
         T = self._dev(T)

@@ -78,6 +78,7 @@ struct sdc_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_ready = false;
+    int fixed_kernels = 0;          // kernel nodes of the step graph outside the CG loops
 };
 
 namespace {
@@ -135,6 +136,7 @@ unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 struct Chain {
     cudaGraph_t g;
     cudaGraphNode_t last = nullptr;
+    int kernels = 0;
     explicit Chain(cudaGraph_t gg) : g(gg) {}
 
     template <typename... KArgs>
@@ -149,6 +151,7 @@ struct Chain {
         cudaGraphNode_t nd;
         SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
         last = nd;
+        ++kernels;
     }
     void copy(void* dst, const void* src, size_t bytes) {
         cudaGraphNode_t nd;
@@ -567,6 +570,7 @@ void build_step_graph(sdc_ctx* c) {
               (int64_t)c->n_fix, c->partials, c->counter, &c->st->heat[0]);
     ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], n_int, NI);
     SDC_CUDA_TRY(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->fixed_kernels = ch.kernels;
     c->graph_ready = true;
 }
 
@@ -606,6 +610,7 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
         rep->refinements_total += s.refinements[i];
     }
     rep->status = s.status;
+    rep->kernel_launches = c->fixed_kernels + 3 * rep->cg_iters_total;
     for (int k = 0; k <= SDC_MAX_SWEEPS; ++k) rep->residual[k] = (c->residuals && k <= c->K_sweeps) ? s.residual[k] : -1.0;
     rep->heat_stand = s.heat[0];
     rep->heat_stock = s.heat[1];
@@ -974,6 +979,37 @@ sdc_status sdc_contact_flux(sdc_ctx* c, const double* T, double t, double* fE) {
         k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 1);
         SDC_CUDA_TRY(cudaGetLastError());
         read_state(c, nullptr);
+    });
+}
+
+sdc_status sdc_time_cg_kernels(sdc_ctx* c, double dtau, int reps, float* ms_out) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(reps >= 1 && ms_out, SDC_ERR_ARG, "reps >= 1 and ms_out required");
+        CgArgs a = cg_args(c, dtau, 0, c->rtol, c->max_iter);
+        a.handle = 0;
+        const unsigned nb = blocks_for(c->n, RED_BLOCK);
+        cudaEvent_t ev[2];
+        SDC_CUDA_TRY(cudaEventCreate(&ev[0]));
+        SDC_CUDA_TRY(cudaEventCreate(&ev[1]));
+        for (int kind = 0; kind < 3; ++kind) {
+            SDC_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
+            for (int r = 0; r < reps; ++r) {
+                if (kind == 0) k_cg_spmv<<<nb, RED_BLOCK, 0, c->stream>>>(a);
+                else if (kind == 1) k_cg_update<<<nb, RED_BLOCK, 0, c->stream>>>(a);
+                else k_cg_pupdate<<<nb, RED_BLOCK, 0, c->stream>>>(a);
+            }
+            SDC_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
+            SDC_CUDA_TRY(cudaEventSynchronize(ev[1]));
+            float ms = 0;
+            SDC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            ms_out[kind] = ms / reps;
+        }
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        SDC_CUDA_TRY(cudaGetLastError());
+        SDC_CUDA_TRY(cudaMemsetAsync(&c->st->status, 0, sizeof(int), c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
     });
 }
 
