@@ -167,6 +167,8 @@ def run_gpu(args, rank, world):
     m, n_int, desc = _workload(args.config)
     s = Solver(local)
     s.set_machine(m, precision=args.precision)
+    if args.eager:
+        s.set_execution(True)
     P = m.scheme.P
     units_per_step = s.n * n_int * P
     stream = s.stream
@@ -249,6 +251,7 @@ def run_gpu(args, rank, world):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_cg_spmv (FP64 sliced-ELL SpMV + <p, y>)",
                      "algorithmic_bytes": spmv_bytes, "ms_per_launch": kt["spmv"],
+                     "ms_cg_update": kt["update"], "ms_cg_pupdate": kt["pupdate"],
                      "peak_kind": peak_kind},
         "clocks": clk.summary(),
     }
@@ -272,6 +275,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="plain kernel launches with host-driven CG loops (for kernel-level profilers)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -158,6 +158,13 @@ sdc_status sdc_set_scheme(sdc_ctx* ctx, sdc_nodes nodes, int M, int P, int sweep
  * the predictor and every sweep (costs extra passes). */
 sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
 
+/* Execution mode. 0 (default): each macro step is one CUDA graph launch with
+ * device-side CG loops. 1: the same kernels as plain launches, each CG loop
+ * driven from the host (one small read-back per iteration); for profilers
+ * that do not trace kernels inside conditional graph nodes, and for
+ * debugging. Results are identical. */
+sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
+
 /* Initial state: T (host or device pointer of n_dof doubles) or, if T is
  * NULL, the uniform value T_uniform; simulated time t0. */
 sdc_status sdc_set_temperature(sdc_ctx* ctx, const double* T, double T_uniform, double t0);

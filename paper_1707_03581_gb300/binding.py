@@ -67,6 +67,7 @@ _SIGS = {
     "sdc_set_scheme": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_double, C.c_int, C.c_int]),
     "sdc_set_diagnostics": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_execution": (C.c_int, [_vp, C.c_int]),
     "sdc_set_temperature": (C.c_int, [_vp, _vp, C.c_double, C.c_double]),
     "sdc_step": (C.c_int, [_vp, C.POINTER(StepReport)]),
     "sdc_run_horizon": (C.c_int, [_vp, C.c_int64, C.POINTER(StepReport)]),
@@ -208,6 +209,10 @@ class Solver:
                    cg_max_iter=2000, precision="fp64"):
         self._call("sdc_set_scheme", NODES[nodes], M, P, sweeps, window, dt, cg_rtol, cg_max_iter,
                    PRECISION[precision])
+
+    def set_execution(self, eager: bool):
+        """True: plain kernel launches with host-driven CG loops (profiling/debugging)."""
+        self._call("sdc_set_execution", 1 if eager else 0)
 
     def set_diagnostics(self, residuals: bool):
         self._call("sdc_set_diagnostics", 1 if residuals else 0)

@@ -78,7 +78,11 @@ struct sdc_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_ready = false;
+    bool buffers_ready = false;
     int fixed_kernels = 0;          // kernel nodes of the step graph outside the CG loops
+    int eager = 0;                  // 1: plain launches, host-driven CG loop
+    int eager_kernels = 0;          // kernels launched by the last eager step
+    int* done_host = nullptr;       // pinned
 };
 
 namespace {
@@ -137,11 +141,24 @@ struct Chain {
     cudaGraph_t g;
     cudaGraphNode_t last = nullptr;
     int kernels = 0;
+    cudaStream_t eager = nullptr;   // non-null: launch immediately instead of recording
+    bool is_eager = false;
     explicit Chain(cudaGraph_t gg) : g(gg) {}
+    static Chain launcher(cudaStream_t s) {
+        Chain c(nullptr);
+        c.eager = s;
+        c.is_eager = true;
+        return c;
+    }
 
     template <typename... KArgs>
     void kernel(void (*f)(KArgs...), unsigned grid, unsigned block, KArgs... args) {
         void* params[] = {(void*)&args...};
+        ++kernels;
+        if (is_eager) {
+            SDC_CUDA_TRY(cudaLaunchKernel((const void*)f, dim3(grid), dim3(block), params, 0, eager));
+            return;
+        }
         cudaKernelNodeParams p{};
         p.func = (void*)f;
         p.gridDim = dim3(grid);
@@ -151,9 +168,12 @@ struct Chain {
         cudaGraphNode_t nd;
         SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
         last = nd;
-        ++kernels;
     }
     void copy(void* dst, const void* src, size_t bytes) {
+        if (is_eager) {
+            SDC_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, eager));
+            return;
+        }
         cudaGraphNode_t nd;
         SDC_CUDA_TRY(cudaGraphAddMemcpyNode1D(&nd, g, last ? &last : nullptr, last ? 1 : 0, dst, src, bytes,
                                               cudaMemcpyDeviceToDevice));
@@ -199,6 +219,21 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
 
 // init kernel, then WHILE { spmv, update, p-update }
 void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
+    const unsigned nbe = blocks_for(c->n, RED_BLOCK);
+    if (ch.is_eager) {
+        // host-driven loop: same kernels, the stop flag is read back after each iteration
+        a.handle = 0;
+        ch.kernel(k_cg_init, nbe, RED_BLOCK, a, r);
+        for (;;) {
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->cgs->done, sizeof(int), cudaMemcpyDeviceToHost, ch.eager));
+            SDC_CUDA_TRY(cudaStreamSynchronize(ch.eager));
+            if (*c->done_host) break;
+            ch.kernel(k_cg_spmv, nbe, RED_BLOCK, a);
+            ch.kernel(k_cg_update, nbe, RED_BLOCK, a);
+            ch.kernel(k_cg_pupdate, nbe, RED_BLOCK, a);
+        }
+        return;
+    }
     cudaGraphConditionalHandle h;
     SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, ch.g, 1u, cudaGraphCondAssignDefault));
     a.handle = (unsigned long long)h;
@@ -261,6 +296,7 @@ void do_assemble(sdc_ctx* c) {
     free_pool(c, c->pool_asm);
     c->assembled = false;
     c->temp_set = false;
+    c->buffers_ready = false;
 
     HostCSR K0, K1;
     std::vector<double> m0, m1, g0, g1;
@@ -414,17 +450,13 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
 }
 
-void build_step_graph(sdc_ctx* c) {
-    drop_graph(c);
-    alloc_scheme_buffers(c);
+void emit_step(sdc_ctx* c, Chain& ch) {
     const Weights& W = c->W;
     const int M = W.M, P = W.P, K = c->K_sweeps;
     const int NI = c->C.n_iface;
     const int n_int = (int)c->nondeg.size();
     const double dt = c->dt;
     const unsigned nb = blocks_for(c->n, RED_BLOCK);
-    SDC_CUDA_TRY(cudaGraphCreate(&c->graph, 0));
-    Chain ch(c->graph);
 
     // geometry of f^E at every embedded node of the step (independent of T)
     GeomArgs ga{};
@@ -569,6 +601,13 @@ void build_step_graph(sdc_ctx* c) {
     ch.kernel(k_heat, nb, (unsigned)RED_BLOCK, (const double*)c->d_mass, (const double*)c->Tn, (int64_t)c->n,
               (int64_t)c->n_fix, c->partials, c->counter, &c->st->heat[0]);
     ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], n_int, NI);
+}
+
+void build_step_graph(sdc_ctx* c) {
+    drop_graph(c);
+    SDC_CUDA_TRY(cudaGraphCreate(&c->graph, 0));
+    Chain ch(c->graph);
+    emit_step(c, ch);
     SDC_CUDA_TRY(cudaGraphInstantiate(&c->exec, c->graph, 0));
     c->fixed_kernels = ch.kernels;
     c->graph_ready = true;
@@ -610,7 +649,7 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
         rep->refinements_total += s.refinements[i];
     }
     rep->status = s.status;
-    rep->kernel_launches = c->fixed_kernels + 3 * rep->cg_iters_total;
+    rep->kernel_launches = c->eager ? c->eager_kernels : c->fixed_kernels + 3 * rep->cg_iters_total;
     for (int k = 0; k <= SDC_MAX_SWEEPS; ++k) rep->residual[k] = (c->residuals && k <= c->K_sweeps) ? s.residual[k] : -1.0;
     rep->heat_stand = s.heat[0];
     rep->heat_stock = s.heat[1];
@@ -634,7 +673,23 @@ void ensure_ready(sdc_ctx* c) {
     require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
     require(c->scheme_set, SDC_ERR_STATE, "call sdc_set_scheme first");
     require(c->temp_set, SDC_ERR_STATE, "call sdc_set_temperature first");
-    if (!c->graph_ready) build_step_graph(c);
+    if (!c->buffers_ready) {
+        drop_graph(c);
+        alloc_scheme_buffers(c);
+        c->buffers_ready = true;
+    }
+    if (!c->eager && !c->graph_ready) build_step_graph(c);
+}
+
+// One macro step on the context's stream.
+void launch_step(sdc_ctx* c) {
+    if (c->eager) {
+        Chain ch = Chain::launcher(c->stream);
+        emit_step(c, ch);
+        c->eager_kernels = ch.kernels;
+    } else {
+        SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
+    }
 }
 
 }  // namespace
@@ -656,7 +711,8 @@ sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream) {
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(device) != cudaSuccess ||
-        cudaMallocHost((void**)&c->st_host, sizeof(StepState)) != cudaSuccess) {
+        cudaMallocHost((void**)&c->st_host, sizeof(StepState)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->done_host, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SDC_ERR_CUDA;
@@ -673,6 +729,7 @@ void sdc_destroy(sdc_ctx* c) {
     free_pool(c, c->pool_scheme);
     free_pool(c, c->pool_asm);
     if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->done_host) cudaFreeHost(c->done_host);
     delete c;
 }
 
@@ -794,12 +851,20 @@ sdc_status sdc_set_scheme(sdc_ctx* c, sdc_nodes nodes, int M, int P, int sweeps,
             if (c->W.c[m] > c->W.c[m - 1]) c->nondeg.push_back(m);
         c->scheme_set = true;
         c->graph_ready = false;
+        c->buffers_ready = false;
         if (c->assembled) {
             c->st_host->dt = dt;
             SDC_CUDA_TRY(cudaMemcpyAsync(&c->st->dt, &c->st_host->dt, sizeof(double), cudaMemcpyHostToDevice,
                                          c->stream));
             SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
         }
+    });
+}
+
+sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
+    return guarded(c, [&] {
+        c->eager = eager ? 1 : 0;
+        c->graph_ready = false;
     });
 }
 
@@ -833,7 +898,7 @@ sdc_status sdc_set_temperature(sdc_ctx* c, const double* T, double T_uniform, do
 sdc_status sdc_step(sdc_ctx* c, sdc_step_report* rep) {
     return guarded(c, [&] {
         ensure_ready(c);
-        SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
+        launch_step(c);
         if (rep) read_state(c, rep);
     });
 }
@@ -842,7 +907,7 @@ sdc_status sdc_run_horizon(sdc_ctx* c, int64_t n_steps, sdc_step_report* last) {
     return guarded(c, [&] {
         require(n_steps >= 0, SDC_ERR_ARG, "n_steps must be >= 0");
         ensure_ready(c);
-        for (int64_t i = 0; i < n_steps; ++i) SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
+        for (int64_t i = 0; i < n_steps; ++i) launch_step(c);
         read_state(c, last);
     });
 }

@@ -206,3 +206,16 @@ def test_errors_are_reported_not_fatal(torch):
     s2.set_scheme("lobatto", 3, 20, 3, 0, 1.0, 1e-12, 2000)
     s2.set_temperature(None, 20.0, 0.0)
     s2.step(report=True)
+
+
+def test_eager_execution_matches_graph(torch):
+    mach = machine_config(0)
+    a = _solver(mach)
+    b = _solver(mach)
+    b.set_execution(True)
+    for _ in range(3):
+        ra = a.step(report=True)
+        rb = b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    assert ra["cg_iters_total"] == rb["cg_iters_total"]
+    assert ra["kernel_launches"] == rb["kernel_launches"]
