@@ -229,6 +229,32 @@ sdc_status sdc_contact_flux(sdc_ctx* ctx, const double* T_dev, double t, double*
  * The values of the work vectors are overwritten. Waits. */
 sdc_status sdc_time_cg_kernels(sdc_ctx* ctx, double dtau, int reps, float* ms_out);
 
+/* ---------------------------------------------------------------- allocation-free variant
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory while they run. Examples are a monitoring hook
+ * inside a real-time look-ahead loop, where a cudaMalloc/cudaFree would
+ * implicitly synchronise the device and stall the steps in flight, and a
+ * process that has handed all free device memory to another framework's
+ * pool.
+ *
+ * heat_dev[0] = sum over stand DOFs of m_i T_i, heat_dev[1] = the same over
+ * stock DOFs [J], for any temperature field T_dev (device, n_dof doubles) of
+ * this context's model. Same reduction as the ledger behind
+ * sdc_get_heat_totals. heat_dev is a device pointer to 2 doubles, written
+ * asynchronously on the context's stream.
+ *
+ * The call allocates nothing. Its scratch is one fixed 512 KiB (+256 B) device
+ * array inside the library, present on every GPU that loads the library
+ * until the process exits. Limit: n_dof <= 8,388,608; larger models get
+ * SDC_ERR_ARG with a message.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls on a device share the one array. Calls whose kernels overlap on
+ * the GPU (other streams, other contexts) race on it and give wrong totals,
+ * so serialise them, e.g. on one stream. */
+sdc_status sdc_heat_totals_noalloc(sdc_ctx* ctx, const double* T_dev, double* heat_dev);
+
 #ifdef __cplusplus
 }
 #endif

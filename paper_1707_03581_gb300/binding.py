@@ -81,6 +81,7 @@ _SIGS = {
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_time_cg_kernels": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_float)]),
+    "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
 }
 
 _LIB = None
@@ -324,4 +325,12 @@ class Solver:
         T = self._dev(T)
         out = self._torch.empty_like(T)
         self._call("sdc_contact_flux", _vp(T.data_ptr()), float(t), _vp(out.data_ptr()))
+        return out
+
+    def heat_totals_noalloc(self, T_ptr: int, out):
+        """Stored heat of stand and stock of the device field at T_ptr, into the
+        2-element float64 CUDA tensor `out`, without any device allocation
+        (see sdc_heat_totals_noalloc: fixed scratch, at most 8,388,608 DOF;
+        concurrent calls on one device race)."""
+        self._call("sdc_heat_totals_noalloc", _vp(int(T_ptr)), _vp(out.data_ptr()))
         return out

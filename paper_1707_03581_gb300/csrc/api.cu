@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1079,3 +1080,75 @@ sdc_status sdc_time_cg_kernels(sdc_ctx* c, double dtau, int reps, float* ms_out)
 }
 
 }  // extern "C"
+
+// ============================================================================ allocation-free heat ledger
+//
+// sdc_heat_totals_noalloc runs the heat-ledger reduction k_heat with its
+// scratch (per-block partial sums, then the arrival counter of the
+// last-block combination) in the fixed device array below instead of the
+// context's buffers, so the call itself never allocates device memory.
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 32768;
+constexpr int64_t NOALLOC_MAX_DOF = (int64_t)NOALLOC_MAX_BLOCKS * RED_BLOCK;      // 8,388,608
+constexpr size_t NOALLOC_PARTIAL_BYTES = 2 * (size_t)NOALLOC_MAX_BLOCKS * sizeof(double);  // 512 KiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_PARTIAL_BYTES + 256;             // + counter
+
+// Host code must not use this name as an address: the host-side symbol is a
+// stand-in. Its device address comes from cudaGetSymbolAddress, per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on `device`, looked up once per device
+// with that device current (the caller makes it current).
+unsigned char* noalloc_scratch(int device) {
+    require(device >= 0 && device < NOALLOC_MAX_DEVICES, SDC_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            throw ApiError(SDC_ERR_CUDA, std::string("cudaGetSymbolAddress of the heat-ledger scratch failed: ") +
+                                             cudaGetErrorString(e));
+        }
+        g_noalloc_addr[device] = p;
+    }
+    return static_cast<unsigned char*>(g_noalloc_addr[device]);
+}
+
+// Makes `device` current for the scope and restores the caller's device.
+struct CurrentDevice {
+    int prev = -1;
+    explicit CurrentDevice(int device) {
+        SDC_CUDA_TRY(cudaGetDevice(&prev));
+        if (prev != device) SDC_CUDA_TRY(cudaSetDevice(device));
+    }
+    ~CurrentDevice() {
+        int now = -1;
+        if (cudaGetDevice(&now) == cudaSuccess && now != prev && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" sdc_status sdc_heat_totals_noalloc(sdc_ctx* c, const double* T_dev, double* heat_dev) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(T_dev && heat_dev, SDC_ERR_ARG, "null buffer");
+        require(c->n <= NOALLOC_MAX_DOF, SDC_ERR_ARG,
+                "sdc_heat_totals_noalloc handles at most 8,388,608 DOF (its fixed scratch holds 32,768 "
+                "block partials); use sdc_get_heat_totals for larger models");
+        CurrentDevice on(c->device);
+        unsigned char* base = noalloc_scratch(c->device);
+        double* partials = reinterpret_cast<double*>(base);
+        unsigned int* counter = reinterpret_cast<unsigned int*>(base + NOALLOC_PARTIAL_BYTES);
+        SDC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c->stream));
+        k_heat<<<blocks_for(c->n, RED_BLOCK), RED_BLOCK, 0, c->stream>>>(c->d_mass, T_dev, c->n, c->n_fix, partials,
+                                                                          counter, heat_dev);
+        SDC_CUDA_TRY(cudaGetLastError());
+    });
+}
