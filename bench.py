@@ -156,8 +156,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed_steps(s, stream, flush, steps, torch):
+    """Run `steps` macro steps, each bracketed by CUDA events on the solver's
+    stream, with L2 flushed before each one outside the events; return ms per step."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        s.step(report=False)
+        ends[k].record(stream)
+        s.synchronize()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
 def run_gpu(args, rank, world):
-    import numpy as np
     import torch
 
     from paper_1707_03581_gb300 import Solver
@@ -180,23 +194,22 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        launches, cg_iters = 0, 0
         with ClockSampler(local) as clk:
-            for k in range(args.steps):
-                flush.fill_(float(k))
-                starts[k].record(stream)
-                s.step(report=False)
-                ends[k].record(stream)
-                s.synchronize()
-            torch.cuda.synchronize()
-        ms_steps = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+            ms_steps = _timed_steps(s, stream, flush, args.steps, torch)
         total_ms = float(sum(ms_steps))
-    # launches and CG work of one step, from a reported step after the timed region
-    rep = s.step(report=True)
-    launches = rep["kernel_launches"] * args.steps
-    cg_iters = rep["cg_iters_total"]
+        # launches and CG work of one step, from a reported step after the timed region
+        rep = s.step(report=True)
+        launches = rep["kernel_launches"] * args.steps
+        cg_iters = rep["cg_iters_total"]
+
+        # per-kernel device times of the same steps, each launch between CUDA events on the
+        # solver's stream (plain launches; the CG loop is driven from the host one iteration ahead)
+        s.set_execution(True)
+        s.set_kernel_timing(True)
+        eager_ms = _timed_steps(s, stream, flush, args.steps, torch)
+        kt = s.kernel_times()
+        s.set_kernel_timing(False)
+        s.set_execution(bool(args.eager))
 
     t_max = total_ms
     if world > 1:
@@ -225,12 +238,16 @@ def run_gpu(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
 
-    # dominant kernel (CG SpMV + dot), timed live on the solver's stream
-    dtau = m.scheme.dt * (0.5 if m.scheme.nodes == "lobatto" else 1.0 / m.scheme.M)
-    kt = s.time_cg_kernels(dtau, reps=50)
+    # dominant HBM kernel: the CG SpMV y = m p + dtau K p with <p, y>
     peak, peak_kind = _peaks()
     spmv_bytes = 12 * s.nnz + 24 * s.n
-    achieved = spmv_bytes / (kt["spmv"] * 1e-3) / 1e9
+    n_spmv, ms_spmv = kt.get("k_cg_spmv", (0, 0.0))
+    ms_per_spmv = ms_spmv / max(n_spmv, 1)
+    achieved = spmv_bytes / (ms_per_spmv * 1e-3) / 1e9 if n_spmv else 0.0
+    kern_total = sum(v[1] for v in kt.values())
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                   "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / kern_total if kern_total else 0.0}
+               for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
 
     if rank != 0:
         return
@@ -240,19 +257,23 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MiB write)"},
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "execution": "eager launches" if args.eager else "one CUDA graph per macro step"},
         "eta": args.steps * m.scheme.dt / (t_max * 1e-3),
         "cg_iters_per_step": cg_iters,
+        "contact_cluster": rep["contact_cluster"],
         "e2e": {"value": units_per_step * args.steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * s.n, "d2h_bytes_per_step": 8 * s.n,
                 "eta": args.steps * m.scheme.dt / e2e_s},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": None,
                      "kernel": "k_cg_spmv (FP64 sliced-ELL SpMV + <p, y>)",
-                     "algorithmic_bytes": spmv_bytes, "ms_per_launch": kt["spmv"],
-                     "ms_cg_update": kt["update"], "ms_cg_pupdate": kt["pupdate"],
-                     "peak_kind": peak_kind},
+                     "algorithmic_bytes": spmv_bytes, "ms_per_launch": ms_per_spmv,
+                     "launches_timed": n_spmv, "peak_kind": peak_kind,
+                     "timing": "CUDA events around each launch of the eager timed steps"},
+        "kernels": kernels,
+        "eager_ms_per_step": sum(eager_ms) / len(eager_ms),
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and world == 1:

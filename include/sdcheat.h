@@ -75,6 +75,9 @@ typedef struct {
     double residual[SDC_MAX_SWEEPS + 1];    /* r^k, k = 0..K (Eq. residual), if enabled; else -1 */
     double heat_stand;                      /* sum_i m_i T_i over stand DOFs [J]              */
     double heat_stock;                      /* sum_i m_i T_i over stock DOFs [J]              */
+    int32_t contact_cluster;                /* CTAs of the thread-block cluster that runs the
+                                               contact substeps                               */
+    int32_t pad_;
 } sdc_step_report;
 
 /* Heat ledger (all FP64). */
@@ -165,6 +168,19 @@ sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
  * debugging. Results are identical. */
 sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
 
+/* Measurement aid for eager execution (sdc_set_execution(ctx, 1)): when on,
+ * every kernel launch of a step is bracketed by CUDA events on the
+ * context's stream and each step waits for its launches, summing the
+ * device time per kernel. Switching it (on or off) clears the sums. */
+sdc_status sdc_set_kernel_timing(sdc_ctx* ctx, int on);
+
+/* Per-kernel sums since timing was switched on: up to `capacity` entries of
+ * names (static strings owned by the library), launch counts and total
+ * device milliseconds; *n_kinds receives the number of kernels seen. Any
+ * output array may be NULL. */
+sdc_status sdc_get_kernel_times(sdc_ctx* ctx, int32_t capacity, const char** names, int32_t* launches,
+                                double* ms_total, int32_t* n_kinds);
+
 /* Initial state: T (host or device pointer of n_dof doubles) or, if T is
  * NULL, the uniform value T_uniform; simulated time t0. */
 sdc_status sdc_set_temperature(sdc_ctx* ctx, const double* T, double T_uniform, double t0);
@@ -222,12 +238,6 @@ sdc_status sdc_solve(sdc_ctx* ctx, double dtau, const double* b_dev, double* x_d
  * and friction terms of Eq. femContFix / femContMov. */
 sdc_status sdc_contact_flux(sdc_ctx* ctx, const double* T_dev, double t, double* fE_dev);
 
-/* Measurement aid: run the three kernels of one FP64 CG iteration
- * (SpMV + dot, update + dots, direction update) `reps` times each, outside
- * any graph, on the context's stream, on the work vectors of the last solve,
- * and return their average device times in ms_out[0..2] (CUDA events).
- * The values of the work vectors are overwritten. Waits. */
-sdc_status sdc_time_cg_kernels(sdc_ctx* ctx, double dtau, int reps, float* ms_out);
 
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart: this is a service for callers that must not

@@ -34,7 +34,8 @@ class StepReport(C.Structure):
                 ("cg_iters_total", C.c_int32), ("cg_iters_max", C.c_int32),
                 ("refinements_total", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int32),
                 ("residual", C.c_double * (MAX_SWEEPS + 1)),
-                ("heat_stand", C.c_double), ("heat_stock", C.c_double)]
+                ("heat_stand", C.c_double), ("heat_stock", C.c_double),
+                ("contact_cluster", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self):
         return {"t": self.t, "sweeps": self.sweeps, "n_solves": self.n_solves,
@@ -42,7 +43,8 @@ class StepReport(C.Structure):
                 "refinements_total": self.refinements_total, "status": self.status,
                 "kernel_launches": self.kernel_launches,
                 "residual": [r for r in self.residual[: self.sweeps + 1]],
-                "heat_stand": self.heat_stand, "heat_stock": self.heat_stock}
+                "heat_stand": self.heat_stand, "heat_stock": self.heat_stock,
+                "contact_cluster": self.contact_cluster}
 
 
 class Heat(C.Structure):
@@ -68,6 +70,9 @@ _SIGS = {
                                  C.c_double, C.c_int, C.c_int]),
     "sdc_set_diagnostics": (C.c_int, [_vp, C.c_int]),
     "sdc_set_execution": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "sdc_get_kernel_times": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int32),
+                                       _f64p, C.POINTER(C.c_int32)]),
     "sdc_set_temperature": (C.c_int, [_vp, _vp, C.c_double, C.c_double]),
     "sdc_step": (C.c_int, [_vp, C.POINTER(StepReport)]),
     "sdc_run_horizon": (C.c_int, [_vp, C.c_int64, C.POINTER(StepReport)]),
@@ -80,7 +85,6 @@ _SIGS = {
     "sdc_apply_operator": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
-    "sdc_time_cg_kernels": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_float)]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
 }
 
@@ -215,6 +219,20 @@ class Solver:
         """True: plain kernel launches with host-driven CG loops (profiling/debugging)."""
         self._call("sdc_set_execution", 1 if eager else 0)
 
+    def set_kernel_timing(self, on: bool):
+        """Eager steps time every kernel launch with CUDA events (see sdc_set_kernel_timing)."""
+        self._call("sdc_set_kernel_timing", 1 if on else 0)
+
+    def kernel_times(self):
+        """{kernel name: (launches, total device ms)} of the timed eager steps."""
+        cap = 32
+        names = (C.c_char_p * cap)()
+        n = (C.c_int32 * cap)()
+        ms = (C.c_double * cap)()
+        k = C.c_int32()
+        self._call("sdc_get_kernel_times", cap, names, n, ms, C.byref(k))
+        return {names[i].decode(): (n[i], ms[i]) for i in range(min(k.value, cap))}
+
     def set_diagnostics(self, residuals: bool):
         self._call("sdc_set_diagnostics", 1 if residuals else 0)
 
@@ -314,12 +332,6 @@ class Solver:
         it = C.c_int32()
         self._call("sdc_solve", dtau, _vp(b.data_ptr()), _vp(x.data_ptr()), C.byref(it))
         return x, it.value
-
-    def time_cg_kernels(self, dtau, reps=20):
-        """Average device ms of the CG SpMV, update and direction kernels (see sdc_time_cg_kernels)."""
-        out = (C.c_float * 3)()
-        self._call("sdc_time_cg_kernels", dtau, int(reps), out)
-        return {"spmv": out[0], "update": out[1], "pupdate": out[2]}
 
     def contact_flux(self, T, t):
         T = self._dev(T)

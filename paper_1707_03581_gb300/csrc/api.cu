@@ -73,7 +73,9 @@ struct sdc_ctx {
     double* FI[2][MAX_M] = {{nullptr}};
     double* fe[2] = {nullptr, nullptr};
     double* ihat[2] = {nullptr, nullptr};
-    double *Ta = nullptr, *Tb = nullptr, *fst = nullptr;
+    double *cpre = nullptr, *fst = nullptr;
+    int iface_cluster = 0;          // CTAs of the substep-loop cluster
+    size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
     double *w_Stil = nullptr, *w_Semb = nullptr, *w_Shat = nullptr, *w_emb = nullptr, *w_slot = nullptr;
     cudaGraph_t graph = nullptr;
@@ -83,7 +85,21 @@ struct sdc_ctx {
     int fixed_kernels = 0;          // kernel nodes of the step graph outside the CG loops
     int eager = 0;                  // 1: plain launches, host-driven CG loop
     int eager_kernels = 0;          // kernels launched by the last eager step
-    int* done_host = nullptr;       // pinned
+    int* done_host = nullptr;       // pinned: CG iteration count and stop flag
+    cudaEvent_t done_ev = nullptr;  // marks the copy of the CG stop flag (eager loop)
+
+    // per-kernel device times of eager steps (CUDA events around each launch)
+    int timing = 0;
+    struct TimedLaunch {
+        const void* f;
+        int ev;                     // events ev (start) and ev + 1 (end) of ev_pool
+        bool valid;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<TimedLaunch> launches;
+    std::vector<const void*> kind_f;            // accumulated per kernel
+    std::vector<int> kind_n;
+    std::vector<double> kind_ms;
 };
 
 namespace {
@@ -144,7 +160,27 @@ struct Chain {
     int kernels = 0;
     cudaStream_t eager = nullptr;   // non-null: launch immediately instead of recording
     bool is_eager = false;
+    sdc_ctx* timer = nullptr;       // eager only: record CUDA events around every launch
     explicit Chain(cudaGraph_t gg) : g(gg) {}
+    int begin_timed(const void* f) {
+        if (!timer) return -1;
+        const int ev = next_event();
+        SDC_CUDA_TRY(cudaEventRecord(timer->ev_pool[ev], eager));
+        timer->launches.push_back({f, ev, true});
+        return ev;
+    }
+    void end_timed(int ev) {
+        if (ev >= 0) SDC_CUDA_TRY(cudaEventRecord(timer->ev_pool[ev + 1], eager));
+    }
+    int next_event() {
+        const int ev = 2 * (int)timer->launches.size();
+        while ((int)timer->ev_pool.size() < ev + 2) {
+            cudaEvent_t e;
+            SDC_CUDA_TRY(cudaEventCreate(&e));
+            timer->ev_pool.push_back(e);
+        }
+        return ev;
+    }
     static Chain launcher(cudaStream_t s) {
         Chain c(nullptr);
         c.eager = s;
@@ -157,7 +193,9 @@ struct Chain {
         void* params[] = {(void*)&args...};
         ++kernels;
         if (is_eager) {
+            const int ev = begin_timed((const void*)f);
             SDC_CUDA_TRY(cudaLaunchKernel((const void*)f, dim3(grid), dim3(block), params, 0, eager));
+            end_timed(ev);
             return;
         }
         cudaKernelNodeParams p{};
@@ -168,6 +206,45 @@ struct Chain {
         p.kernelParams = params;
         cudaGraphNode_t nd;
         SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        last = nd;
+    }
+    // Launch with dynamic shared memory and a thread-block cluster of `cluster` CTAs along x.
+    template <typename... KArgs>
+    void kernel_cluster(void (*f)(KArgs...), unsigned grid, unsigned block, size_t smem, unsigned cluster,
+                        KArgs... args) {
+        void* params[] = {(void*)&args...};
+        ++kernels;
+        if (is_eager) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(block);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = eager;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cluster;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            const int ev = begin_timed((const void*)f);
+            SDC_CUDA_TRY(cudaLaunchKernelExC(&cfg, (const void*)f, params));
+            end_timed(ev);
+            return;
+        }
+        cudaKernelNodeParams p{};
+        p.func = (void*)f;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = (unsigned)smem;
+        p.kernelParams = params;
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        cudaLaunchAttributeValue v{};
+        v.clusterDim.x = cluster;
+        v.clusterDim.y = 1;
+        v.clusterDim.z = 1;
+        SDC_CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributeClusterDimension, &v));
         last = nd;
     }
     void copy(void* dst, const void* src, size_t bytes) {
@@ -222,17 +299,35 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
 void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
     const unsigned nbe = blocks_for(c->n, RED_BLOCK);
     if (ch.is_eager) {
-        // host-driven loop: same kernels, the stop flag is read back after each iteration
+        // Host-driven loop with one iteration of lookahead: iteration j+1 is
+        // queued before the stop flag after iteration j is examined, so the GPU
+        // never waits for the host; the iteration queued after convergence
+        // finds the flag set and returns at once.
         a.handle = 0;
         ch.kernel(k_cg_init, nbe, RED_BLOCK, a, r);
-        for (;;) {
-            SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->cgs->done, sizeof(int), cudaMemcpyDeviceToHost, ch.eager));
-            SDC_CUDA_TRY(cudaStreamSynchronize(ch.eager));
-            if (*c->done_host) break;
+        auto iteration = [&] {
             ch.kernel(k_cg_spmv, nbe, RED_BLOCK, a);
             ch.kernel(k_cg_update, nbe, RED_BLOCK, a);
             ch.kernel(k_cg_pupdate, nbe, RED_BLOCK, a);
+        };
+        iteration();
+        int queued = 1;
+        for (;;) {
+            // iter and done are adjacent in CgState: one copy of both
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->cgs->iter, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                         ch.eager));
+            SDC_CUDA_TRY(cudaEventRecord(c->done_ev, ch.eager));
+            iteration();
+            ++queued;
+            SDC_CUDA_TRY(cudaEventSynchronize(c->done_ev));
+            if (c->done_host[1]) break;
         }
+        // iterations queued after convergence did no work: neither count nor time them
+        const int idle = queued - c->done_host[0];
+        ch.kernels -= 3 * idle;
+        if (ch.timer)
+            for (size_t k = ch.timer->launches.size() - 3 * (size_t)idle; k < ch.timer->launches.size(); ++k)
+                ch.timer->launches[k].valid = false;
         return;
     }
     cudaGraphConditionalHandle h;
@@ -344,6 +439,9 @@ void do_assemble(sdc_ctx* c) {
     ContactDev& C = c->C;
     C = ContactDev{};
     C.n_iface = (int)H.dof.size();
+    require(C.n_iface <= IFACE_MAX_NI, SDC_ERR_ARG,
+            "the contact interface has more than 14,336 DOFs (the substep loop keeps two replicas of it in "
+            "each CTA's shared memory)");
     C.n_iface_fix = H.n_iface_fix;
     C.nq_fix = H.nq_fix;
     C.nq_mov = H.nq_mov;
@@ -351,6 +449,15 @@ void do_assemble(sdc_ctx* c) {
     std::vector<double> mI(H.dof.size());
     for (size_t a = 0; a < H.dof.size(); ++a) mI[a] = c->mass_h[H.dof[a]];
     C.mass = upload(c, c->pool_asm, mI);
+    std::vector<double> mIinv(H.dof.size());
+    for (size_t a = 0; a < H.dof.size(); ++a) mIinv[a] = minv[H.dof[a]];
+    C.minv = upload(c, c->pool_asm, mIinv);
+    std::vector<double> rinv(H.rect.size() / 2);
+    for (size_t f = 0; f < H.rect.size() / 4; ++f) {
+        rinv[2 * f + 0] = 1.0 / (H.rect[4 * f + 2] - H.rect[4 * f + 0]);
+        rinv[2 * f + 1] = 1.0 / (H.rect[4 * f + 3] - H.rect[4 * f + 1]);
+    }
+    C.rinv = reinterpret_cast<const double2*>(upload(c, c->pool_asm, rinv));
     C.inc_ptr = upload(c, c->pool_asm, H.inc_ptr);
     C.inc_quad = upload(c, c->pool_asm, H.inc_quad);
     C.inc_code = upload(c, c->pool_asm, H.inc_code);
@@ -405,6 +512,39 @@ void do_assemble(sdc_ctx* c) {
     c->assembled = true;
 }
 
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule with the
+// substep loop's shared-memory replicas and that has room for every contact DOF.
+void pick_iface_cluster(sdc_ctx* c) {
+    const int NI = c->C.n_iface;
+    const size_t smem = (size_t)2 * std::max(NI, 1) * sizeof(double);
+    // the largest size any context may use, so that contexts with different interfaces coexist
+    SDC_CUDA_TRY(cudaFuncSetAttribute(k_iface_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * IFACE_MAX_NI * sizeof(double))));
+    SDC_CUDA_TRY(cudaFuncSetAttribute(k_iface_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int cs = IFACE_MAX_CLUSTER; cs >= 1; cs /= 2) {
+        if ((int64_t)cs * IFACE_THREADS * IFACE_PER_THREAD < NI) break;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(IFACE_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (void*)k_iface_loop, &cfg) == cudaSuccess && n >= 1) {
+            c->iface_cluster = cs;
+            c->iface_smem = smem;
+            return;
+        }
+        cudaGetLastError();
+    }
+    throw ApiError(SDC_ERR_CUDA, "no thread-block cluster for the contact substep loop fits on this device");
+}
+
 void alloc_scheme_buffers(sdc_ctx* c) {
     free_pool(c, c->pool_scheme);
     const Weights& W = c->W;
@@ -428,9 +568,9 @@ void alloc_scheme_buffers(sdc_ctx* c) {
         c->ihat[s] = dalloc_n<double>(c, c->pool_scheme, (size_t)n_int * NI);
         SDC_CUDA_TRY(cudaMemsetAsync(c->ihat[s], 0, (size_t)n_int * NI * sizeof(double), c->stream));
     }
-    c->Ta = dalloc_n<double>(c, c->pool_scheme, NI);
-    c->Tb = dalloc_n<double>(c, c->pool_scheme, NI);
+    c->cpre = dalloc_n<double>(c, c->pool_scheme, (size_t)P * NI);
     c->fst = dalloc_n<double>(c, c->pool_scheme, NI);
+    pick_iface_cluster(c);
     const size_t slots = (size_t)n_int * (P + 1);
     c->E.cnt = dalloc_n<int32_t>(c, c->pool_scheme, slots * NI);
     c->E.idx = dalloc_n<int32_t>(c, c->pool_scheme, slots * MAXE * NI);
@@ -479,11 +619,25 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         for (int j = 0; j < MAX_M; ++j) out[j] = j < M ? dt * W.S[(size_t)(m - 1) * M + j] : 0.0;
     };
     int solve = 0;
-    auto iface_args = [&](int ii, int m, int mode, int set_old, int set_new) {
+    // substeps of interval ii (standard node m): k_iface_prep, then the cluster loop
+    auto substeps = [&](int ii, int m, int mode, int set_old, int set_new) {
+        PrepArgs pa{};
+        pa.C = c->C;
+        pa.mode = mode;
+        pa.P = P;
+        pa.dt = dt;
+        pa.st = c->st;
+        pa.emb = c->w_emb + (size_t)(m - 1) * (P + 1);
+        pa.fstar = c->fst;
+        for (int j = 0; j < M; ++j) pa.FI[j] = c->FI[set_old][j];
+        pa.nFI = M;
+        pa.Stil = c->w_Stil + (size_t)(m - 1) * P * M;
+        pa.Semb = c->w_Semb + (size_t)(m - 1) * P * P;
+        pa.fe_old = c->fe[set_old] + (size_t)ii * (P + 1) * NI;
+        pa.cpre = c->cpre;
+        ch.kernel(k_iface_prep, blocks_for((int64_t)P * NI, 256), 256u, pa);
         IfaceArgs ia{};
         ia.C = c->C;
-        ia.A = c->A;
-        ia.g = c->d_genv;
         ia.mode = mode;
         ia.first = ii == 0;
         ia.P = P;
@@ -492,12 +646,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.emb = c->w_emb + (size_t)(m - 1) * (P + 1);
         ia.Tprev = c->Tstd[m - 1];
         ia.Tout = c->Tstd[m];
-        ia.X = c->X;
-        ia.FIm = c->FI[set_old][m - 1];
-        for (int j = 0; j < M; ++j) ia.FI[j] = c->FI[set_old][j];
-        ia.nFI = M;
-        ia.Stil = c->w_Stil + (size_t)(m - 1) * P * M;
-        ia.Semb = c->w_Semb + (size_t)(m - 1) * P * P;
+        ia.cpre = c->cpre;
         ia.Shat = c->w_Shat + (size_t)(m - 1) * P;
         ia.E = c->E;
         ia.slot0 = ii * (P + 1);
@@ -505,10 +654,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.fe_new = c->fe[set_new] + (size_t)ii * (P + 1) * NI;
         ia.fe_prev_end = ii > 0 ? c->fe[set_new] + ((size_t)(ii - 1) * (P + 1) + P) * NI : nullptr;
         ia.ihat_new = c->ihat[set_new] + (size_t)ii * NI;
-        ia.Ta = c->Ta;
-        ia.Tb = c->Tb;
-        ia.fstar = c->fst;
-        return ia;
+        ch.kernel_cluster(k_iface_loop, (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
+                          (unsigned)c->iface_cluster, ia);
     };
     auto residual = [&](int set, int k) {
         ResidualArgs ra{};
@@ -552,8 +699,10 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         b.dtau = dtau;
         b.mode = RHS_PRED;
         b.n = c->n;
+        b.pos = c->C.pos;
+        b.fstar_I = c->fst;
         ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
-        ch.kernel(k_iface_loop, (unsigned)IFACE_CLUSTER, (unsigned)IFACE_THREADS, iface_args(ii, m, RHS_PRED, 0, 0));
+        substeps(ii, m, RHS_PRED, 0, 0);
         ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m], c->FI[0][m - 1]);
     }
     // ---- Algorithm 2 (sweeps)
@@ -589,9 +738,10 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.dtau = dtau;
             b.mode = RHS_SWEEP;
             b.n = c->n;
+            b.pos = c->C.pos;
+            b.fstar_I = c->fst;
             ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
-            ch.kernel(k_iface_loop, (unsigned)IFACE_CLUSTER, (unsigned)IFACE_THREADS,
-                      iface_args(ii, m, RHS_SWEEP, so, sn));
+            substeps(ii, m, RHS_SWEEP, so, sn);
             if (k < K || c->residuals)
                 ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m],
                           c->FI[sn][m - 1]);
@@ -654,6 +804,7 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
     for (int k = 0; k <= SDC_MAX_SWEEPS; ++k) rep->residual[k] = (c->residuals && k <= c->K_sweeps) ? s.residual[k] : -1.0;
     rep->heat_stand = s.heat[0];
     rep->heat_stock = s.heat[1];
+    rep->contact_cluster = c->iface_cluster;
 }
 
 sdc_status read_state(sdc_ctx* c, sdc_step_report* rep) {
@@ -682,12 +833,48 @@ void ensure_ready(sdc_ctx* c) {
     if (!c->eager && !c->graph_ready) build_step_graph(c);
 }
 
+const char* kernel_name(const void* f) {
+    static const std::pair<const void*, const char*> names[] = {
+        {(const void*)k_cg_init, "k_cg_init"},         {(const void*)k_cg_spmv, "k_cg_spmv"},
+        {(const void*)k_cg_update, "k_cg_update"},     {(const void*)k_cg_pupdate, "k_cg_pupdate"},
+        {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
+        {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_loop, "k_iface_loop"},
+        {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
+        {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
+    };
+    for (const auto& n : names)
+        if (n.first == f) return n.second;
+    return "other";
+}
+
+// Wait for the timed launches of an eager step and add their durations to the per-kernel sums.
+void collect_times(sdc_ctx* c) {
+    SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (const auto& L : c->launches) {
+        if (!L.valid) continue;
+        float ms = 0.f;
+        SDC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_pool[L.ev], c->ev_pool[L.ev + 1]));
+        size_t k = 0;
+        while (k < c->kind_f.size() && c->kind_f[k] != L.f) ++k;
+        if (k == c->kind_f.size()) {
+            c->kind_f.push_back(L.f);
+            c->kind_n.push_back(0);
+            c->kind_ms.push_back(0.0);
+        }
+        c->kind_n[k] += 1;
+        c->kind_ms[k] += ms;
+    }
+    c->launches.clear();
+}
+
 // One macro step on the context's stream.
 void launch_step(sdc_ctx* c) {
     if (c->eager) {
         Chain ch = Chain::launcher(c->stream);
+        if (c->timing) ch.timer = c;
         emit_step(c, ch);
         c->eager_kernels = ch.kernels;
+        if (c->timing) collect_times(c);
     } else {
         SDC_CUDA_TRY(cudaGraphLaunch(c->exec, c->stream));
     }
@@ -713,7 +900,8 @@ sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaMallocHost((void**)&c->st_host, sizeof(StepState)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->done_host, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost((void**)&c->done_host, 2 * sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SDC_ERR_CUDA;
@@ -731,6 +919,8 @@ void sdc_destroy(sdc_ctx* c) {
     free_pool(c, c->pool_asm);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->done_host) cudaFreeHost(c->done_host);
+    if (c->done_ev) cudaEventDestroy(c->done_ev);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -866,6 +1056,30 @@ sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
     return guarded(c, [&] {
         c->eager = eager ? 1 : 0;
         c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_kernel_timing(sdc_ctx* c, int on) {
+    return guarded(c, [&] {
+        c->timing = on ? 1 : 0;
+        c->launches.clear();
+        c->kind_f.clear();
+        c->kind_n.clear();
+        c->kind_ms.clear();
+    });
+}
+
+sdc_status sdc_get_kernel_times(sdc_ctx* c, int32_t capacity, const char** names, int32_t* launches,
+                                double* ms_total, int32_t* n_kinds) {
+    return guarded(c, [&] {
+        require(n_kinds != nullptr, SDC_ERR_ARG, "n_kinds is NULL");
+        const int n = (int)c->kind_f.size();
+        *n_kinds = n;
+        for (int k = 0; k < std::min(n, (int)capacity); ++k) {
+            if (names) names[k] = kernel_name(c->kind_f[k]);
+            if (launches) launches[k] = c->kind_n[k];
+            if (ms_total) ms_total[k] = c->kind_ms[k];
+        }
     });
 }
 
@@ -1045,37 +1259,6 @@ sdc_status sdc_contact_flux(sdc_ctx* c, const double* T, double t, double* fE) {
         k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 1);
         SDC_CUDA_TRY(cudaGetLastError());
         read_state(c, nullptr);
-    });
-}
-
-sdc_status sdc_time_cg_kernels(sdc_ctx* c, double dtau, int reps, float* ms_out) {
-    return guarded(c, [&] {
-        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
-        require(reps >= 1 && ms_out, SDC_ERR_ARG, "reps >= 1 and ms_out required");
-        CgArgs a = cg_args(c, dtau, 0, c->rtol, c->max_iter);
-        a.handle = 0;
-        const unsigned nb = blocks_for(c->n, RED_BLOCK);
-        cudaEvent_t ev[2];
-        SDC_CUDA_TRY(cudaEventCreate(&ev[0]));
-        SDC_CUDA_TRY(cudaEventCreate(&ev[1]));
-        for (int kind = 0; kind < 3; ++kind) {
-            SDC_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
-            for (int r = 0; r < reps; ++r) {
-                if (kind == 0) k_cg_spmv<<<nb, RED_BLOCK, 0, c->stream>>>(a);
-                else if (kind == 1) k_cg_update<<<nb, RED_BLOCK, 0, c->stream>>>(a);
-                else k_cg_pupdate<<<nb, RED_BLOCK, 0, c->stream>>>(a);
-            }
-            SDC_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
-            SDC_CUDA_TRY(cudaEventSynchronize(ev[1]));
-            float ms = 0;
-            SDC_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-            ms_out[kind] = ms / reps;
-        }
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-        SDC_CUDA_TRY(cudaGetLastError());
-        SDC_CUDA_TRY(cudaMemsetAsync(&c->st->status, 0, sizeof(int), c->stream));
-        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
     });
 }
 

@@ -109,6 +109,8 @@ struct ContactDev {
     int nq_fix = 0, nq_mov = 0;            // quads: stand 0..nq_fix-1, stock nq_fix..
     const int32_t* dof = nullptr;          // n_iface global DOF ids
     const double* mass = nullptr;          // n_iface lumped masses
+    const double* minv = nullptr;          // n_iface inverse lumped masses
+    const double2* rinv = nullptr;         // per quad: 1 / (hi_u - lo_u), 1 / (hi_v - lo_v)
     const int32_t* inc_ptr = nullptr;      // n_iface + 1
     const int32_t* inc_quad = nullptr;     // incident quad ids
     const int32_t* inc_code = nullptr;     // corner code of the node in that quad

@@ -163,6 +163,7 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
 
 // y = m .* p + dtau K p; alpha = (r, z) / (p, y)
 __global__ void k_cg_spmv(CgArgs a) {
+    if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (i < a.n) {
@@ -180,6 +181,7 @@ __global__ void k_cg_spmv(CgArgs a) {
 
 // x += alpha p; r -= alpha y; z = D r; beta = (r, z)_new / (r, z)_old; stop test
 __global__ void k_cg_update(CgArgs a) {
+    if (a.cg->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double alpha = a.cg->alpha;
     double v[2] = {0.0, 0.0};
@@ -212,6 +214,7 @@ __global__ void k_cg_update(CgArgs a) {
 
 // p = z + beta p
 __global__ void k_cg_pupdate(CgArgs a) {
+    if (a.cg->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double beta = a.cg->beta;
     if (i < a.n) a.P[i] = fma(beta, a.P[i], a.Z[i]);
@@ -229,16 +232,19 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const double KX = ell_row(a.A, i, a.X);
-    double incr;
+    double incr, fstar;
     if (a.mode == RHS_PRED) {
-        incr = a.dtau * (a.g[i] - KX);
+        fstar = a.g[i] - KX;
+        incr = a.dtau * fstar;
     } else {
-        const double fstar = -KX - (a.FIm[i] - a.g[i]);
+        fstar = -KX - (a.FIm[i] - a.g[i]);
         double I = 0.0;
         for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
         incr = fma(a.dtau, fstar, I);
     }
     a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
+    const int pa = a.pos[i];
+    if (pa >= 0) a.fstar_I[pa] = fstar;
 }
 
 // ------------------------------------------------------------------ contact geometry
@@ -249,13 +255,6 @@ __device__ __forceinline__ void motion_at(const ContactDev& C, double tau, doubl
     du = C.dir_u * s;
     dv = C.dir_v * s;
     q = C.q0 * fabs(cos(ph));
-}
-
-__device__ __forceinline__ double corner_phi(int code, const Rect4& r, double pu, double pv) {
-    const double wu = r.z - r.x, wv = r.w - r.y;
-    const double fu = (code & 1) ? (pu - r.x) / wu : (r.z - pu) / wu;
-    const double fv = (code & 2) ? (pv - r.y) / wv : (r.w - pv) / wv;
-    return fu * fv;
 }
 
 __device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, int node, double c, bool& overflow) {
@@ -275,9 +274,13 @@ __device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, in
 
 // Coupling operator of Sec. 2 at one substep time, row by row:
 //   f^E_a = sum over faces Q containing a, faces R of the other body
-//           overlapping Q, and the 2x2 Gauss points of the overlap of
-//           w phi^Q_a (h_c (T_R - T_Q) + q/2),
-// stored as a constant plus coefficients on contact DOFs.
+//           overlapping Q, of the 2x2 Gauss rule on the overlap of
+//           phi^Q_a (h_c (T_R - T_Q) + q/2),
+// stored as a constant plus coefficients on contact DOFs. Shape functions
+// of axis-aligned bilinear faces are products of linear functions of u and
+// of v, and the 2x2 rule is the product of two 2-point rules, so every
+// coefficient is a product of two one-dimensional sums:
+//   int phi^Q_a phi^X_c = [sum_g w_g l^Q_a(u_g) l^X_c(u_g)] [sum_g w_g l^Q_a(v_g) l^X_c(v_g)].
 __global__ void k_iface_geom(GeomArgs g) {
     const ContactDev& C = g.C;
     const int NI = C.n_iface;
@@ -306,16 +309,20 @@ __global__ void k_iface_geom(GeomArgs g) {
     for (int e = C.inc_ptr[a]; e < C.inc_ptr[a + 1]; ++e) {
         const int Qf = C.inc_quad[e];
         const int code = C.inc_code[e];
+        const int au = code & 1, av = code >> 1;
         Rect4 Q = C.rect[Qf];
         if (stock) {
             Q.x += du; Q.z += du; Q.y += dv; Q.w += dv;
         }
+        const double2 qi = C.rinv[Qf];
         const int4 qn = C.qnode[Qf];
         // query rectangle in the partner body's frame (stock partners are in reference position)
         const double su = stock ? 0.0 : du, sv = stock ? 0.0 : dv;
         const double lo_u = Q.x - su, lo_v = Q.y - sv, hi_u = Q.z - su, hi_v = Q.w - sv;
-        int iu0 = (int)floor((lo_u - B.bu - B.ou) / B.bu) - 1, iu1 = (int)floor((hi_u - B.ou) / B.bu) + 1;
-        int iv0 = (int)floor((lo_v - B.bv - B.ov) / B.bv) - 1, iv1 = (int)floor((hi_v - B.ov) / B.bv) + 1;
+        // a partner's low corner lies in (lo - bin, hi) along each axis (bins are at least one face
+        // wide); the 1e-9 bin margin absorbs the rounding of these quotients
+        int iu0 = (int)floor((lo_u - B.bu - B.ou) / B.bu - 1e-9), iu1 = (int)floor((hi_u - B.ou) / B.bu + 1e-9);
+        int iv0 = (int)floor((lo_v - B.bv - B.ov) / B.bv - 1e-9), iv1 = (int)floor((hi_v - B.ov) / B.bv + 1e-9);
         iu0 = max(iu0, 0); iv0 = max(iv0, 0);
         iu1 = min(iu1, B.nu - 1); iv1 = min(iv1, B.nv - 1);
         for (int iv = iv0; iv <= iv1; ++iv)
@@ -330,28 +337,40 @@ __global__ void k_iface_geom(GeomArgs g) {
                     const double ua = fmax(Q.x, R.x), ub = fmin(Q.z, R.z);
                     const double va = fmax(Q.y, R.y), vb = fmin(Q.w, R.w);
                     if (!(ub > ua && vb > va)) continue;
+                    const double2 ri = C.rinv[Rf];
                     const int4 rn = C.qnode[Rf];
-                    const double cu = 0.5 * (ua + ub), cv = 0.5 * (va + vb);
                     const double hu = 0.5 * (ub - ua), hv = 0.5 * (vb - va);
-                    const double w = hu * hv;
-                    for (int gq = 0; gq < 4; ++gq) {
-                        const double pu = cu + ((gq & 1) ? gp : -gp) * hu;
-                        const double pv = cv + ((gq & 2) ? gp : -gp) * hv;
-                        const double pq[4] = {corner_phi(0, Q, pu, pv), corner_phi(1, Q, pu, pv),
-                                              corner_phi(2, Q, pu, pv), corner_phi(3, Q, pu, pv)};
-                        const double pr[4] = {corner_phi(0, R, pu, pv), corner_phi(1, R, pu, pv),
-                                              corner_phi(2, R, pu, pv), corner_phi(3, R, pu, pv)};
-                        const double wa = w * pq[code];
-                        cst += wa * 0.5 * q;
-                        const double wh = wa * h_c;
-                        add_entry(idx, coef, n, qn.x, -wh * pq[0], overflow);
-                        add_entry(idx, coef, n, qn.y, -wh * pq[1], overflow);
-                        add_entry(idx, coef, n, qn.z, -wh * pq[2], overflow);
-                        add_entry(idx, coef, n, qn.w, -wh * pq[3], overflow);
-                        add_entry(idx, coef, n, rn.x, wh * pr[0], overflow);
-                        add_entry(idx, coef, n, rn.y, wh * pr[1], overflow);
-                        add_entry(idx, coef, n, rn.z, wh * pr[2], overflow);
-                        add_entry(idx, coef, n, rn.w, wh * pr[3], overflow);
+                    const double cu = 0.5 * (ua + ub), cv = 0.5 * (va + vb);
+                    const double u[2] = {cu - gp * hu, cu + gp * hu};
+                    const double v[2] = {cv - gp * hv, cv + gp * hv};
+                    // linear factors at the Gauss abscissae: index 0 = low-side node, 1 = high-side node
+                    double lqu[2][2], lru[2][2], lqv[2][2], lrv[2][2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        lqu[1][k] = (u[k] - Q.x) * qi.x;
+                        lqu[0][k] = (Q.z - u[k]) * qi.x;
+                        lru[1][k] = (u[k] - R.x) * ri.x;
+                        lru[0][k] = (R.z - u[k]) * ri.x;
+                        lqv[1][k] = (v[k] - Q.y) * qi.y;
+                        lqv[0][k] = (Q.w - v[k]) * qi.y;
+                        lrv[1][k] = (v[k] - R.y) * ri.y;
+                        lrv[0][k] = (R.w - v[k]) * ri.y;
+                    }
+                    double iqu[2], iru[2], iqv[2], irv[2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        iqu[c] = hu * fma(lqu[au][0], lqu[c][0], lqu[au][1] * lqu[c][1]);
+                        iru[c] = hu * fma(lqu[au][0], lru[c][0], lqu[au][1] * lru[c][1]);
+                        iqv[c] = hv * fma(lqv[av][0], lqv[c][0], lqv[av][1] * lqv[c][1]);
+                        irv[c] = hv * fma(lqv[av][0], lrv[c][0], lqv[av][1] * lrv[c][1]);
+                    }
+                    cst += 0.5 * q * (hu * (lqu[au][0] + lqu[au][1])) * (hv * (lqv[av][0] + lqv[av][1]));
+                    const int qnc[4] = {qn.x, qn.y, qn.z, qn.w};
+                    const int rnc[4] = {rn.x, rn.y, rn.z, rn.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        add_entry(idx, coef, n, qnc[c], -h_c * iqu[c & 1] * iqv[c >> 1], overflow);
+                        add_entry(idx, coef, n, rnc[c], h_c * iru[c & 1] * irv[c >> 1], overflow);
                     }
                 }
             }
@@ -378,6 +397,55 @@ __device__ __forceinline__ double apply_coupling(const CouplingOp& E, int slot, 
     return acc;
 }
 
+// Coupling entries of one contact DOF at one slot, first batch loaded ahead
+// of use (the operator does not depend on T, so these loads can be issued
+// before the barrier that publishes T).
+struct CouplingRow {
+    int n;
+    double cst;
+    int idx[IFACE_BATCH];
+    double coef[IFACE_BATCH];
+};
+
+__device__ __forceinline__ void coupling_prefetch(const CouplingOp& E, int slot, int NI, int a, CouplingRow& r) {
+    const size_t so = (size_t)slot * NI + a;
+    r.n = __ldg(E.cnt + so);
+    r.cst = __ldg(E.cst + so);
+#pragma unroll
+    for (int k = 0; k < IFACE_BATCH; ++k) {  // entries past n are never used
+        const size_t o = ((size_t)slot * MAXE + k) * NI + a;
+        r.idx[k] = __ldg(E.idx + o);
+        r.coef[k] = __ldg(E.coef + o);
+    }
+}
+
+// cst + sum_k coef_k T[idx_k] on a replica of T_I in this CTA's shared memory,
+// in entry order; entries past the prefetched batch are fetched IFACE_BATCH at a time.
+__device__ __forceinline__ double coupling_apply_shared(const CouplingOp& E, int slot, int NI, int a,
+                                                        const CouplingRow& r, const double* Tsh) {
+    double acc = r.cst;
+#pragma unroll
+    for (int k = 0; k < IFACE_BATCH; ++k)
+        if (k < r.n) acc = fma(r.coef[k], Tsh[r.idx[k]], acc);
+    for (int k0 = IFACE_BATCH; k0 < r.n; k0 += IFACE_BATCH) {
+        int id[IFACE_BATCH];
+        double cf[IFACE_BATCH];
+#pragma unroll
+        for (int j = 0; j < IFACE_BATCH; ++j) {
+            const int k = k0 + j;
+            if (k < r.n) {
+                const size_t o = ((size_t)slot * MAXE + k) * NI + a;
+                id[j] = __ldg(E.idx + o);
+                cf[j] = __ldg(E.coef + o);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < IFACE_BATCH; ++j)
+            if (k0 + j < r.n) acc = fma(cf[j], Tsh[id[j]], acc);
+    }
+    return acc;
+}
+
 // f^E(T, tau) on all DOFs for one precomputed slot (zero elsewhere is set by the caller).
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* __restrict__ T,
                                 double* __restrict__ Ti, double* __restrict__ out, int phase) {
@@ -392,76 +460,116 @@ __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const doub
 
 // ------------------------------------------------------------------ substep loop
 
-// The P explicit substeps of one interval on the contact DOFs, on one
-// cluster of IFACE_CLUSTER CTAs (Algorithm 1 / Algorithm 2 inner loops):
-//   predictor: m T_{m,p} = m T_{m,p-1} + dt_p (f*_m + f^E(T_{m,p-1}, tau_{m,p-1}))
-//   sweep:     m T_{m,p} = m T_{m,p-1} + dt_p f*_m
-//                          + dt_p (f^E(T^{k+1}_{m,p-1}) - f^E(T^k_{m,p-1})) + I_{m,p-1}^p
-// with I_{m,p-1}^p = sum_j dt stil_{m,p,j} F^I_j + sum_q dt s_{m,p,q} f^E(T^k_{m,q}).
-// Every f^E of the current iterate is stored for the next sweep, together
-// with ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m).
-__global__ void __cluster_dims__(IFACE_CLUSTER, 1, 1) __launch_bounds__(IFACE_THREADS)
-    k_iface_loop(IfaceArgs a) {
+__device__ __forceinline__ double substep_dt(const IfaceArgs& a, double tn, int p) {
+    return __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
+}
+
+// c_p of every substep and contact DOF (see PrepArgs); one thread per (p, DOF).
+__global__ void k_iface_prep(PrepArgs a) {
+    const int NI = a.C.n_iface;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)NI * a.P) return;
+    const int p = (int)(gid / NI) + 1, i = (int)(gid % NI);
+    const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+    const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
+    double c;
+    if (a.mode == RHS_PRED) {
+        c = dtp * a.fstar[i];
+    } else {
+        const int row = a.C.dof[i];
+        double I = 0.0;
+        for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
+        for (int qq = 1; qq <= a.P; ++qq) {
+            const double wq = a.Semb[(size_t)(p - 1) * a.P + (qq - 1)];
+            if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)qq * NI + i], I);
+        }
+        c = fma(dtp, a.fstar[i] - a.fe_old[(size_t)(p - 1) * NI + i], I);
+    }
+    a.cpre[(size_t)(p - 1) * NI + i] = c;
+}
+
+// The P explicit substeps of one interval on the contact DOFs (Algorithm 1 /
+// Algorithm 2 inner loops):
+//   m T_{m,p} = m T_{m,p-1} + c_p + dt_p f^E(T_{m,p-1}, tau_{m,p-1})
+// with c_p from k_iface_prep. One cluster of CTAs; contact DOF i belongs to
+// CTA i mod (cluster size). Every CTA keeps both buffers of a full replica of
+// T_I in shared memory; an owner writes each new value into every CTA's
+// replica (distributed shared memory), then one cluster barrier publishes the
+// substep, and the coupling gathers read the local replica. Each f^E of the
+// current iterate is stored for the next sweep, and
+// ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m) is accumulated.
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
+    extern __shared__ double shT[];            // [2][NI]
     cg::cluster_group cluster = cg::this_cluster();
     const ContactDev& C = a.C;
     const int NI = C.n_iface;
-    const int stride = IFACE_CLUSTER * IFACE_THREADS;
-    const int tid0 = (int)(cluster.block_rank() * IFACE_THREADS + threadIdx.x);
+    const int csize = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
     const int P = a.P;
     const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
 
-    // load T_{m,0} = T_{m-1} and f*_m on the contact DOFs
-    for (int i = tid0; i < NI; i += stride) {
-        const int row = C.dof[i];
-        a.Ta[i] = a.Tprev[row];
-        const double KX = ell_row(a.A, row, a.X);
-        a.fstar[i] = (a.mode == RHS_PRED) ? (a.g[row] - KX) : (-KX - (a.FIm[row] - a.g[row]));
+    // owned DOFs: i = rank + csize * (threadIdx.x + IFACE_THREADS * r)
+    int own[IFACE_PER_THREAD];
+    double T[IFACE_PER_THREAD], fe[IFACE_PER_THREAD], mi[IFACE_PER_THREAD], ih[IFACE_PER_THREAD];
+    CouplingRow row[IFACE_PER_THREAD];
+#pragma unroll
+    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+        const int i = rank + csize * ((int)threadIdx.x + IFACE_THREADS * r);
+        own[r] = i < NI ? i : -1;
+        ih[r] = 0.0;
+        if (own[r] >= 0 && a.first && a.mode == RHS_PRED) coupling_prefetch(a.E, a.slot0, NI, i, row[r]);
     }
+    // T_{m,0} = T_{m-1}: every CTA fills its own replica (buffer 0)
+    for (int i = threadIdx.x; i < NI; i += IFACE_THREADS) shT[i] = a.Tprev[C.dof[i]];
+    // every CTA of the cluster has started (and filled its replica) before any remote write
     cluster.sync();
     // f^E at tau_{m,0}
-    for (int i = tid0; i < NI; i += stride) {
+#pragma unroll
+    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+        const int i = own[r];
+        if (i < 0) continue;
+        T[r] = shT[i];
+        mi[r] = C.minv[i];
         double f0;
         if (a.first) {
-            f0 = (a.mode == RHS_PRED) ? apply_coupling(a.E, a.slot0, NI, i, a.Ta) : a.fe_old[i];
+            f0 = (a.mode == RHS_PRED) ? coupling_apply_shared(a.E, a.slot0, NI, i, row[r], shT) : a.fe_old[i];
         } else {
             f0 = a.fe_prev_end[i];
         }
+        fe[r] = f0;
         a.fe_new[i] = f0;
     }
-    double* Tc = a.Ta;
-    double* Tn = a.Tb;
     for (int p = 1; p <= P; ++p) {
-        const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
-        for (int i = tid0; i < NI; i += stride) {
-            const double fe_cur = a.fe_new[(size_t)(p - 1) * NI + i];
-            double incr;
-            if (a.mode == RHS_PRED) {
-                incr = dtp * (a.fstar[i] + fe_cur);
-            } else {
-                const int row = C.dof[i];
-                double I = 0.0;
-                for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
-                for (int q = 1; q <= P; ++q) {
-                    const double wq = a.Semb[(size_t)(p - 1) * P + (q - 1)];
-                    if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)q * NI + i], I);
-                }
-                incr = dtp * a.fstar[i] + dtp * (fe_cur - a.fe_old[(size_t)(p - 1) * NI + i]) + I;
-            }
-            Tn[i] = Tc[i] + incr / C.mass[i];
+        const double dtp = substep_dt(a, tn, p);
+        double* buf = shT + (size_t)(p & 1) * NI;
+#pragma unroll
+        for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+            const int i = own[r];
+            if (i < 0) continue;
+            coupling_prefetch(a.E, a.slot0 + p, NI, i, row[r]);
+            const double incr = fma(dtp, fe[r], a.cpre[(size_t)(p - 1) * NI + i]);
+            T[r] = fma(incr, mi[r], T[r]);
+            for (int q = 0; q < csize; ++q) *cluster.map_shared_rank(buf + i, q) = T[r];
         }
         cluster.sync();
-        for (int i = tid0; i < NI; i += stride)
-            a.fe_new[(size_t)p * NI + i] = apply_coupling(a.E, a.slot0 + p, NI, i, Tn);
-        double* t = Tc;
-        Tc = Tn;
-        Tn = t;
+#pragma unroll
+        for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+            const int i = own[r];
+            if (i < 0) continue;
+            fe[r] = coupling_apply_shared(a.E, a.slot0 + p, NI, i, row[r], buf);
+            a.fe_new[(size_t)p * NI + i] = fe[r];
+            ih[r] = fma(a.Shat[p - 1], fe[r], ih[r]);
+        }
     }
-    for (int i = tid0; i < NI; i += stride) {
-        a.Tout[C.dof[i]] = Tc[i];
-        double ih = 0.0;
-        for (int q = 1; q <= P; ++q) ih = fma(a.Shat[q - 1], a.fe_new[(size_t)q * NI + i], ih);
-        a.ihat_new[i] = ih;
+#pragma unroll
+    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+        const int i = own[r];
+        if (i < 0) continue;
+        a.Tout[C.dof[i]] = T[r];
+        a.ihat_new[i] = ih[r];
     }
+    // no CTA may exit while others can still write into its shared memory
+    cluster.sync();
 }
 
 // ------------------------------------------------------------------ diagnostics

@@ -6,8 +6,12 @@
 namespace sdc {
 
 constexpr int MAXE = 32;            // coupling entries per contact DOF and substep time
-constexpr int IFACE_CLUSTER = 8;    // CTAs of the substep-loop cluster
-constexpr int IFACE_THREADS = 512;  // threads per CTA of that cluster
+constexpr int IFACE_MAX_CLUSTER = 16;   // CTAs of the substep-loop cluster (at most)
+constexpr int IFACE_THREADS = 512;      // threads per CTA of that cluster
+constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of the loop can own
+constexpr int IFACE_BATCH = 8;          // coupling entries fetched per round
+// largest contact interface the loop takes: two shared-memory replicas of T_I per CTA
+constexpr int IFACE_MAX_NI = 14336;
 
 enum RhsMode { RHS_GIVEN = 0, RHS_PRED = 1, RHS_SWEEP = 2 };
 
@@ -59,6 +63,8 @@ struct BulkArgs {
     double dtau;
     int mode;
     int64_t n;
+    const int32_t* pos;             // DOF -> contact index or -1
+    double* fstar_I;                // [NI] f*_m on the contact DOFs (output)
 };
 
 // Precomputed coupling operator f^E(T, tau_s)_a = cst[s][a] + sum_k coef[s][k][a] T_I[idx[s][k][a]].
@@ -80,25 +86,40 @@ struct GeomArgs {
     int* status;
 };
 
-// Substep loop of one interval (Algorithm 1 or 2, interface DOFs only).
+// T-independent part of every substep increment of one interval
+// (Algorithm 1 / Algorithm 2 inner loops), on the contact DOFs:
+//   predictor: c_p = dt_p f*_m
+//   sweep:     c_p = dt_p (f*_m - f^E(T^k_{m,p-1})) + I_{m,p-1}^p,
+//              I_{m,p-1}^p = sum_j dt stil_{m,p,j} F^I_j + sum_q dt s_{m,p,q} f^E(T^k_{m,q})
+// so that m T_{m,p} = m T_{m,p-1} + c_p + dt_p f^E(T^{k+1}_{m,p-1}).
+struct PrepArgs {
+    ContactDev C;
+    int mode;                       // RHS_PRED or RHS_SWEEP
+    int P;
+    double dt;
+    const StepState* st;
+    const double* emb;              // P+1 unit-step positions of this interval's embedded nodes
+    const double* fstar;            // [NI]
+    const double* FI[MAX_M];
+    int nFI;
+    const double* Stil;             // [P][nFI] dt stil_{m,p,j}
+    const double* Semb;             // [P][P]  dt s_{m,p,q}
+    const double* fe_old;           // [(P+1)][NI] previous iterate (sweep)
+    double* cpre;                   // [P][NI] output
+};
+
+// Sequential substeps of one interval on the contact DOFs (one cluster).
 struct IfaceArgs {
     ContactDev C;
-    EllDev A;
-    const double* g;
     int mode;                       // RHS_PRED or RHS_SWEEP
     int first;                      // first non-degenerate interval of the step
     int P;
     double dt;
     const StepState* st;
     const double* emb;              // P+1 unit-step positions of this interval's embedded nodes
-    const double* Tprev;
-    double* Tout;
-    const double* X;                // T*
-    const double* FIm;
-    const double* FI[MAX_M];
-    int nFI;
-    const double* Stil;             // [P][nFI] dt stil_{m,p,j}
-    const double* Semb;             // [P][P]  dt s_{m,p,q}
+    const double* Tprev;            // T_{m-1} (N)
+    double* Tout;                   // T_m (N), contact rows written here
+    const double* cpre;             // [P][NI]
     const double* Shat;             // [P]     dt shat_{m,q}
     CouplingOp E;                   // slots of this interval start at slot0
     int slot0;
@@ -106,9 +127,6 @@ struct IfaceArgs {
     double* fe_new;                 // [(P+1)][NI]
     const double* fe_prev_end;      // [NI] this iterate's f^E at the end of the previous interval
     double* ihat_new;               // [NI]
-    double* Ta;                     // work [NI]
-    double* Tb;                     // work [NI]
-    double* fstar;                  // work [NI]
 };
 
 struct ResidualArgs {
@@ -137,6 +155,7 @@ __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_iface_geom(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,
                                 int phase);
+__global__ void k_iface_prep(PrepArgs a);
 __global__ void k_iface_loop(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,

@@ -219,3 +219,18 @@ def test_eager_execution_matches_graph(torch):
     assert np.array_equal(a.temperature(), b.temperature())
     assert ra["cg_iters_total"] == rb["cg_iters_total"]
     assert ra["kernel_launches"] == rb["kernel_launches"]
+
+
+def test_eager_kernel_timing_counts_every_launch(torch):
+    mach = machine_config(0)
+    s = _solver(mach)
+    s.set_execution(True)
+    s.set_kernel_timing(True)
+    rep = s.step(report=True)
+    kt = s.kernel_times()
+    assert sum(n for n, _ in kt.values()) == rep["kernel_launches"]
+    assert kt["k_cg_spmv"][0] == rep["cg_iters_total"]
+    assert kt["k_iface_loop"][0] == rep["n_solves"]
+    assert all(ms > 0 for _, ms in kt.values())
+    assert rep["contact_cluster"] >= 1
+    s.close()
