@@ -52,10 +52,17 @@ struct sdc_ctx {
     CgState* cgs = nullptr;
     double* partials = nullptr;
     unsigned int* counter = nullptr;
-    double *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Y = nullptr, *D = nullptr;
+    double *X = nullptr, *R = nullptr, *U = nullptr, *P = nullptr, *Wv = nullptr, *S = nullptr, *D = nullptr;
+    // mixed precision: FP64 right-hand side, FP32 inner vectors, FP32 mass, outer scalars
+    double* Bv = nullptr;
+    float *Dl = nullptr, *Rl = nullptr, *Ul = nullptr, *Pl = nullptr, *Wl = nullptr, *Sl = nullptr,
+          *Dinv = nullptr;
+    float* mass32 = nullptr;
+    MixState* ms = nullptr;
     CouplingOp E1{};                // one slot, for sdc_contact_flux
     double* Ti1 = nullptr;
     int max_blocks = 0;
+    int n_sms = 0;
 
     // scheme
     bool scheme_set = false;
@@ -85,7 +92,7 @@ struct sdc_ctx {
     int fixed_kernels = 0;          // kernel nodes of the step graph outside the CG loops
     int eager = 0;                  // 1: plain launches, host-driven CG loop
     int eager_kernels = 0;          // kernels launched by the last eager step
-    int* done_host = nullptr;       // pinned: CG iteration count and stop flag
+    int* done_host = nullptr;       // pinned: CG iteration count, stop flag, SpMV runs
     cudaEvent_t done_ev = nullptr;  // marks the copy of the CG stop flag (eager loop)
 
     // per-kernel device times of eager steps (CUDA events around each launch)
@@ -152,6 +159,17 @@ void drop_graph(sdc_ctx* c) {
 }
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Grid of a row kernel (blocks of RED_BLOCK threads) over the context's n
+// rows: one row per thread. Row kernels also accept smaller grids (each
+// thread then loops over several rows); measured on GB300 at 313k rows, a
+// one-wave grid with several rows per thread was no faster for the FP32 SpMV
+// and slower for the FP64 one, whose rows then run one after another.
+template <class F>
+unsigned row_grid(sdc_ctx* c, F* kernel) {
+    (void)kernel;
+    return blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK);
+}
 
 // Appends nodes to a graph in a single dependency chain.
 struct Chain {
@@ -280,11 +298,13 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
     a.n = c->n;
     a.X = c->X;
     a.R = c->R;
-    a.Z = c->Z;
+    a.U = c->U;
     a.P = c->P;
-    a.Y = c->Y;
+    a.W = c->Wv;
+    a.S = c->S;
     a.D = c->D;
     a.cg = c->cgs;
+    a.loop_kernels = &c->st->loop_kernels;
     a.partials = c->partials;
     a.counter = c->counter;
     a.iters_out = &c->st->cg_iters[solve_idx];
@@ -295,55 +315,134 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
     return a;
 }
 
+// Host-driven CG iterations (eager execution) with one iteration of lookahead:
+// iteration j+1 is queued before the stop flag after iteration j is examined,
+// so the GPU never waits for the host; an iteration queued after convergence
+// finds the flag set and returns at once. Iterations that did no work are
+// neither counted nor timed.
+template <class Iter>
+void eager_cg_loop(sdc_ctx* c, Chain& ch, Iter iteration) {
+    constexpr int KPI = 2;  // kernels per iteration
+    iteration();
+    int queued = 1;
+    for (;;) {
+        // iter, done and runs are adjacent in CgState: one copy of all three
+        SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->cgs->iter, 3 * sizeof(int), cudaMemcpyDeviceToHost, ch.eager));
+        SDC_CUDA_TRY(cudaEventRecord(c->done_ev, ch.eager));
+        iteration();
+        ++queued;
+        SDC_CUDA_TRY(cudaEventSynchronize(c->done_ev));
+        if (c->done_host[1]) break;
+    }
+    const int idle = queued - c->done_host[2];
+    ch.kernels -= KPI * idle;
+    if (ch.timer)
+        for (size_t k = ch.timer->launches.size() - (size_t)KPI * idle; k < ch.timer->launches.size(); ++k)
+            ch.timer->launches[k].valid = false;
+}
+
+// Mixed precision: init, then WHILE_outer { inner init, WHILE_inner { spmv, update, p-update }, refine }
+void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
+    if (ch.is_eager) {
+        a.h_outer = a.h_inner = 0;
+        ch.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+        for (;;) {
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->ms->passes, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                         ch.eager));
+            SDC_CUDA_TRY(cudaStreamSynchronize(ch.eager));
+            if (c->done_host[1]) break;
+            ch.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
+            eager_cg_loop(c, ch, [&] {
+                ch.kernel(k_mx_spmv, row_grid(c, k_mx_spmv), RED_BLOCK, a);
+                ch.kernel(k_mx_update, row_grid(c, k_mx_update), RED_BLOCK, a);
+            });
+            ch.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
+        }
+        return;
+    }
+    cudaGraphConditionalHandle ho;
+    SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, ch.g, 1u, cudaGraphCondAssignDefault));
+    a.h_outer = (unsigned long long)ho;
+    a.h_inner = 0;
+    ch.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+    Chain outer(ch.while_node(ho));
+    cudaGraphConditionalHandle hi;
+    SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, outer.g, 0u, 0));
+    a.h_inner = (unsigned long long)hi;
+    outer.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
+    Chain inner(outer.while_node(hi));
+    inner.kernel(k_mx_spmv, row_grid(c, k_mx_spmv), RED_BLOCK, a);
+    inner.kernel(k_mx_update, row_grid(c, k_mx_update), RED_BLOCK, a);
+    outer.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
+}
+
 // init kernel, then WHILE { spmv, update, p-update }
 void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
-    const unsigned nbe = blocks_for(c->n, RED_BLOCK);
     if (ch.is_eager) {
-        // Host-driven loop with one iteration of lookahead: iteration j+1 is
-        // queued before the stop flag after iteration j is examined, so the GPU
-        // never waits for the host; the iteration queued after convergence
-        // finds the flag set and returns at once.
         a.handle = 0;
-        ch.kernel(k_cg_init, nbe, RED_BLOCK, a, r);
-        auto iteration = [&] {
-            ch.kernel(k_cg_spmv, nbe, RED_BLOCK, a);
-            ch.kernel(k_cg_update, nbe, RED_BLOCK, a);
-            ch.kernel(k_cg_pupdate, nbe, RED_BLOCK, a);
-        };
-        iteration();
-        int queued = 1;
-        for (;;) {
-            // iter and done are adjacent in CgState: one copy of both
-            SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->cgs->iter, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                                         ch.eager));
-            SDC_CUDA_TRY(cudaEventRecord(c->done_ev, ch.eager));
-            iteration();
-            ++queued;
-            SDC_CUDA_TRY(cudaEventSynchronize(c->done_ev));
-            if (c->done_host[1]) break;
-        }
-        // iterations queued after convergence did no work: neither count nor time them
-        const int idle = queued - c->done_host[0];
-        ch.kernels -= 3 * idle;
-        if (ch.timer)
-            for (size_t k = ch.timer->launches.size() - 3 * (size_t)idle; k < ch.timer->launches.size(); ++k)
-                ch.timer->launches[k].valid = false;
+        ch.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
+        eager_cg_loop(c, ch, [&] {
+            ch.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, a);
+            ch.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, a);
+        });
         return;
     }
     cudaGraphConditionalHandle h;
     SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, ch.g, 1u, cudaGraphCondAssignDefault));
     a.handle = (unsigned long long)h;
-    const unsigned nb = blocks_for(c->n, RED_BLOCK);
-    ch.kernel(k_cg_init, nb, RED_BLOCK, a, r);
+    ch.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
     Chain body(ch.while_node(h));
-    body.kernel(k_cg_spmv, nb, RED_BLOCK, a);
-    body.kernel(k_cg_update, nb, RED_BLOCK, a);
-    body.kernel(k_cg_pupdate, nb, RED_BLOCK, a);
+    body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, a);
+    body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, a);
 }
 
 void require(bool ok, sdc_status code, const char* msg) {
     if (!ok) throw ApiError(code, msg);
 }
+
+constexpr double MIX_INNER_RTOL = 1e-6;   // FP32 inner solve: relative reduction per refinement pass
+constexpr int MIX_INNER_MAX = 500;        // and its iteration cap per pass
+constexpr int MIX_MAX_REFINE = 30;
+
+MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter) {
+    MixArgs a{};
+    a.A = c->A;
+    a.mass = c->d_mass;
+    a.mass32 = c->mass32;
+    a.diagK = c->d_diagK;
+    a.dtau = dtau;
+    a.n = c->n;
+    a.X = c->X;
+    a.R = c->R;
+    a.B = c->Bv;
+    a.Dl = c->Dl;
+    a.Rl = c->Rl;
+    a.Ul = c->Ul;
+    a.Pl = c->Pl;
+    a.Wl = c->Wl;
+    a.Sl = c->Sl;
+    a.Dinv = c->Dinv;
+    a.cg = c->cgs;
+    a.ms = c->ms;
+    a.loop_kernels = &c->st->loop_kernels;
+    a.partials = c->partials;
+    a.counter = c->counter;
+    a.iters_out = &c->st->cg_iters[solve_idx];
+    a.refine_out = &c->st->refinements[solve_idx];
+    a.status = &c->st->status;
+    a.max_iter = std::min(max_iter, MIX_INNER_MAX);
+    a.max_refine = MIX_MAX_REFINE;
+    a.rtol2 = rtol * rtol;
+    a.inner_rtol2 = MIX_INNER_RTOL * MIX_INNER_RTOL;
+    return a;
+}
+
+void add_implicit_solve(sdc_ctx* c, Chain& ch, double dtau, int solve_idx, double rtol, int max_iter,
+                        const RhsArgs& r) {
+    if (c->precision == SDC_MIXED_FP32) add_solve_mixed(c, ch, mix_args(c, dtau, solve_idx, rtol, max_iter), r);
+    else add_solve(c, ch, cg_args(c, dtau, solve_idx, rtol, max_iter), r);
+}
+
 
 void build_ell(sdc_ctx* c) {
     const int64_t n = c->n;
@@ -491,10 +590,24 @@ void do_assemble(sdc_ctx* c) {
     c->Tn = dalloc_n<double>(c, c->pool_asm, N);
     c->X = dalloc_n<double>(c, c->pool_asm, N);
     c->R = dalloc_n<double>(c, c->pool_asm, N);
-    c->Z = dalloc_n<double>(c, c->pool_asm, N);
+    c->U = dalloc_n<double>(c, c->pool_asm, N);
     c->P = dalloc_n<double>(c, c->pool_asm, N);
-    c->Y = dalloc_n<double>(c, c->pool_asm, N);
+    c->Wv = dalloc_n<double>(c, c->pool_asm, N);
+    c->S = dalloc_n<double>(c, c->pool_asm, N);
     c->D = dalloc_n<double>(c, c->pool_asm, N);
+    c->Bv = dalloc_n<double>(c, c->pool_asm, N);
+    c->Dl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Rl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Ul = dalloc_n<float>(c, c->pool_asm, N);
+    c->Pl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Wl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Sl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Dinv = dalloc_n<float>(c, c->pool_asm, N);
+    {
+        std::vector<float> m32(c->mass_h.begin(), c->mass_h.end());
+        c->mass32 = upload(c, c->pool_asm, m32);
+    }
+    c->ms = dalloc_n<MixState>(c, c->pool_asm, 1);
     c->st = dalloc_n<StepState>(c, c->pool_asm, 1);
     c->cgs = dalloc_n<CgState>(c, c->pool_asm, 1);
     c->max_blocks = (int)blocks_for(c->n, RED_BLOCK) + 1;
@@ -597,7 +710,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     const int NI = c->C.n_iface;
     const int n_int = (int)c->nondeg.size();
     const double dt = c->dt;
-    const unsigned nb = blocks_for(c->n, RED_BLOCK);
 
     // geometry of f^E at every embedded node of the step (independent of T)
     GeomArgs ga{};
@@ -608,12 +720,13 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.use_fixed = 0;
     ga.n_slots = n_int * (P + 1);
     ga.status = &c->st->status;
+    ga.loop_kernels = &c->st->loop_kernels;
     ch.kernel(k_iface_geom, blocks_for((int64_t)NI * ga.n_slots, 128), 128u, ga);
 
     // F^I at a standard node that coincides with t_n (Lobatto)
     for (int j = 1; j <= M; ++j)
         if (std::find(c->nondeg.begin(), c->nondeg.end(), j) == c->nondeg.end())
-            ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->FI[0][j - 1]);
+            ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->FI[0][j - 1]);
 
     auto sdt_row = [&](int m, double* out) {
         for (int j = 0; j < MAX_M; ++j) out[j] = j < M ? dt * W.S[(size_t)(m - 1) * M + j] : 0.0;
@@ -675,7 +788,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ra.partials = c->partials;
         ra.counter = c->counter;
         ra.out = &c->st->residual[k];
-        ch.kernel(k_residual, nb, (unsigned)RED_BLOCK, ra);
+        ch.kernel(k_residual, row_grid(c, k_residual), (unsigned)RED_BLOCK, ra);
     };
 
     // ---- Algorithm 1 (predictor)
@@ -688,7 +801,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         r.g = c->d_genv;
         r.x0 = c->Tstd[m - 1];
         r.pos = c->C.pos;
-        add_solve(c, ch, cg_args(c, dtau, solve++, c->rtol, c->max_iter), r);
+        add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
         BulkArgs b{};
         b.A = c->A;
         b.minv = c->d_minv;
@@ -701,9 +814,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         b.n = c->n;
         b.pos = c->C.pos;
         b.fstar_I = c->fst;
-        ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
+        ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
         substeps(ii, m, RHS_PRED, 0, 0);
-        ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m], c->FI[0][m - 1]);
+        ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m], c->FI[0][m - 1]);
     }
     // ---- Algorithm 2 (sweeps)
     for (int k = 1; k <= K; ++k) {
@@ -723,7 +836,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             r.ihat = c->ihat[so] + (size_t)ii * NI;
             r.pos = c->C.pos;
             r.x0 = c->Tstd[m];
-            add_solve(c, ch, cg_args(c, dtau, solve++, c->rtol, c->max_iter), r);
+            add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
             BulkArgs b{};
             b.A = c->A;
             b.minv = c->d_minv;
@@ -740,16 +853,16 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.n = c->n;
             b.pos = c->C.pos;
             b.fstar_I = c->fst;
-            ch.kernel(k_bulk_endpoint, blocks_for(c->n, 256), 256u, b);
+            ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
             substeps(ii, m, RHS_SWEEP, so, sn);
             if (k < K || c->residuals)
-                ch.kernel(k_fi, nb, 256u, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m],
+                ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m],
                           c->FI[sn][m - 1]);
         }
     }
     if (c->residuals) residual(K & 1, K);
     ch.copy(c->Tn, c->Tstd[M], (size_t)c->n * sizeof(double));
-    ch.kernel(k_heat, nb, (unsigned)RED_BLOCK, (const double*)c->d_mass, (const double*)c->Tn, (int64_t)c->n,
+    ch.kernel(k_heat, row_grid(c, k_heat), (unsigned)RED_BLOCK, (const double*)c->d_mass, (const double*)c->Tn, (int64_t)c->n,
               (int64_t)c->n_fix, c->partials, c->counter, &c->st->heat[0]);
     ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], n_int, NI);
 }
@@ -800,7 +913,8 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
         rep->refinements_total += s.refinements[i];
     }
     rep->status = s.status;
-    rep->kernel_launches = c->eager ? c->eager_kernels : c->fixed_kernels + 3 * rep->cg_iters_total;
+    // graph: kernels outside the loops + those the loop bodies ran (counted on the device)
+    rep->kernel_launches = c->eager ? c->eager_kernels : c->fixed_kernels + s.loop_kernels;
     for (int k = 0; k <= SDC_MAX_SWEEPS; ++k) rep->residual[k] = (c->residuals && k <= c->K_sweeps) ? s.residual[k] : -1.0;
     rep->heat_stand = s.heat[0];
     rep->heat_stock = s.heat[1];
@@ -836,11 +950,14 @@ void ensure_ready(sdc_ctx* c) {
 const char* kernel_name(const void* f) {
     static const std::pair<const void*, const char*> names[] = {
         {(const void*)k_cg_init, "k_cg_init"},         {(const void*)k_cg_spmv, "k_cg_spmv"},
-        {(const void*)k_cg_update, "k_cg_update"},     {(const void*)k_cg_pupdate, "k_cg_pupdate"},
+        {(const void*)k_cg_update, "k_cg_update"},
         {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
         {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_loop, "k_iface_loop"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
+        {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
+        {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_update, "k_mx_update"},
+        {(const void*)k_mx_refine, "k_mx_refine"},
     };
     for (const auto& n : names)
         if (n.first == f) return n.second;
@@ -900,13 +1017,17 @@ sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaMallocHost((void**)&c->st_host, sizeof(StepState)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->done_host, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->done_host, 4 * sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SDC_ERR_CUDA;
     }
     std::memset(c->st_host, 0, sizeof(StepState));
+    if (cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        c->n_sms = 1;
+    }
     *out = c;
     return SDC_OK;
 }
@@ -1029,7 +1150,7 @@ sdc_status sdc_set_scheme(sdc_ctx* c, sdc_nodes nodes, int M, int P, int sweeps,
         require(dt > 0 && std::isfinite(dt), SDC_ERR_ARG, "dt must be positive");
         require(cg_rtol > 0 && cg_rtol < 1, SDC_ERR_ARG, "cg_rtol must be in (0, 1)");
         require(cg_max_iter >= 1, SDC_ERR_ARG, "cg_max_iter must be >= 1");
-        require(precision == SDC_FP64, SDC_ERR_ARG, "only SDC_FP64 is available in this build");
+        require(precision == SDC_FP64 || precision == SDC_MIXED_FP32, SDC_ERR_ARG, "unknown precision");
         require(!(nodes == SDC_NODES_LOBATTO && M < 2), SDC_ERR_ARG, "Lobatto needs M >= 2");
         c->W = make_weights(nodes, M, P, window);
         c->K_sweeps = sweeps;
@@ -1203,7 +1324,7 @@ sdc_status sdc_apply_operator(sdc_ctx* c, double dtau, const double* x, double* 
     return guarded(c, [&] {
         require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
         require(x && y, SDC_ERR_ARG, "null buffer");
-        k_apply_operator<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->A, c->d_mass, dtau, x, y);
+        k_apply_operator<<<row_grid(c, k_apply_operator), RED_BLOCK, 0, c->stream>>>(c->A, c->d_mass, dtau, x, y);
         SDC_CUDA_TRY(cudaGetLastError());
     });
 }
@@ -1224,7 +1345,7 @@ sdc_status sdc_solve(sdc_ctx* c, double dtau, const double* b, double* x, int32_
         r.b_in = b;
         r.x0 = x;
         r.pos = c->C.pos;
-        add_solve(c, ch, cg_args(c, dtau, 0, rtol, max_iter), r);
+        add_implicit_solve(c, ch, dtau, 0, rtol, max_iter, r);
         ch.copy(x, c->X, (size_t)c->n * sizeof(double));
         cudaGraphExec_t ex;
         SDC_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));

@@ -124,9 +124,21 @@ struct ContactDev {
 };
 
 // Scalars of one CG solve (device).
+// Scalars of one CG solve (device). Chronopoulos-Gear recurrences: gamma =
+// (r, u), delta = (A u, u), rr = (r, r) of the current residual; alpha and
+// gamma of the previous iteration are kept for the next step length.
 struct CgState {
-    double rz, alpha, beta, bb, rr, pAp;
-    int iter;
+    double gamma, alpha, beta, bb, rr, delta;
+    int iter;                  // updates applied
+    int done;                  // stop flag (converged or capped)
+    int runs;                  // executions of the SpMV kernel that did work
+    int pad;
+};
+
+// Outer scalars of one mixed-precision solve (FP64 iterative refinement).
+struct MixState {
+    double bb, rr;             // ||b||^2 and ||b - A x||^2 (FP64)
+    int passes;                // refinement passes done
     int done;
 };
 
@@ -136,7 +148,7 @@ struct StepState {
     double dt;
     long long n_done;          // macro steps completed since set_temperature
     int status;                // sticky sdc_status
-    int pad;
+    int loop_kernels;          // kernels run inside the CG/refinement loops of this step
     int cg_iters[MAX_SOLVES];
     int refinements[MAX_SOLVES];
     double residual[SDC_MAX_SWEEPS + 1];

@@ -29,37 +29,96 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // sum_k K[row, k] x[k] over the sliced-ELL row (padding entries carry 0).
-__device__ __forceinline__ double ell_row(const EllDev& A, int64_t row, const double* __restrict__ x) {
+// Entries are taken CH at a time: the CH value and column loads of a chunk
+// are all issued before its CH gathers of x, so a row costs ceil(w / CH)
+// dependent memory round trips instead of w. Summation stays in entry order.
+template <int CH, typename V, typename X>
+__device__ __forceinline__ V ell_row_t(const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                                       const V* __restrict__ val, int64_t row, const X* __restrict__ x) {
     const int64_t s = row >> 5;
     const int lane = (int)(row & 31);
-    const int64_t b = A.slice_ptr[s], e = A.slice_ptr[s + 1];
-    double acc = 0.0;
-#pragma unroll 4
-    for (int64_t k = b + lane; k < e; k += SLICE) acc = fma(__ldg(A.val + k), __ldg(x + __ldg(A.col + k)), acc);
+    const int64_t b = slice_ptr[s], e = slice_ptr[s + 1];
+    V acc = V(0);
+    for (int64_t k0 = b + lane; k0 < e; k0 += (int64_t)CH * SLICE) {
+        V v[CH];
+        int c[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int64_t k = k0 + (int64_t)j * SLICE;
+            const bool in = k < e;
+            v[j] = in ? __ldg(val + k) : V(0);
+            c[j] = in ? __ldg(col + k) : 0;
+        }
+        X xv[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) xv[j] = __ldg(x + c[j]);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) acc = fma(v[j], (V)xv[j], acc);
+    }
     return acc;
 }
 
+__device__ __forceinline__ double ell_row(const EllDev& A, int64_t row, const double* __restrict__ x) {
+    return ell_row_t<8, double, double>(A.slice_ptr, A.col, A.val, row, x);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Block-reduce NQ values, publish per-block partials, and let the last block
-// to finish combine them in a fixed order into out[0..NQ). Returns true in
-// every thread of that last block, after out[] is written.
-template <int NQ, bool MAX>
-__device__ bool reduce_last(double (&v)[NQ], double* partials, unsigned int* counter, double* out) {
+// to finish combine them in a fixed order into out[0..NQ). The warp stage
+// runs in the type of v (FP32 for the FP32 kernels: GB300's FP64 pipe is
+// narrow, and a warp butterfly costs five adds per value and lane); block and
+// grid stages run in FP64. Returns true in every thread of that last block,
+// after out[] is written.
+template <int NQ, bool MAX, typename W>
+__device__ bool reduce_last(W (&v)[NQ], double* partials, unsigned int* counter, double* out) {
     __shared__ double sh[NQ][32];
     __shared__ int am_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if constexpr (sizeof(W) == sizeof(float)) {
+        // FP32 butterfly in every warp, then FP64 over the warp sums
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = MAX ? warp_max(v[q]) : warp_sum(v[q]);
-    if (lane == 0)
+        for (int q = 0; q < NQ; ++q) v[q] = MAX ? warp_max(v[q]) : warp_sum(v[q]);
+        if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) sh[q][warp] = v[q];
-    __syncthreads();
+            for (int q = 0; q < NQ; ++q) sh[q][warp] = (double)v[q];
+        __syncthreads();
+        if (warp == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double t = lane < nw ? sh[q][lane] : (MAX ? -1.0 : 0.0);
+                sh[q][lane] = MAX ? warp_max(t) : warp_sum(t);
+            }
+    } else {
+        // FP64: the block's values go to shared memory as columns of 32; warp 0 alone sums the
+        // columns, then one butterfly (about a third of the FP64 warp instructions of a
+        // butterfly in every warp)
+        __shared__ double colv[NQ][RED_BLOCK];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) colv[q][threadIdx.x] = v[q];
+        __syncthreads();
+        if (warp == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                double t = colv[q][lane];
+                for (int w = 1; w < nw; ++w) t = MAX ? fmax(t, colv[q][lane + 32 * w]) : t + colv[q][lane + 32 * w];
+                sh[q][lane] = MAX ? warp_max(t) : warp_sum(t);
+            }
+    }
     if (warp == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            double t = lane < nw ? sh[q][lane] : (MAX ? -1.0 : 0.0);
-            t = MAX ? warp_max(t) : warp_sum(t);
-            if (lane == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = t;
-        }
+        for (int q = 0; q < NQ; ++q)
+            if (lane == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = sh[q][0];
         if (lane == 0) {
             __threadfence();
             const unsigned int prev = atomicAdd(counter, 1u);
@@ -69,6 +128,7 @@ __device__ bool reduce_last(double (&v)[NQ], double* partials, unsigned int* cou
     __syncthreads();
     if (!am_last) return false;
     __threadfence();
+    double dv[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         double t = MAX ? -1.0 : 0.0;
@@ -76,12 +136,12 @@ __device__ bool reduce_last(double (&v)[NQ], double* partials, unsigned int* cou
             const double p = __ldcg(partials + (size_t)q * gridDim.x + i);
             t = MAX ? fmax(t, p) : t + p;
         }
-        v[q] = MAX ? warp_max(t) : warp_sum(t);
+        dv[q] = MAX ? warp_max(t) : warp_sum(t);
     }
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) sh[q][warp] = v[q];
+        for (int q = 0; q < NQ; ++q) sh[q][warp] = dv[q];
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -96,128 +156,337 @@ __device__ bool reduce_last(double (&v)[NQ], double* partials, unsigned int* cou
     return true;
 }
 
+// FP32 row of the sliced ELL: sum_k K32[row, k] x[k]
+__device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const float* __restrict__ x) {
+    return ell_row_t<8, float, float>(A.slice_ptr, A.col, A.val32, row, x);
+}
+
+// Row kernels take any grid: thread t of block b covers rows
+// (b * rpt + j) * blockDim.x + t, j < rpt, so each warp takes whole 32-row
+// slices and a thread's reduction terms are summed before the block stage.
+__device__ __forceinline__ int rows_per_thread(int64_t n) {
+    const int64_t t = (int64_t)gridDim.x * blockDim.x;
+    return (int)((n + t - 1) / t);
+}
+
+__device__ __forceinline__ int64_t row_of(int j, int rpt) {
+    return ((int64_t)blockIdx.x * rpt + j) * blockDim.x + threadIdx.x;
+}
+
 // ------------------------------------------------------------------ operator
 
 // y = m .* x + dtau K x
 __global__ void k_apply_operator(EllDev A, const double* __restrict__ mass, double dtau,
                                  const double* __restrict__ x, double* __restrict__ y) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < A.n) y[i] = fma(dtau, ell_row(A, i, x), mass[i] * x[i]);
+    const int rpt = rows_per_thread(A.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= A.n) break;
+        y[i] = fma(dtau, ell_row(A, i, x), mass[i] * x[i]);
+    }
 }
 
 // F = -K T + g   (f^I(T) + g of Eq. ivp)
 __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < A.n) F[i] = g[i] - ell_row(A, i, T);
+    const int rpt = rows_per_thread(A.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= A.n) break;
+        F[i] = g[i] - ell_row(A, i, T);
+    }
 }
 
 // ------------------------------------------------------------------ Jacobi-PCG
 
 // Right-hand side of the implicit stage (Algorithm 1: m T_{m-1} + dtau g;
 // Algorithm 2: m T^{k+1}_{m-1} - dtau f^I(T^k_m) + I_{m-1}^m), the initial
-// residual r = b - (m x0 + dtau K x0), z = D r, p = z, and the scalars.
+// residual r = b - (m x0 + dtau K x0), u = D r, and the stop test.
 __global__ void k_cg_init(CgArgs a, RhsArgs r) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {0.0, 0.0, 0.0};
-    if (i < a.n) {
-        const double m = a.mass[i];
-        double b;
-        if (r.mode == RHS_GIVEN) {
-            b = r.b_in[i];
-        } else if (r.mode == RHS_PRED) {
-            b = m * r.Tprev[i] + a.dtau * r.g[i];
-        } else {
-            double I = 0.0;
-            for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
-            const int pa = r.pos[i];
-            if (pa >= 0) I += r.ihat[pa];
-            b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
-        }
-        const double x0 = r.x0[i];
-        const double Ax = fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
-        const double res = b - Ax;
-        const double d = 1.0 / (m + a.dtau * a.diagK[i]);
-        const double z = res * d;
-        a.X[i] = x0;
-        a.R[i] = res;
-        a.D[i] = d;
-        a.Z[i] = z;
-        a.P[i] = z;
-        v[0] = res * z;
-        v[1] = b * b;
-        v[2] = res * res;
-    }
-    double out[3];
-    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
-        a.cg->rz = out[0];
-        a.cg->bb = out[1];
-        a.cg->rr = out[2];
-        a.cg->iter = 0;
-        a.cg->beta = 0.0;
-        *a.iters_out = 0;
-        const bool conv = out[2] <= a.rtol2 * out[1];
-        a.cg->done = conv ? 1 : 0;
-        if (conv && a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
-    }
-}
-
-// y = m .* p + dtau K p; alpha = (r, z) / (p, y)
-__global__ void k_cg_spmv(CgArgs a) {
-    if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v[1] = {0.0};
-    if (i < a.n) {
-        const double p = a.P[i];
-        const double y = fma(a.dtau, ell_row(a.A, i, a.P), a.mass[i] * p);
-        a.Y[i] = y;
-        v[0] = p * y;
-    }
-    double out[1];
-    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
-        a.cg->pAp = out[0];
-        a.cg->alpha = a.cg->rz / out[0];
-    }
-}
-
-// x += alpha p; r -= alpha y; z = D r; beta = (r, z)_new / (r, z)_old; stop test
-__global__ void k_cg_update(CgArgs a) {
-    if (a.cg->done) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double alpha = a.cg->alpha;
     double v[2] = {0.0, 0.0};
-    if (i < a.n) {
-        const double p = a.P[i];
-        a.X[i] = fma(alpha, p, a.X[i]);
-        const double res = fma(-alpha, a.Y[i], a.R[i]);
-        a.R[i] = res;
-        const double z = res * a.D[i];
-        a.Z[i] = z;
-        v[0] = res * z;
-        v[1] = res * res;
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const double m = a.mass[i];
+            double b;
+            if (r.mode == RHS_GIVEN) {
+                b = r.b_in[i];
+            } else if (r.mode == RHS_PRED) {
+                b = m * r.Tprev[i] + a.dtau * r.g[i];
+            } else {
+                double I = 0.0;
+                for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
+                const int pa = r.pos[i];
+                if (pa >= 0) I += r.ihat[pa];
+                b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
+            }
+            const double x0 = r.x0[i];
+            const double Ax = fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
+            const double res = b - Ax;
+            const double d = 1.0 / (m + a.dtau * a.diagK[i]);
+            a.X[i] = x0;
+            a.R[i] = res;
+            a.D[i] = d;
+            a.U[i] = res * d;
+            v[0] += b * b;
+            v[1] += res * res;
     }
     double out[2];
     if (reduce_last<2, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
-        s->beta = out[0] / s->rz;
-        s->rz = out[0];
+        s->bb = out[0];
         s->rr = out[1];
-        s->iter += 1;
-        *a.iters_out = s->iter;
-        const bool conv = out[1] <= a.rtol2 * s->bb;
+        s->iter = 0;
+        s->runs = 0;
+        s->beta = 0.0;
+        *a.iters_out = 0;
+        const bool conv = out[1] <= a.rtol2 * out[0];
+        s->done = conv ? 1 : 0;
+        if (conv && a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
+    }
+}
+
+// w = m u + dtau K u; gamma = (r, u), delta = (w, u), rr = (r, r). The last
+// block tests ||r|| <= rtol ||b|| (stop) or sets the step lengths:
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev).
+__global__ void k_cg_spmv(CgArgs a) {
+    if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
+    double v[3] = {0.0, 0.0, 0.0};
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const double u = a.U[i];
+            const double w = fma(a.dtau, ell_row(a.A, i, a.U), a.mass[i] * u);
+            const double res = a.R[i];
+            a.W[i] = w;
+            v[0] += res * u;
+            v[1] += w * u;
+            v[2] += res * res;
+    }
+    double out[3];
+    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        CgState* s = a.cg;
+        s->runs += 1;
+        *a.loop_kernels += 2;
+        const double gamma = out[0], delta = out[1];
+        s->rr = out[2];
+        const bool conv = out[2] <= a.rtol2 * s->bb;
         if (conv || s->iter >= a.max_iter) {
             s->done = 1;
             if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
             if (a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
+            return;
         }
+        if (s->iter == 0) {
+            s->beta = 0.0;
+            s->alpha = gamma / delta;
+        } else {
+            const double beta = gamma / s->gamma;
+            s->beta = beta;
+            s->alpha = gamma / (delta - beta * gamma / s->alpha);
+        }
+        s->gamma = gamma;
+        s->delta = delta;
+        s->iter += 1;
+        *a.iters_out = s->iter;
     }
 }
 
-// p = z + beta p
-__global__ void k_cg_pupdate(CgArgs a) {
+// p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D r
+__global__ void k_cg_update(CgArgs a) {
     if (a.cg->done) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double beta = a.cg->beta;
-    if (i < a.n) a.P[i] = fma(beta, a.P[i], a.Z[i]);
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+        const double alpha = a.cg->alpha, beta = a.cg->beta;
+        const bool first = a.cg->iter == 1;
+        const double u = a.U[i], w = a.W[i];
+        const double p = first ? u : fma(beta, a.P[i], u);
+        const double sp = first ? w : fma(beta, a.S[i], w);
+        a.P[i] = p;
+        a.S[i] = sp;
+        a.X[i] = fma(alpha, p, a.X[i]);
+        const double res = fma(-alpha, sp, a.R[i]);
+        a.R[i] = res;
+        a.U[i] = res * a.D[i];
+    }
+}
+
+// ------------------------------------------------------------------ mixed precision (iterative refinement)
+
+// FP64: b of the implicit stage (as k_cg_init), x = x0, r = b - A x0, and
+// the outer stop test; FP32 inverse diagonal for the inner solves.
+__global__ void k_mx_init(MixArgs a, RhsArgs r) {
+    double v[2] = {0.0, 0.0};
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const double m = a.mass[i];
+            double b;
+            if (r.mode == RHS_GIVEN) {
+                b = r.b_in[i];
+            } else if (r.mode == RHS_PRED) {
+                b = m * r.Tprev[i] + a.dtau * r.g[i];
+            } else {
+                double I = 0.0;
+                for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
+                const int pa = r.pos[i];
+                if (pa >= 0) I += r.ihat[pa];
+                b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
+            }
+            const double x0 = r.x0[i];
+            const double res = b - fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
+            a.B[i] = b;
+            a.X[i] = x0;
+            a.R[i] = res;
+            a.Dinv[i] = 1.0f / (float)(m + a.dtau * a.diagK[i]);
+            v[0] += b * b;
+            v[1] += res * res;
+    }
+    double out[2];
+    if (reduce_last<2, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        MixState* s = a.ms;
+        s->bb = out[0];
+        s->rr = out[1];
+        s->passes = 0;
+        *a.iters_out = 0;
+        *a.refine_out = 0;
+        const bool conv = out[1] <= a.rtol2 * out[0];
+        s->done = conv ? 1 : 0;
+        if (conv && a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
+    }
+}
+
+// Start of one refinement pass: r32 = r, d = 0, u = D r32. The inner target
+// is the larger of a fixed FP32 reduction and what the outer test still
+// needs (with a margin for the FP32 recurrence), so a pass stops as soon as
+// one more FP64 residual can meet ||b - A x|| <= rtol ||b||.
+__global__ void k_mx_inner_init(MixArgs a) {
+    float v[1] = {0.0f};
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const float res = (float)a.R[i];
+            a.Rl[i] = res;
+            a.Dl[i] = 0.0f;
+            a.Ul[i] = res * a.Dinv[i];
+            v[0] += res * res;
+    }
+    double out[1];
+    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        CgState* s = a.cg;
+        s->bb = fmax(a.inner_rtol2 * out[0], 0.1 * a.rtol2 * a.ms->bb);
+        s->rr = out[0];
+        s->beta = 0.0;
+        s->iter = 0;
+        s->runs = 0;
+        const bool zero = !(out[0] > 0.0);
+        s->done = zero ? 1 : 0;
+        if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, zero ? 0u : 1u);
+    }
+}
+
+// FP32: w = m u + dtau K32 u; gamma, delta, rr; inner stop test or step lengths
+__global__ void k_mx_spmv(MixArgs a) {
+    if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
+    float v[3] = {0.0f, 0.0f, 0.0f};
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const float u = a.Ul[i];
+            const float w = fmaf((float)a.dtau, ell_row32(a.A, i, a.Ul), a.mass32[i] * u);
+            const float res = a.Rl[i];
+            a.Wl[i] = w;
+            v[0] += res * u;
+            v[1] += w * u;
+            v[2] += res * res;
+    }
+    double out[3];
+    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        CgState* s = a.cg;
+        s->runs += 1;
+        *a.loop_kernels += 2;
+        const double gamma = out[0], delta = out[1];
+        s->rr = out[2];
+        if (out[2] <= s->bb || s->iter >= a.max_iter) {
+            s->done = 1;
+            if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+            return;
+        }
+        if (s->iter == 0) {
+            s->beta = 0.0;
+            s->alpha = gamma / delta;
+        } else {
+            const double beta = gamma / s->gamma;
+            s->beta = beta;
+            s->alpha = gamma / (delta - beta * gamma / s->alpha);
+        }
+        s->gamma = gamma;
+        s->delta = delta;
+        s->iter += 1;
+        *a.iters_out += 1;
+    }
+}
+
+// FP32: p = u + beta p; s = w + beta s; d += alpha p; r -= alpha s; u = D r
+__global__ void k_mx_update(MixArgs a) {
+    if (a.cg->done) return;
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+        const float alpha = (float)a.cg->alpha, beta = (float)a.cg->beta;
+        const bool first = a.cg->iter == 1;
+        const float u = a.Ul[i], w = a.Wl[i];
+        const float p = first ? u : fmaf(beta, a.Pl[i], u);
+        const float sp = first ? w : fmaf(beta, a.Sl[i], w);
+        a.Pl[i] = p;
+        a.Sl[i] = sp;
+        a.Dl[i] = fmaf(alpha, p, a.Dl[i]);
+        const float res = fmaf(-alpha, sp, a.Rl[i]);
+        a.Rl[i] = res;
+        a.Ul[i] = res * a.Dinv[i];
+    }
+}
+
+// FP64 row of K applied to the FP32 correction
+__device__ __forceinline__ double ell_row_f32in(const EllDev& A, int64_t row, const float* __restrict__ x) {
+    return ell_row_t<8, double, float>(A.slice_ptr, A.col, A.val, row, x);
+}
+
+// FP64 end of a refinement pass: x += d; r -= (m d + dtau K d), i.e. the
+// residual b - A x of the corrected iterate, formed in FP64; outer stop test.
+__global__ void k_mx_refine(MixArgs a) {
+    double v[1] = {0.0};
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const double d = (double)a.Dl[i];
+            a.X[i] += d;
+            const double res = a.R[i] - fma(a.dtau, ell_row_f32in(a.A, i, a.Dl), a.mass[i] * d);
+            a.R[i] = res;
+            v[0] += res * res;
+    }
+    double out[1];
+    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+        MixState* s = a.ms;
+        s->rr = out[0];
+        s->passes += 1;
+        *a.loop_kernels += 2;
+        *a.refine_out = s->passes;
+        const bool conv = out[0] <= a.rtol2 * s->bb;
+        if (conv || s->passes >= a.max_refine) {
+            s->done = 1;
+            if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
+            if (a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ endpoint
@@ -229,22 +498,25 @@ __global__ void k_cg_pupdate(CgArgs a) {
 // (sum_p stil_{m,p,j} = s_{m,j}). Contact rows are overwritten by the
 // substep loop that follows.
 __global__ void k_bulk_endpoint(BulkArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const double KX = ell_row(a.A, i, a.X);
-    double incr, fstar;
-    if (a.mode == RHS_PRED) {
-        fstar = a.g[i] - KX;
-        incr = a.dtau * fstar;
-    } else {
-        fstar = -KX - (a.FIm[i] - a.g[i]);
-        double I = 0.0;
-        for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
-        incr = fma(a.dtau, fstar, I);
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+        const double KX = ell_row(a.A, i, a.X);
+        double incr, fstar;
+        if (a.mode == RHS_PRED) {
+            fstar = a.g[i] - KX;
+            incr = a.dtau * fstar;
+        } else {
+            fstar = -KX - (a.FIm[i] - a.g[i]);
+            double I = 0.0;
+            for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
+            incr = fma(a.dtau, fstar, I);
+        }
+        a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
+        const int pa = a.pos[i];
+        if (pa >= 0) a.fstar_I[pa] = fstar;
     }
-    a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
-    const int pa = a.pos[i];
-    if (pa >= 0) a.fstar_I[pa] = fstar;
 }
 
 // ------------------------------------------------------------------ contact geometry
@@ -287,6 +559,7 @@ __global__ void k_iface_geom(GeomArgs g) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)NI * g.n_slots) return;
     const int s = (int)(gid / NI), a = (int)(gid % NI);
+    if (gid == 0 && g.loop_kernels) *g.loop_kernels = 0;  // first kernel of a macro step
     double tau;
     if (g.use_fixed) {
         tau = g.t_fixed;
@@ -576,21 +849,23 @@ __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
 
 // r^k = max_m || m T_m - m T_n - sum_{j<=m} I_{j-1}^j ||_inf (Eq. residual)
 __global__ void k_residual(ResidualArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
-    if (i < a.n) {
-        const double m = a.mass[i];
-        const double tn = a.Tn[i];
-        const int pa = a.pos[i];
-        double cum = 0.0, r = 0.0;
-        for (int mm = 0; mm < a.M; ++mm) {
-            double I = 0.0;
-            for (int j = 0; j < a.M; ++j) I = fma(a.Sdt[mm][j], a.FI[j][i], I);
-            if (pa >= 0 && a.ihat[mm]) I += a.ihat[mm][pa];
-            cum += I;
-            r = fmax(r, fabs(m * a.Tm[mm][i] - m * tn - cum));
-        }
-        v[0] = r;
+    const int rpt = rows_per_thread(a.n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= a.n) break;
+            const double m = a.mass[i];
+            const double tn = a.Tn[i];
+            const int pa = a.pos[i];
+            double cum = 0.0, r = 0.0;
+            for (int mm = 0; mm < a.M; ++mm) {
+                double I = 0.0;
+                for (int j = 0; j < a.M; ++j) I = fma(a.Sdt[mm][j], a.FI[j][i], I);
+                if (pa >= 0 && a.ihat[mm]) I += a.ihat[mm][pa];
+                cum += I;
+                r = fmax(r, fabs(m * a.Tm[mm][i] - m * tn - cum));
+            }
+            v[0] = fmax(v[0], r);
     }
     double out[1];
     if (reduce_last<1, true>(v, a.partials, a.counter, out) && threadIdx.x == 0) *a.out = out[0];
@@ -599,11 +874,13 @@ __global__ void k_residual(ResidualArgs a) {
 // heat[0] = sum over stand rows of m T, heat[1] = stock rows
 __global__ void k_heat(const double* __restrict__ mass, const double* __restrict__ T, int64_t n, int64_t n_fix,
                        double* partials, unsigned int* counter, double* heat) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v[2] = {0.0, 0.0};
-    if (i < n) {
-        const double h = mass[i] * T[i];
-        if (i < n_fix) v[0] = h; else v[1] = h;
+    const int rpt = rows_per_thread(n);
+    for (int jr = 0; jr < rpt; ++jr) {
+        const int64_t i = row_of(jr, rpt);
+        if (i >= n) break;
+            const double h = mass[i] * T[i];
+            if (i < n_fix) v[0] += h; else v[1] += h;
     }
     double out[2];
     if (reduce_last<2, false>(v, partials, counter, out) && threadIdx.x == 0) {

@@ -15,15 +15,18 @@ constexpr int IFACE_MAX_NI = 14336;
 
 enum RhsMode { RHS_GIVEN = 0, RHS_PRED = 1, RHS_SWEEP = 2 };
 
-// One Jacobi-PCG solve of (diag(m) + dtau K) x = b.
+// One Jacobi-PCG solve of (diag(m) + dtau K) x = b in the Chronopoulos-Gear
+// arrangement: per iteration one kernel forms w = A u and the three dot
+// products (one global reduction), a second updates the vectors.
 struct CgArgs {
     EllDev A;
     const double* mass;
     const double* diagK;
     double dtau;
     int64_t n;
-    double *X, *R, *Z, *P, *Y, *D;   // iterate, residual, preconditioned residual, direction, A p, 1/diag
+    double *X, *R, *U, *P, *W, *S, *D;  // iterate, residual, u = D r, direction, A u, A p, 1/diag
     CgState* cg;
+    int* loop_kernels;              // StepState::loop_kernels
     double* partials;
     unsigned int* counter;
     int* iters_out;                 // iteration count of this solve
@@ -31,6 +34,32 @@ struct CgArgs {
     int max_iter;
     double rtol2;
     unsigned long long handle;      // cudaGraphConditionalHandle of the enclosing while node
+};
+
+// One mixed-precision solve of (diag(m) + dtau K) x = b: FP64 residuals
+// r = b - A x around FP32 Jacobi-PCG solves of A d = r (iterative refinement).
+struct MixArgs {
+    EllDev A;                       // val (FP64) for residuals, val32 for the inner solves
+    const double* mass;
+    const float* mass32;
+    const double* diagK;
+    double dtau;
+    int64_t n;
+    double *X, *R, *B;              // FP64 iterate, residual, right-hand side
+    float *Dl, *Rl, *Ul, *Pl, *Wl, *Sl, *Dinv;   // FP32 correction, residual, u, direction, A u, A p, 1/diag
+    int* loop_kernels;              // StepState::loop_kernels
+    CgState* cg;                    // inner scalars (bb holds the inner initial ||r||^2)
+    MixState* ms;                   // outer scalars
+    double* partials;
+    unsigned int* counter;
+    int* iters_out;                 // inner iterations of this solve (all passes)
+    int* refine_out;                // refinement passes of this solve
+    int* status;
+    int max_iter;                   // per inner solve
+    int max_refine;
+    double rtol2;                   // outer: ||b - A x||^2 <= rtol2 ||b||^2
+    double inner_rtol2;             // inner: ||r||^2 <= inner_rtol2 ||r_0||^2
+    unsigned long long h_outer, h_inner;
 };
 
 // Right-hand side of the implicit stage.
@@ -84,6 +113,7 @@ struct GeomArgs {
     int use_fixed;
     int n_slots;
     int* status;
+    int* loop_kernels;        // reset here (the step's first kernel); NULL outside a step
 };
 
 // T-independent part of every substep increment of one interval
@@ -150,7 +180,11 @@ __global__ void k_fi(EllDev A, const double* g, const double* T, double* F);
 __global__ void k_cg_init(CgArgs a, RhsArgs r);
 __global__ void k_cg_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);
-__global__ void k_cg_pupdate(CgArgs a);
+__global__ void k_mx_init(MixArgs a, RhsArgs r);
+__global__ void k_mx_inner_init(MixArgs a);
+__global__ void k_mx_spmv(MixArgs a);
+__global__ void k_mx_update(MixArgs a);
+__global__ void k_mx_refine(MixArgs a);
 __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_iface_geom(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,

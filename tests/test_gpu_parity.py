@@ -39,12 +39,12 @@ def _solver(mach, **kw):
     return s
 
 
-def _compare(got, ref, T0, tag):
+def _compare(got, ref, T0, tag, rel_t=REL_T, rel_rise=REL_RISE):
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     d = np.linalg.norm(ref - T0)
     rise = np.linalg.norm(got - ref) / d if d > 0 else np.linalg.norm(got - ref)
-    assert rel <= REL_T, (tag, rel)
-    assert rise <= REL_RISE, (tag, rise)
+    assert rel <= rel_t, (tag, rel)
+    assert rise <= rel_rise, (tag, rise)
     return rel, rise
 
 
@@ -86,8 +86,8 @@ def test_operator_solve_and_contact_components(torch):
         assert np.abs(fe - ref).max() <= 1e-12 * np.abs(ref).max(), t
 
 
-def _run_parity(mach, n_steps, residuals=False, T0=None):
-    s = _solver(mach, residuals=residuals, T0=T0)
+def _run_parity(mach, n_steps, residuals=False, T0=None, precision="fp64", rel_t=REL_T, rel_rise=REL_RISE):
+    s = _solver(mach, residuals=residuals, T0=T0, precision=precision)
     prob = MachineProblem(mach)
     sc = mach.scheme
     W = mrsdc_weights(sc.nodes, sc.M, sc.P, sc.window)
@@ -98,7 +98,7 @@ def _run_parity(mach, n_steps, residuals=False, T0=None):
         rep = s.step(report=True)
         T, r = mrsdc_step(prob, T, mach.t0 + n * sc.dt, sc.dt, W, sc.sweeps, want_residuals=residuals)
         got = s.temperature()
-        rel, rise = _compare(got, T, start, f"step {n}")
+        rel, rise = _compare(got, T, start, f"step {n}", rel_t, rel_rise)
         worst = (max(worst[0], rel), max(worst[1], rise))
         assert rep["status"] == 0
         if residuals:
@@ -229,8 +229,72 @@ def test_eager_kernel_timing_counts_every_launch(torch):
     rep = s.step(report=True)
     kt = s.kernel_times()
     assert sum(n for n, _ in kt.values()) == rep["kernel_launches"]
-    assert kt["k_cg_spmv"][0] == rep["cg_iters_total"]
+    # one SpMV per update plus the one whose residual test stops each solve
+    assert kt["k_cg_spmv"][0] == kt["k_cg_update"][0]
+    assert rep["cg_iters_total"] <= kt["k_cg_spmv"][0] <= rep["cg_iters_total"] + rep["n_solves"]
     assert kt["k_iface_loop"][0] == rep["n_solves"]
     assert all(ms > 0 for _, ms in kt.values())
     assert rep["contact_cluster"] >= 1
     s.close()
+
+
+# Mixed precision (FP32 inner CG inside FP64 iterative refinement). The stated
+# bar is rel-L2 <= 1e-6 against the FP64 oracle per macro step; the FP64 outer
+# residual to cg_rtol keeps the result far inside it, so the rise metric is
+# checked at 1e-6 as well.
+REL_MIXED = 1e-6
+
+
+def test_mixed_config0_full_horizon(torch):
+    mach = machine_config(0)
+    worst = _run_parity(mach, 60, precision="mixed", rel_t=REL_MIXED, rel_rise=REL_MIXED)
+    assert worst[0] <= REL_MIXED
+
+
+@pytest.mark.parametrize("nodes,M,P,K,window", [("radau_right", 4, 8, 4, 0), ("lobatto", 3, 20, 3, 0),
+                                                 ("equi_noleft", 3, 2, 2, 2)])
+def test_mixed_schemes_on_tiny_machine(torch, nodes, M, P, K, window):
+    mach = with_scheme(tiny_machine(z0=0.37, amp=0.21, period=1.7), nodes=nodes, M=M, P=P, sweeps=K,
+                       window=window, dt=0.8)
+    rng = np.random.default_rng(6)
+    T0 = 20.0 + rng.standard_normal(mach.n_dof)
+    _run_parity(mach, 4, residuals=True, T0=T0, precision="mixed", rel_t=REL_MIXED, rel_rise=REL_MIXED)
+
+
+def test_mixed_solve_component_and_refinement(torch):
+    mach = machine_config(0)
+    s = _solver(mach, precision="mixed")
+    prob = MachineProblem(mach)
+    rng = np.random.default_rng(12)
+    b = prob.mass * (20.0 + rng.standard_normal(s.n))
+    xs, it = s.solve(0.5, b, np.full(s.n, 20.0))
+    A = (sp.diags(prob.mass) + 0.5 * prob.K).toarray()
+    xd = np.linalg.solve(A, b)
+    assert it > 0
+    # FP64 outer residual to 1e-12: the solution is FP64-accurate, not FP32-accurate
+    assert np.abs(xs.cpu().numpy() - xd).max() <= 1e-10 * np.abs(xd).max()
+    rep = s.step(report=True)
+    assert rep["refinements_total"] >= rep["n_solves"] - 1
+    s.close()
+
+
+def test_mixed_config1_two_macro_steps(torch):
+    mach = machine_config(1)
+    _run_parity(mach, 2, precision="mixed", rel_t=REL_MIXED, rel_rise=REL_MIXED)
+
+
+def test_mixed_eager_matches_graph(torch):
+    mach = machine_config(0)
+    a = _solver(mach, precision="mixed")
+    b = _solver(mach, precision="mixed")
+    b.set_execution(True)
+    b.set_kernel_timing(True)
+    for _ in range(3):
+        ra = a.step(report=True)
+        rb = b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    assert ra["cg_iters_total"] == rb["cg_iters_total"]
+    assert ra["refinements_total"] == rb["refinements_total"]
+    assert ra["kernel_launches"] == rb["kernel_launches"]
+    kt = b.kernel_times()
+    assert kt["k_mx_spmv"][0] > 0 and "k_cg_spmv" not in kt
