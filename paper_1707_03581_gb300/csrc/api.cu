@@ -81,7 +81,9 @@ struct sdc_ctx {
     double* fe[2] = {nullptr, nullptr};
     double* ihat[2] = {nullptr, nullptr};
     double *cpre = nullptr, *fst = nullptr;
+    double* fe_base = nullptr;      // mixed: f^E(T_{m-1}) at the interval's embedded nodes
     int iface_cluster = 0;          // CTAs of the substep-loop cluster
+    int iface_chunk = 0;            // replica slots per CTA of that cluster
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
     double *w_Stil = nullptr, *w_Semb = nullptr, *w_Shat = nullptr, *w_emb = nullptr, *w_slot = nullptr;
@@ -160,11 +162,9 @@ void drop_graph(sdc_ctx* c) {
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-// Grid of a row kernel (blocks of RED_BLOCK threads) over the context's n
-// rows: one row per thread. Row kernels also accept smaller grids (each
-// thread then loops over several rows); measured on GB300 at 313k rows, a
-// one-wave grid with several rows per thread was no faster for the FP32 SpMV
-// and slower for the FP64 one, whose rows then run one after another.
+// Grid of a row kernel (blocks of RED_BLOCK threads): one row per thread.
+// Measured on GB300 at 313k rows, grids of one wave with several rows per
+// thread were no faster for the FP32 SpMV and slower for the FP64 one.
 template <class F>
 unsigned row_grid(sdc_ctx* c, F* kernel) {
     (void)kernel;
@@ -221,6 +221,25 @@ struct Chain {
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
         p.sharedMemBytes = 0;
+        p.kernelParams = params;
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        last = nd;
+    }
+    template <typename... KArgs>
+    void kernel_2d(void (*f)(KArgs...), dim3 grid, dim3 block, KArgs... args) {
+        void* params[] = {(void*)&args...};
+        ++kernels;
+        if (is_eager) {
+            const int ev = begin_timed((const void*)f);
+            SDC_CUDA_TRY(cudaLaunchKernel((const void*)f, grid, block, params, 0, eager));
+            end_timed(ev);
+            return;
+        }
+        cudaKernelNodeParams p{};
+        p.func = (void*)f;
+        p.gridDim = grid;
+        p.blockDim = block;
         p.kernelParams = params;
         cudaGraphNode_t nd;
         SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
@@ -557,6 +576,30 @@ void do_assemble(sdc_ctx* c) {
         rinv[2 * f + 1] = 1.0 / (H.rect[4 * f + 3] - H.rect[4 * f + 1]);
     }
     C.rinv = reinterpret_cast<const double2*>(upload(c, c->pool_asm, rinv));
+    {
+        // bounding boxes: per contact DOF (its faces) and per body (all its contact faces)
+        std::vector<double> dbox((size_t)4 * C.n_iface);
+        double bb[2][4] = {{1e300, 1e300, -1e300, -1e300}, {1e300, 1e300, -1e300, -1e300}};
+        for (int a = 0; a < C.n_iface; ++a) {
+            double b4[4] = {1e300, 1e300, -1e300, -1e300};
+            for (int e = H.inc_ptr[a]; e < H.inc_ptr[a + 1]; ++e) {
+                const double* r = &H.rect[4 * (size_t)H.inc_quad[e]];
+                b4[0] = std::min(b4[0], r[0]);
+                b4[1] = std::min(b4[1], r[1]);
+                b4[2] = std::max(b4[2], r[2]);
+                b4[3] = std::max(b4[3], r[3]);
+            }
+            double* bd = bb[a >= C.n_iface_fix ? 1 : 0];
+            for (int k = 0; k < 4; ++k) dbox[4 * (size_t)a + k] = b4[k];
+            bd[0] = std::min(bd[0], b4[0]);
+            bd[1] = std::min(bd[1], b4[1]);
+            bd[2] = std::max(bd[2], b4[2]);
+            bd[3] = std::max(bd[3], b4[3]);
+        }
+        C.dof_box = reinterpret_cast<const Rect4*>(upload(c, c->pool_asm, dbox));
+        C.box_fix = Rect4{bb[0][0], bb[0][1], bb[0][2], bb[0][3]};
+        C.box_mov = Rect4{bb[1][0], bb[1][1], bb[1][2], bb[1][3]};
+    }
     C.inc_ptr = upload(c, c->pool_asm, H.inc_ptr);
     C.inc_quad = upload(c, c->pool_asm, H.inc_quad);
     C.inc_code = upload(c, c->pool_asm, H.inc_code);
@@ -568,6 +611,8 @@ void do_assemble(sdc_ctx* c) {
         d.ov = b.ov;
         d.bu = b.bu;
         d.bv = b.bv;
+        d.ibu = 1.0 / b.bu;
+        d.ibv = 1.0 / b.bv;
         d.nu = b.nu;
         d.nv = b.nv;
         d.ptr = upload(c, c->pool_asm, b.ptr);
@@ -625,17 +670,36 @@ void do_assemble(sdc_ctx* c) {
     c->assembled = true;
 }
 
+// The substep-loop kernel for a precision and a chunk size (one DOF per
+// thread when the chunk fits the block).
+using IfaceKernel = void (*)(IfaceArgs);
+IfaceKernel iface_loop_kernel(bool mixed, int chunk) {
+    const bool one = chunk <= IFACE_THREADS;
+    if (mixed) return one ? k_iface_loop_mx1 : k_iface_loop_mx;
+    return one ? k_iface_loop1 : k_iface_loop;
+}
+
 // Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule with the
-// substep loop's shared-memory replicas and that has room for every contact DOF.
+// substep loop's shared-memory replicas and that has room for every contact
+// DOF. A CTA owns `chunk` replica slots (a multiple of 4, so that every
+// chunk is a whole number of 16-byte units for the bulk copies).
 void pick_iface_cluster(sdc_ctx* c) {
-    const int NI = c->C.n_iface;
-    const size_t smem = (size_t)2 * std::max(NI, 1) * sizeof(double);
+    const int NI = std::max(c->C.n_iface, 1);
+    const bool mixed = c->precision == SDC_MIXED_FP32;
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
     // the largest size any context may use, so that contexts with different interfaces coexist
-    SDC_CUDA_TRY(cudaFuncSetAttribute(k_iface_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * IFACE_MAX_NI * sizeof(double))));
-    SDC_CUDA_TRY(cudaFuncSetAttribute(k_iface_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const int max_chunk = ((IFACE_MAX_NI + IFACE_MAX_CLUSTER - 1) / IFACE_MAX_CLUSTER + 3) & ~3;
+    for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_mx,
+                          (const void*)k_iface_loop_mx1}) {
+        SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(2 * IFACE_MAX_CLUSTER * max_chunk * sizeof(double))));
+        SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
     for (int cs = IFACE_MAX_CLUSTER; cs >= 1; cs /= 2) {
-        if ((int64_t)cs * IFACE_THREADS * IFACE_PER_THREAD < NI) break;
+        const int chunk = ((NI + cs - 1) / cs + 3) & ~3;
+        if (chunk > IFACE_THREADS * IFACE_PER_THREAD) break;
+        const size_t smem = 2 * (size_t)cs * chunk * esz;
+        const void* kern = (const void*)iface_loop_kernel(mixed, chunk);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(IFACE_THREADS);
@@ -648,8 +712,9 @@ void pick_iface_cluster(sdc_ctx* c) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (void*)k_iface_loop, &cfg) == cudaSuccess && n >= 1) {
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
             c->iface_cluster = cs;
+            c->iface_chunk = chunk;
             c->iface_smem = smem;
             return;
         }
@@ -689,6 +754,9 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     c->E.idx = dalloc_n<int32_t>(c, c->pool_scheme, slots * MAXE * NI);
     c->E.coef = dalloc_n<double>(c, c->pool_scheme, slots * MAXE * NI);
     c->E.cst = dalloc_n<double>(c, c->pool_scheme, slots * NI);
+    const bool mixed = c->precision == SDC_MIXED_FP32;
+    c->E.coef32 = mixed ? dalloc_n<float>(c, c->pool_scheme, slots * MAXE * NI) : nullptr;
+    c->fe_base = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)(P + 1) * NI) : nullptr;
     // dt-scaled weights
     std::vector<double> Stil(W.Stil), Semb(W.Semb), Shat(W.Shat), slot_pos(slots);
     for (double& v : Stil) v *= c->dt;
@@ -721,7 +789,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.n_slots = n_int * (P + 1);
     ga.status = &c->st->status;
     ga.loop_kernels = &c->st->loop_kernels;
-    ch.kernel(k_iface_geom, blocks_for((int64_t)NI * ga.n_slots, 128), 128u, ga);
+    ga.cs = c->iface_cluster;
+    ga.chunk = c->iface_chunk;
+    ch.kernel_2d(k_iface_geom, dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
 
     // F^I at a standard node that coincides with t_n (Lobatto)
     for (int j = 1; j <= M; ++j)
@@ -748,7 +818,13 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         pa.Semb = c->w_Semb + (size_t)(m - 1) * P * P;
         pa.fe_old = c->fe[set_old] + (size_t)ii * (P + 1) * NI;
         pa.cpre = c->cpre;
-        ch.kernel(k_iface_prep, blocks_for((int64_t)P * NI, 256), 256u, pa);
+        pa.base = c->fe_base;
+        pa.E = c->E;
+        pa.slot0 = ii * (P + 1);
+        pa.Tprev = c->Tstd[m - 1];
+        pa.cs = c->iface_cluster;
+        pa.chunk = c->iface_chunk;
+        ch.kernel(k_iface_prep, blocks_for((int64_t)(P + 1) * NI, 256), 256u, pa);
         IfaceArgs ia{};
         ia.C = c->C;
         ia.mode = mode;
@@ -767,7 +843,11 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.fe_new = c->fe[set_new] + (size_t)ii * (P + 1) * NI;
         ia.fe_prev_end = ii > 0 ? c->fe[set_new] + ((size_t)(ii - 1) * (P + 1) + P) * NI : nullptr;
         ia.ihat_new = c->ihat[set_new] + (size_t)ii * NI;
-        ch.kernel_cluster(k_iface_loop, (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
+        ia.base = c->fe_base;
+        ia.chunk = c->iface_chunk;
+        ia.status = &c->st->status;
+        ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk),
+                          (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
                           (unsigned)c->iface_cluster, ia);
     };
     auto residual = [&](int set, int k) {
@@ -930,6 +1010,8 @@ sdc_status read_state(sdc_ctx* c, sdc_step_report* rep) {
         SDC_CUDA_TRY(cudaMemsetAsync(&c->st->status, 0, sizeof(int), c->stream));
         if (s == SDC_ERR_NOT_CONVERGED) throw ApiError(SDC_ERR_NOT_CONVERGED, "a CG solve reached cg_max_iter");
         if (s == SDC_ERR_ARG) throw ApiError(SDC_ERR_ARG, "contact operator has more than 32 entries per DOF");
+        if (s == SDC_ERR_TIMEOUT)
+            throw ApiError(SDC_ERR_TIMEOUT, "a bounded wait of the contact substep loop gave up");
         throw ApiError((sdc_status)s, "device reported an error");
     }
     return SDC_OK;
@@ -953,6 +1035,8 @@ const char* kernel_name(const void* f) {
         {(const void*)k_cg_update, "k_cg_update"},
         {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
         {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_loop, "k_iface_loop"},
+        {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
+        {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
         {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
@@ -1375,7 +1459,7 @@ sdc_status sdc_contact_flux(sdc_ctx* c, const double* T, double t, double* fE) {
         ga.status = &c->st->status;
         const int NI = c->C.n_iface;
         SDC_CUDA_TRY(cudaMemsetAsync(fE, 0, (size_t)c->n * sizeof(double), c->stream));
-        k_iface_geom<<<blocks_for(NI, 128), 128, 0, c->stream>>>(ga);
+        k_iface_geom<<<dim3(blocks_for(NI, GEOM_THREADS), 1), GEOM_THREADS, 0, c->stream>>>(ga);
         k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 0);
         k_contact_apply<<<blocks_for(NI, 256), 256, 0, c->stream>>>(c->C, c->E1, 0, T, c->Ti1, fE, 1);
         SDC_CUDA_TRY(cudaGetLastError());

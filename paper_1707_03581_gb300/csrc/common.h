@@ -97,6 +97,7 @@ struct Rect4 {
 
 struct BinsDev {
     double ou = 0, ov = 0, bu = 1, bv = 1;   // origin and bin size
+    double ibu = 1, ibv = 1;                // 1 / bin size
     int nu = 0, nv = 0;
     const int32_t* ptr = nullptr;           // nu*nv + 1
     const int32_t* item = nullptr;          // quad ids, stand quads or stock quads
@@ -111,6 +112,8 @@ struct ContactDev {
     const double* mass = nullptr;          // n_iface lumped masses
     const double* minv = nullptr;          // n_iface inverse lumped masses
     const double2* rinv = nullptr;         // per quad: 1 / (hi_u - lo_u), 1 / (hi_v - lo_v)
+    const Rect4* dof_box = nullptr;        // per contact DOF: union of its faces (stock: reference position)
+    Rect4 box_fix{}, box_mov{};            // union of each body's contact faces (stock: reference position)
     const int32_t* inc_ptr = nullptr;      // n_iface + 1
     const int32_t* inc_quad = nullptr;     // incident quad ids
     const int32_t* inc_code = nullptr;     // corner code of the node in that quad

@@ -7,6 +7,7 @@
 // reproducible run to run). The contact substep loop runs on one
 // thread-block cluster synchronised with hardware cluster barriers.
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -161,37 +162,21 @@ __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const f
     return ell_row_t<8, float, float>(A.slice_ptr, A.col, A.val32, row, x);
 }
 
-// Row kernels take any grid: thread t of block b covers rows
-// (b * rpt + j) * blockDim.x + t, j < rpt, so each warp takes whole 32-row
-// slices and a thread's reduction terms are summed before the block stage.
-__device__ __forceinline__ int rows_per_thread(int64_t n) {
-    const int64_t t = (int64_t)gridDim.x * blockDim.x;
-    return (int)((n + t - 1) / t);
-}
-
-__device__ __forceinline__ int64_t row_of(int j, int rpt) {
-    return ((int64_t)blockIdx.x * rpt + j) * blockDim.x + threadIdx.x;
-}
-
 // ------------------------------------------------------------------ operator
 
 // y = m .* x + dtau K x
 __global__ void k_apply_operator(EllDev A, const double* __restrict__ mass, double dtau,
                                  const double* __restrict__ x, double* __restrict__ y) {
-    const int rpt = rows_per_thread(A.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= A.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.n) {
         y[i] = fma(dtau, ell_row(A, i, x), mass[i] * x[i]);
     }
 }
 
 // F = -K T + g   (f^I(T) + g of Eq. ivp)
 __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F) {
-    const int rpt = rows_per_thread(A.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= A.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.n) {
         F[i] = g[i] - ell_row(A, i, T);
     }
 }
@@ -203,10 +188,8 @@ __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __res
 // residual r = b - (m x0 + dtau K x0), u = D r, and the stop test.
 __global__ void k_cg_init(CgArgs a, RhsArgs r) {
     double v[2] = {0.0, 0.0};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const double m = a.mass[i];
             double b;
             if (r.mode == RHS_GIVEN) {
@@ -252,10 +235,8 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
 __global__ void k_cg_spmv(CgArgs a) {
     if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     double v[3] = {0.0, 0.0, 0.0};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const double u = a.U[i];
             const double w = fma(a.dtau, ell_row(a.A, i, a.U), a.mass[i] * u);
             const double res = a.R[i];
@@ -296,10 +277,8 @@ __global__ void k_cg_spmv(CgArgs a) {
 // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D r
 __global__ void k_cg_update(CgArgs a) {
     if (a.cg->done) return;
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
         const double alpha = a.cg->alpha, beta = a.cg->beta;
         const bool first = a.cg->iter == 1;
         const double u = a.U[i], w = a.W[i];
@@ -320,10 +299,8 @@ __global__ void k_cg_update(CgArgs a) {
 // the outer stop test; FP32 inverse diagonal for the inner solves.
 __global__ void k_mx_init(MixArgs a, RhsArgs r) {
     double v[2] = {0.0, 0.0};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const double m = a.mass[i];
             double b;
             if (r.mode == RHS_GIVEN) {
@@ -366,10 +343,8 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
 // one more FP64 residual can meet ||b - A x|| <= rtol ||b||.
 __global__ void k_mx_inner_init(MixArgs a) {
     float v[1] = {0.0f};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const float res = (float)a.R[i];
             a.Rl[i] = res;
             a.Dl[i] = 0.0f;
@@ -394,10 +369,8 @@ __global__ void k_mx_inner_init(MixArgs a) {
 __global__ void k_mx_spmv(MixArgs a) {
     if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     float v[3] = {0.0f, 0.0f, 0.0f};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const float u = a.Ul[i];
             const float w = fmaf((float)a.dtau, ell_row32(a.A, i, a.Ul), a.mass32[i] * u);
             const float res = a.Rl[i];
@@ -436,10 +409,8 @@ __global__ void k_mx_spmv(MixArgs a) {
 // FP32: p = u + beta p; s = w + beta s; d += alpha p; r -= alpha s; u = D r
 __global__ void k_mx_update(MixArgs a) {
     if (a.cg->done) return;
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
         const float alpha = (float)a.cg->alpha, beta = (float)a.cg->beta;
         const bool first = a.cg->iter == 1;
         const float u = a.Ul[i], w = a.Wl[i];
@@ -463,10 +434,8 @@ __device__ __forceinline__ double ell_row_f32in(const EllDev& A, int64_t row, co
 // residual b - A x of the corrected iterate, formed in FP64; outer stop test.
 __global__ void k_mx_refine(MixArgs a) {
     double v[1] = {0.0};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const double d = (double)a.Dl[i];
             a.X[i] += d;
             const double res = a.R[i] - fma(a.dtau, ell_row_f32in(a.A, i, a.Dl), a.mass[i] * d);
@@ -498,10 +467,8 @@ __global__ void k_mx_refine(MixArgs a) {
 // (sum_p stil_{m,p,j} = s_{m,j}). Contact rows are overwritten by the
 // substep loop that follows.
 __global__ void k_bulk_endpoint(BulkArgs a) {
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
         const double KX = ell_row(a.A, i, a.X);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
@@ -529,15 +496,16 @@ __device__ __forceinline__ void motion_at(const ContactDev& C, double tau, doubl
     q = C.q0 * fabs(cos(ph));
 }
 
+// Merge c into the row's entry for `node` (entry k of this thread at idx[k * GEOM_THREADS]).
 __device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, int node, double c, bool& overflow) {
     for (int k = 0; k < n; ++k)
-        if (idx[k] == node) {
-            coef[k] += c;
+        if (idx[k * GEOM_THREADS] == node) {
+            coef[k * GEOM_THREADS] += c;
             return;
         }
     if (n < MAXE) {
-        idx[n] = node;
-        coef[n] = c;
+        idx[n * GEOM_THREADS] = node;
+        coef[n * GEOM_THREADS] = c;
         ++n;
     } else {
         overflow = true;
@@ -553,28 +521,50 @@ __device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, in
 // of v, and the 2x2 rule is the product of two 2-point rules, so every
 // coefficient is a product of two one-dimensional sums:
 //   int phi^Q_a phi^X_c = [sum_g w_g l^Q_a(u_g) l^X_c(u_g)] [sum_g w_g l^Q_a(v_g) l^X_c(v_g)].
-__global__ void k_iface_geom(GeomArgs g) {
+__global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
     const ContactDev& C = g.C;
     const int NI = C.n_iface;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)NI * g.n_slots) return;
-    const int s = (int)(gid / NI), a = (int)(gid % NI);
-    if (gid == 0 && g.loop_kernels) *g.loop_kernels = 0;  // first kernel of a macro step
-    double tau;
-    if (g.use_fixed) {
-        tau = g.t_fixed;
-    } else {
-        const double tn = __dadd_rn(g.st->t0, __dmul_rn((double)g.st->n_done, g.st->dt));
-        tau = __dadd_rn(tn, __dmul_rn(g.st->dt, g.slot_pos[s]));
+    const int s = (int)blockIdx.y;
+    const int a = (int)(blockIdx.x * GEOM_THREADS + threadIdx.x);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && g.loop_kernels) *g.loop_kernels = 0;  // step start
+    // the slot's motion, once per block
+    __shared__ double mot[3];
+    __shared__ int32_t s_idx[MAXE * GEOM_THREADS];
+    __shared__ double s_coef[MAXE * GEOM_THREADS];
+    if (threadIdx.x == 0) {
+        double tau;
+        if (g.use_fixed) {
+            tau = g.t_fixed;
+        } else {
+            const double tn = __dadd_rn(g.st->t0, __dmul_rn((double)g.st->n_done, g.st->dt));
+            tau = __dadd_rn(tn, __dmul_rn(g.st->dt, g.slot_pos[s]));
+        }
+        motion_at(C, tau, mot[0], mot[1], mot[2]);
     }
-    double du, dv, q;
-    motion_at(C, tau, du, dv, q);
+    __syncthreads();
+    if (a >= NI) return;
+    const double du = mot[0], dv = mot[1], q = mot[2];
+    int32_t* idx = s_idx + threadIdx.x;
+    double* coef = s_coef + threadIdx.x;
     const bool stock = a >= C.n_iface_fix;
     const double h_c = C.h_c;
+    {
+        // no face of this DOF can touch the other body's contact faces: empty row
+        Rect4 mine = C.dof_box[a], other = stock ? C.box_fix : C.box_mov;
+        if (stock) {
+            mine.x += du; mine.z += du; mine.y += dv; mine.w += dv;
+        } else {
+            other.x += du; other.z += du; other.y += dv; other.w += dv;
+        }
+        if (!(fmin(mine.z, other.z) > fmax(mine.x, other.x) && fmin(mine.w, other.w) > fmax(mine.y, other.y))) {
+            const size_t so = (size_t)s * NI + a;
+            g.E.cnt[so] = 0;
+            g.E.cst[so] = 0.0;
+            return;
+        }
+    }
     const double gp = 0.57735026918962576451;  // 1/sqrt(3)
 
-    int32_t idx[MAXE];
-    double coef[MAXE];
     int n = 0;
     bool overflow = false;
     double cst = 0.0;
@@ -594,8 +584,8 @@ __global__ void k_iface_geom(GeomArgs g) {
         const double lo_u = Q.x - su, lo_v = Q.y - sv, hi_u = Q.z - su, hi_v = Q.w - sv;
         // a partner's low corner lies in (lo - bin, hi) along each axis (bins are at least one face
         // wide); the 1e-9 bin margin absorbs the rounding of these quotients
-        int iu0 = (int)floor((lo_u - B.bu - B.ou) / B.bu - 1e-9), iu1 = (int)floor((hi_u - B.ou) / B.bu + 1e-9);
-        int iv0 = (int)floor((lo_v - B.bv - B.ov) / B.bv - 1e-9), iv1 = (int)floor((hi_v - B.ov) / B.bv + 1e-9);
+        int iu0 = (int)floor((lo_u - B.bu - B.ou) * B.ibu - 1e-9), iu1 = (int)floor((hi_u - B.ou) * B.ibu + 1e-9);
+        int iv0 = (int)floor((lo_v - B.bv - B.ov) * B.ibv - 1e-9), iv1 = (int)floor((hi_v - B.ov) * B.ibv + 1e-9);
         iu0 = max(iu0, 0); iv0 = max(iv0, 0);
         iu1 = min(iu1, B.nu - 1); iv1 = min(iv1, B.nv - 1);
         for (int iv = iv0; iv <= iv1; ++iv)
@@ -604,6 +594,15 @@ __global__ void k_iface_geom(GeomArgs g) {
                 for (int t = B.ptr[bin]; t < B.ptr[bin + 1]; ++t) {
                     const int Rf = B.item[t];
                     Rect4 R = C.rect[Rf];
+                    {
+                        // FP32 prefilter (a margin of 1e-4 of the face size keeps it conservative);
+                        // the exact FP64 test follows
+                        const float su_ = stock ? 0.f : (float)du, sv_ = stock ? 0.f : (float)dv;
+                        const float mu = 1e-4f * (float)(Q.z - Q.x), mv = 1e-4f * (float)(Q.w - Q.y);
+                        const float ra = fmaxf((float)Q.x, (float)R.x + su_), rb = fminf((float)Q.z, (float)R.z + su_);
+                        const float sa = fmaxf((float)Q.y, (float)R.y + sv_), sb = fminf((float)Q.w, (float)R.w + sv_);
+                        if (rb < ra - mu || sb < sa - mv) continue;
+                    }
                     if (!stock) {
                         R.x += du; R.z += du; R.y += dv; R.w += dv;
                     }
@@ -654,8 +653,11 @@ __global__ void k_iface_geom(GeomArgs g) {
     g.E.cst[so] = cst;
     for (int k = 0; k < n; ++k) {
         const size_t o = ((size_t)s * MAXE + k) * NI + a;
-        g.E.idx[o] = idx[k];
-        g.E.coef[o] = coef[k];
+        const int j = idx[k * GEOM_THREADS];
+        g.E.idx[o] = g.cs ? (j % g.cs) * g.chunk + j / g.cs : j;
+        const double cf = coef[k * GEOM_THREADS];
+        g.E.coef[o] = cf;
+        if (g.E.coef32) g.E.coef32[o] = (float)cf;
     }
 }
 
@@ -670,22 +672,25 @@ __device__ __forceinline__ double apply_coupling(const CouplingOp& E, int slot, 
     return acc;
 }
 
-// Coupling entries of one contact DOF at one slot, first batch loaded ahead
+// Coupling entries of one contact DOF at one slot, the first B loaded ahead
 // of use (the operator does not depend on T, so these loads can be issued
-// before the barrier that publishes T).
-struct CouplingRow {
+// before the wait that publishes T).
+template <int B>
+struct CouplingRowT {
     int n;
     double cst;
-    int idx[IFACE_BATCH];
-    double coef[IFACE_BATCH];
+    int idx[B];
+    double coef[B];
 };
+using CouplingRow = CouplingRowT<IFACE_BATCH>;
 
-__device__ __forceinline__ void coupling_prefetch(const CouplingOp& E, int slot, int NI, int a, CouplingRow& r) {
+template <int B>
+__device__ __forceinline__ void coupling_prefetch(const CouplingOp& E, int slot, int NI, int a, CouplingRowT<B>& r) {
     const size_t so = (size_t)slot * NI + a;
     r.n = __ldg(E.cnt + so);
     r.cst = __ldg(E.cst + so);
 #pragma unroll
-    for (int k = 0; k < IFACE_BATCH; ++k) {  // entries past n are never used
+    for (int k = 0; k < B; ++k) {  // entries past n are never used
         const size_t o = ((size_t)slot * MAXE + k) * NI + a;
         r.idx[k] = __ldg(E.idx + o);
         r.coef[k] = __ldg(E.coef + o);
@@ -693,18 +698,21 @@ __device__ __forceinline__ void coupling_prefetch(const CouplingOp& E, int slot,
 }
 
 // cst + sum_k coef_k T[idx_k] on a replica of T_I in this CTA's shared memory,
-// in entry order; entries past the prefetched batch are fetched IFACE_BATCH at a time.
+// in entry order; the entries past the prefetched batch are fetched 16 at a
+// time with all loads of a round issued together.
+template <int B>
 __device__ __forceinline__ double coupling_apply_shared(const CouplingOp& E, int slot, int NI, int a,
-                                                        const CouplingRow& r, const double* Tsh) {
+                                                        const CouplingRowT<B>& r, const double* Tsh) {
+    constexpr int B2 = 16;  // later rounds
     double acc = r.cst;
 #pragma unroll
-    for (int k = 0; k < IFACE_BATCH; ++k)
+    for (int k = 0; k < B; ++k)
         if (k < r.n) acc = fma(r.coef[k], Tsh[r.idx[k]], acc);
-    for (int k0 = IFACE_BATCH; k0 < r.n; k0 += IFACE_BATCH) {
-        int id[IFACE_BATCH];
-        double cf[IFACE_BATCH];
+    for (int k0 = B; k0 < r.n; k0 += B2) {
+        int id[B2];
+        double cf[B2];
 #pragma unroll
-        for (int j = 0; j < IFACE_BATCH; ++j) {
+        for (int j = 0; j < B2; ++j) {
             const int k = k0 + j;
             if (k < r.n) {
                 const size_t o = ((size_t)slot * MAXE + k) * NI + a;
@@ -713,8 +721,55 @@ __device__ __forceinline__ double coupling_apply_shared(const CouplingOp& E, int
             }
         }
 #pragma unroll
-        for (int j = 0; j < IFACE_BATCH; ++j)
+        for (int j = 0; j < B2; ++j)
             if (k0 + j < r.n) acc = fma(cf[j], Tsh[id[j]], acc);
+    }
+    return acc;
+}
+
+// FP32 coupling entries of one contact DOF at one slot (mixed precision).
+template <int B>
+struct CouplingRow32T {
+    int n;
+    int idx[B];
+    float coef[B];
+};
+
+template <int B>
+__device__ __forceinline__ void coupling_prefetch32(const CouplingOp& E, int slot, int NI, int a, CouplingRow32T<B>& r) {
+    r.n = __ldg(E.cnt + (size_t)slot * NI + a);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {  // entries past n are never used
+        const size_t o = ((size_t)slot * MAXE + k) * NI + a;
+        r.idx[k] = __ldg(E.idx + o);
+        r.coef[k] = __ldg(E.coef32 + o);
+    }
+}
+
+// sum_k coef32_k dT[idx_k] in FP32 on a shared-memory replica of the deviations dT
+template <int B>
+__device__ __forceinline__ float coupling_apply_shared32(const CouplingOp& E, int slot, int NI, int a,
+                                                         const CouplingRow32T<B>& r, const float* dT) {
+    constexpr int B2 = 16;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+        if (k < r.n) acc = fmaf(r.coef[k], dT[r.idx[k]], acc);
+    for (int k0 = B; k0 < r.n; k0 += B2) {
+        int id[B2];
+        float cf[B2];
+#pragma unroll
+        for (int j = 0; j < B2; ++j) {
+            const int k = k0 + j;
+            if (k < r.n) {
+                const size_t o = ((size_t)slot * MAXE + k) * NI + a;
+                id[j] = __ldg(E.idx + o);
+                cf[j] = __ldg(E.coef32 + o);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B2; ++j)
+            if (k0 + j < r.n) acc = fmaf(cf[j], dT[id[j]], acc);
     }
     return acc;
 }
@@ -737,12 +792,28 @@ __device__ __forceinline__ double substep_dt(const IfaceArgs& a, double tn, int 
     return __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
 }
 
-// c_p of every substep and contact DOF (see PrepArgs); one thread per (p, DOF).
+// c_p of every substep and contact DOF (see PrepArgs); one thread per (p, DOF),
+// p = 0..P (p = 0 only forms base_0 in mixed precision).
 __global__ void k_iface_prep(PrepArgs a) {
     const int NI = a.C.n_iface;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)NI * a.P) return;
-    const int p = (int)(gid / NI) + 1, i = (int)(gid % NI);
+    if (gid >= (int64_t)NI * (a.P + 1)) return;
+    const int p = (int)(gid / NI), i = (int)(gid % NI);
+    if (a.base) {
+        // f^E(T_{m-1}, tau_{m,p}) in FP64: the part of the coupling the substeps do not change
+        const int slot = a.slot0 + p;
+        const size_t so = (size_t)slot * NI + i;
+        const int n = a.E.cnt[so];
+        double acc = a.E.cst[so];
+        for (int k = 0; k < n; ++k) {
+            const size_t o = ((size_t)slot * MAXE + k) * NI + i;
+            const int pos = a.E.idx[o];
+            const int j = pos / a.chunk + a.cs * (pos % a.chunk);  // replica position -> contact DOF
+            acc = fma(a.E.coef[o], a.Tprev[a.C.dof[j]], acc);
+        }
+        a.base[(size_t)p * NI + i] = acc;
+    }
+    if (p == 0) return;
     const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
     const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
     double c;
@@ -761,88 +832,182 @@ __global__ void k_iface_prep(PrepArgs a) {
     a.cpre[(size_t)(p - 1) * NI + i] = c;
 }
 
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Wait until the mbarrier at `bar` completes the phase of parity `parity`,
+// for at most ~2^24 polls; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (long it = 0; it < (1l << 24); ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred P1; mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // The P explicit substeps of one interval on the contact DOFs (Algorithm 1 /
 // Algorithm 2 inner loops):
 //   m T_{m,p} = m T_{m,p-1} + c_p + dt_p f^E(T_{m,p-1}, tau_{m,p-1})
-// with c_p from k_iface_prep. One cluster of CTAs; contact DOF i belongs to
-// CTA i mod (cluster size). Every CTA keeps both buffers of a full replica of
-// T_I in shared memory; an owner writes each new value into every CTA's
-// replica (distributed shared memory), then one cluster barrier publishes the
-// substep, and the coupling gathers read the local replica. Each f^E of the
-// current iterate is stored for the next sweep, and
+// with c_p from k_iface_prep, on one cluster of CTAs. Every CTA keeps both
+// buffers of a full replica of the contact temperatures in shared memory,
+// chunk-major: CTA r owns the DOFs r, r + cs, r + 2 cs, ... (interleaved, so
+// that the DOFs under the moving stock spread over all CTAs) and stores them
+// contiguously as chunk r. After a substep's update, one thread pushes the
+// own chunk into every other CTA's replica with a bulk shared-memory copy
+// across the cluster that completes a byte count on the receiver's mbarrier;
+// waiting for all incoming bytes publishes the substep, so no cluster barrier
+// is needed inside the loop. A CTA overwrites a buffer only after it has
+// received every peer's next chunk, which each peer sends only after its
+// gather from that buffer (program order), so the two buffers suffice.
+//   FP64 (MIX = false): the replica holds T; f^E = cst + sum_k coef_k T_k.
+//   Mixed (MIX = true): the replica holds the FP32 deviations T - T_{m-1}
+//   (mK over an interval) and f^E = base_p + sum_k coef32_k dT_k, base_p =
+//   f^E(T_{m-1}, tau_{m,p}) formed in FP64 by k_iface_prep; each DOF's own T
+//   stays FP64.
+// Every f^E of the current iterate is stored for the next sweep, and
 // ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m) is accumulated.
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
-    extern __shared__ double shT[];            // [2][NI]
+template <bool MIX, int PER>
+__device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
+    // one contact DOF per thread leaves registers to prefetch a whole typical row
+    constexpr int B = PER == 1 ? (MIX ? 24 : 16) : IFACE_BATCH;
+    using V = typename std::conditional<MIX, float, double>::type;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ __align__(8) unsigned long long mbar[2];
     cg::cluster_group cluster = cg::this_cluster();
     const ContactDev& C = a.C;
     const int NI = C.n_iface;
-    const int csize = (int)cluster.num_blocks();
+    const int cs = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
+    const int chunk = a.chunk;
     const int P = a.P;
+    V* rep = reinterpret_cast<V*>(dyn);  // [2][cs * chunk]
     const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
 
-    // owned DOFs: i = rank + csize * (threadIdx.x + IFACE_THREADS * r)
-    int own[IFACE_PER_THREAD];
-    double T[IFACE_PER_THREAD], fe[IFACE_PER_THREAD], mi[IFACE_PER_THREAD], ih[IFACE_PER_THREAD];
-    CouplingRow row[IFACE_PER_THREAD];
+    int own[PER], slot[PER];
+    double T[PER], T0[PER], fe[PER], mi[PER],
+        ih[PER], cn[PER], bn[PER];
 #pragma unroll
-    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
-        const int i = rank + csize * ((int)threadIdx.x + IFACE_THREADS * r);
-        own[r] = i < NI ? i : -1;
+    for (int r = 0; r < PER; ++r) {
+        slot[r] = (int)threadIdx.x + IFACE_THREADS * r;
+        const int i = rank + cs * slot[r];
+        own[r] = (slot[r] < chunk && i < NI) ? i : -1;
         ih[r] = 0.0;
-        if (own[r] >= 0 && a.first && a.mode == RHS_PRED) coupling_prefetch(a.E, a.slot0, NI, i, row[r]);
     }
-    // T_{m,0} = T_{m-1}: every CTA fills its own replica (buffer 0)
-    for (int i = threadIdx.x; i < NI; i += IFACE_THREADS) shT[i] = a.Tprev[C.dof[i]];
-    // every CTA of the cluster has started (and filled its replica) before any remote write
+    // buffer 0 = the replica at tau_{m,0}: T_{m-1} (FP64) or zero deviations (mixed)
+    for (int pos = threadIdx.x; pos < cs * chunk; pos += IFACE_THREADS) {
+        const int j = pos / chunk + cs * (pos % chunk);
+        rep[pos] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[b])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // every CTA has started, filled its replica and initialised its barriers before any copy
     cluster.sync();
     // f^E at tau_{m,0}
 #pragma unroll
-    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+    for (int r = 0; r < PER; ++r) {
         const int i = own[r];
         if (i < 0) continue;
-        T[r] = shT[i];
+        T0[r] = a.Tprev[C.dof[i]];
+        T[r] = T0[r];
         mi[r] = C.minv[i];
         double f0;
-        if (a.first) {
-            f0 = (a.mode == RHS_PRED) ? coupling_apply_shared(a.E, a.slot0, NI, i, row[r], shT) : a.fe_old[i];
+        if (a.first && a.mode == RHS_PRED) {
+            if constexpr (MIX) {
+                f0 = a.base[i];
+            } else {
+                CouplingRowT<B> row;
+                coupling_prefetch(a.E, a.slot0, NI, i, row);
+                f0 = coupling_apply_shared(a.E, a.slot0, NI, i, row, rep);
+            }
         } else {
-            f0 = a.fe_prev_end[i];
+            f0 = a.first ? a.fe_old[i] : a.fe_prev_end[i];
         }
         fe[r] = f0;
         a.fe_new[i] = f0;
+        cn[r] = a.cpre[i];
+        if constexpr (MIX) bn[r] = a.base[(size_t)NI + i];
     }
+    unsigned phase[2] = {0u, 0u};
+    const unsigned bytes = (unsigned)(chunk * sizeof(V));
+    bool timed_out = false;
     for (int p = 1; p <= P; ++p) {
+        const int b = p & 1;
+        V* buf = rep + (size_t)b * cs * chunk;
         const double dtp = substep_dt(a, tn, p);
-        double* buf = shT + (size_t)(p & 1) * NI;
+        typename std::conditional<MIX, CouplingRow32T<B>, CouplingRowT<B>>::type row[PER];
+        double bp[PER];
 #pragma unroll
-        for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+        for (int r = 0; r < PER; ++r) {
             const int i = own[r];
             if (i < 0) continue;
-            coupling_prefetch(a.E, a.slot0 + p, NI, i, row[r]);
-            const double incr = fma(dtp, fe[r], a.cpre[(size_t)(p - 1) * NI + i]);
-            T[r] = fma(incr, mi[r], T[r]);
-            for (int q = 0; q < csize; ++q) *cluster.map_shared_rank(buf + i, q) = T[r];
+            if constexpr (MIX) coupling_prefetch32(a.E, a.slot0 + p, NI, i, row[r]);
+            else coupling_prefetch(a.E, a.slot0 + p, NI, i, row[r]);
+            const double cp = cn[r];
+            bp[r] = bn[r];
+            if (p < P) {  // inputs of the next substep, loaded one substep ahead
+                cn[r] = a.cpre[(size_t)p * NI + i];
+                if constexpr (MIX) bn[r] = a.base[(size_t)(p + 1) * NI + i];
+            }
+            T[r] = fma(fma(dtp, fe[r], cp), mi[r], T[r]);
+            buf[rank * chunk + slot[r]] = MIX ? (V)(T[r] - T0[r]) : (V)T[r];
         }
-        cluster.sync();
+        // generic-proxy writes of the own chunk become visible to the bulk copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned src = smem_addr(buf + rank * chunk);
+            const unsigned bar = smem_addr(&mbar[b]);
+            for (int q = 0; q < cs; ++q) {
+                if (q == rank) continue;
+                unsigned dst, rbar;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(src), "r"(q));
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(bar), "r"(q));
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                    "r"(src), "r"(bytes), "r"(rbar)
+                    : "memory");
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes * (cs - 1))
+                         : "memory");
+        }
+        if (!timed_out && !mbar_wait(smem_addr(&mbar[b]), phase[b])) timed_out = true;
+        phase[b] ^= 1u;
 #pragma unroll
-        for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+        for (int r = 0; r < PER; ++r) {
             const int i = own[r];
             if (i < 0) continue;
-            fe[r] = coupling_apply_shared(a.E, a.slot0 + p, NI, i, row[r], buf);
+            if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32(a.E, a.slot0 + p, NI, i, row[r], buf);
+            else fe[r] = coupling_apply_shared(a.E, a.slot0 + p, NI, i, row[r], buf);
             a.fe_new[(size_t)p * NI + i] = fe[r];
             ih[r] = fma(a.Shat[p - 1], fe[r], ih[r]);
         }
     }
+    if (timed_out) atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
 #pragma unroll
-    for (int r = 0; r < IFACE_PER_THREAD; ++r) {
+    for (int r = 0; r < PER; ++r) {
         const int i = own[r];
         if (i < 0) continue;
         a.Tout[C.dof[i]] = T[r];
         a.ihat_new[i] = ih[r];
     }
-    // no CTA may exit while others can still write into its shared memory
+    // no CTA may exit while its shared memory can still be a copy destination
     cluster.sync();
+}
+
+// one contact DOF per thread (chunk <= IFACE_THREADS) / up to IFACE_PER_THREAD
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop1(IfaceArgs a) { iface_loop_impl<false, 1>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
+    iface_loop_impl<false, IFACE_PER_THREAD>(a);
+}
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx1(IfaceArgs a) { iface_loop_impl<true, 1>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx(IfaceArgs a) {
+    iface_loop_impl<true, IFACE_PER_THREAD>(a);
 }
 
 // ------------------------------------------------------------------ diagnostics
@@ -850,10 +1015,8 @@ __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
 // r^k = max_m || m T_m - m T_n - sum_{j<=m} I_{j-1}^j ||_inf (Eq. residual)
 __global__ void k_residual(ResidualArgs a) {
     double v[1] = {0.0};
-    const int rpt = rows_per_thread(a.n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= a.n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
             const double m = a.mass[i];
             const double tn = a.Tn[i];
             const int pa = a.pos[i];
@@ -875,10 +1038,8 @@ __global__ void k_residual(ResidualArgs a) {
 __global__ void k_heat(const double* __restrict__ mass, const double* __restrict__ T, int64_t n, int64_t n_fix,
                        double* partials, unsigned int* counter, double* heat) {
     double v[2] = {0.0, 0.0};
-    const int rpt = rows_per_thread(n);
-    for (int jr = 0; jr < rpt; ++jr) {
-        const int64_t i = row_of(jr, rpt);
-        if (i >= n) break;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
             const double h = mass[i] * T[i];
             if (i < n_fix) v[0] += h; else v[1] += h;
     }

@@ -6,6 +6,7 @@
 namespace sdc {
 
 constexpr int MAXE = 32;            // coupling entries per contact DOF and substep time
+constexpr int GEOM_THREADS = 64;    // threads per block of k_iface_geom (one slot per block row)
 constexpr int IFACE_MAX_CLUSTER = 16;   // CTAs of the substep-loop cluster (at most)
 constexpr int IFACE_THREADS = 512;      // threads per CTA of that cluster
 constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of the loop can own
@@ -102,6 +103,7 @@ struct CouplingOp {
     int32_t* idx;     // [slots][MAXE][NI]
     double* coef;     // [slots][MAXE][NI]
     double* cst;      // [slots][NI]
+    float* coef32;    // [slots][MAXE][NI] FP32 copy (mixed precision), or NULL
 };
 
 struct GeomArgs {
@@ -114,6 +116,9 @@ struct GeomArgs {
     int n_slots;
     int* status;
     int* loop_kernels;        // reset here (the step's first kernel); NULL outside a step
+    // 0: coupling indices are contact-DOF ids; else replica positions of the substep loop
+    // for a cluster of `cs` CTAs with `chunk` slots each (DOF j -> (j % cs) * chunk + j / cs)
+    int cs, chunk;
 };
 
 // T-independent part of every substep increment of one interval
@@ -136,6 +141,13 @@ struct PrepArgs {
     const double* Semb;             // [P][P]  dt s_{m,p,q}
     const double* fe_old;           // [(P+1)][NI] previous iterate (sweep)
     double* cpre;                   // [P][NI] output
+    // mixed precision: base_q = f^E(T_{m-1}, tau_{m,q}) for q = 0..P (output), from
+    // the interval's slots of the coupling operator and T_{m-1} = Tprev
+    double* base;                   // [(P+1)][NI] or NULL
+    CouplingOp E;                   // indices are replica positions (see GeomArgs::cs)
+    int slot0;
+    const double* Tprev;
+    int cs, chunk;
 };
 
 // Sequential substeps of one interval on the contact DOFs (one cluster).
@@ -157,6 +169,9 @@ struct IfaceArgs {
     double* fe_new;                 // [(P+1)][NI]
     const double* fe_prev_end;      // [NI] this iterate's f^E at the end of the previous interval
     double* ihat_new;               // [NI]
+    const double* base;             // mixed: [(P+1)][NI] f^E(T_{m-1}, tau_{m,q}) from k_iface_prep
+    int chunk;                      // replica slots per CTA (the cluster size is the grid)
+    int* status;                    // sticky status word (SDC_ERR_TIMEOUT if an exchange wait gives up)
 };
 
 struct ResidualArgs {
@@ -191,6 +206,9 @@ __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const doub
                                 int phase);
 __global__ void k_iface_prep(PrepArgs a);
 __global__ void k_iface_loop(IfaceArgs a);
+__global__ void k_iface_loop1(IfaceArgs a);
+__global__ void k_iface_loop_mx(IfaceArgs a);
+__global__ void k_iface_loop_mx1(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,
                        unsigned int* counter, double* heat);

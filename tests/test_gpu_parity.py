@@ -232,7 +232,8 @@ def test_eager_kernel_timing_counts_every_launch(torch):
     # one SpMV per update plus the one whose residual test stops each solve
     assert kt["k_cg_spmv"][0] == kt["k_cg_update"][0]
     assert rep["cg_iters_total"] <= kt["k_cg_spmv"][0] <= rep["cg_iters_total"] + rep["n_solves"]
-    assert kt["k_iface_loop"][0] == rep["n_solves"]
+    loops = sum(n for name, (n, _) in kt.items() if name.startswith("k_iface_loop"))
+    assert loops == rep["n_solves"]
     assert all(ms > 0 for _, ms in kt.values())
     assert rep["contact_cluster"] >= 1
     s.close()
