@@ -4,8 +4,14 @@ Workload (default): the 48x48x120 stand + 24x24x36 stock machine (313,646
 DOF, seeded stroke), Lobatto M=3, 3 sweeps, P=20 embedded substeps, dt = 1 s,
 CG to rel 1e-12. One "step" = one macro step (Algorithm 1 + 3 x Algorithm 2).
 
-  value  = DOF x substeps per second (N_dof x M' x P per macro step)
+  value  = DOF x substeps per second (N_dof x M' x P per macro step) of the
+           mixed-precision path (FP32 SpMV/CG on the correction inside FP64
+           iterative refinement; --precision fp64 times the plain FP64 path)
   eta    = simulated seconds per wall second (look-ahead factor)
+  fp64   = the plain FP64 path on the same inputs, timed the same way, with
+           the gain of the mixed path over it and the rel-L2 between the two;
+           `accuracy` also holds the rel-L2 of each path against the CPU
+           oracle's first macro step (computed with the cpu_baseline leg)
 
 Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
 on the solver's stream, with L2 flushed (256 MiB write) between steps
@@ -108,8 +114,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_baseline(config_idx, steps):
-    """Time the CPU oracle (single-threaded numpy/scipy) in a fresh process."""
+def _oracle_baseline(config_idx, steps, save_to=None):
+    """Time the CPU oracle (single-threaded numpy/scipy) in a fresh process;
+    optionally save its final temperature field (.npy) for an accuracy check."""
     code = (
         "import os, sys, time, json, numpy as np\n"
         f"sys.path.insert(0, {ROOT!r})\n"
@@ -125,6 +132,8 @@ def _oracle_baseline(config_idx, steps):
         f"for n in range({steps}):\n"
         "    T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)\n"
         "el = time.perf_counter() - t\n"
+        f"save_to = {save_to!r}\n"
+        "if save_to: np.save(save_to, T)\n"
         "print(json.dumps({'seconds': el, 'n': prob.n}))\n"
     )
     env = dict(os.environ)
@@ -171,7 +180,28 @@ def _timed_steps(s, stream, flush, steps, torch):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
+def _rel_l2(a, b):
+    import numpy as np
+
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
+# capture of the current kernel on the named workload (summary under profiles/);
+# reported only for that workload, and to be cleared whenever the kernel changes.
+TRAFFIC = {("k_mx_spmv", 1): 70.545664e6 + 0.929792e6}
+
+
+def _spmv_bytes(precision, nnz, n):
+    """Algorithmic bytes of one CG SpMV launch: stored nonzeros (value + int32
+    column) plus the row vectors it reads (u, r, m) and writes (w)."""
+    if precision == "mixed":
+        return 8 * nnz + 16 * n, "k_mx_spmv", "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)"
+    return 12 * nnz + 32 * n, "k_cg_spmv", "FP64 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)"
+
+
 def run_gpu(args, rank, world):
+    import numpy as np
     import torch
 
     from paper_1707_03581_gb300 import Solver
@@ -179,11 +209,18 @@ def run_gpu(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     m, n_int, desc = _workload(args.config)
-    s = Solver(local)
-    s.set_machine(m, precision=args.precision)
-    if args.eager:
-        s.set_execution(True)
     P = m.scheme.P
+
+    def make(precision):
+        s = Solver(local)
+        s.set_machine(m, precision=precision)
+        if args.eager:
+            s.set_execution(True)
+        return s
+
+    s = make(args.precision)
+    compare = args.precision == "mixed" and not args.no_compare
+    s64 = make("fp64") if compare else None
     units_per_step = s.n * n_int * P
     stream = s.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
@@ -191,6 +228,8 @@ def run_gpu(args, rank, world):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.step(report=True)
+            if s64 is not None:
+                s64.step(report=True)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -200,7 +239,11 @@ def run_gpu(args, rank, world):
         # launches and CG work of one step, from a reported step after the timed region
         rep = s.step(report=True)
         launches = rep["kernel_launches"] * args.steps
-        cg_iters = rep["cg_iters_total"]
+        ms64 = None
+        if s64 is not None:
+            ms64 = _timed_steps(s64, stream, flush, args.steps, torch)
+            rep64 = s64.step(report=True)
+            rel_vs_fp64 = _rel_l2(s.temperature(), s64.temperature())
 
         # per-kernel device times of the same steps, each launch between CUDA events on the
         # solver's stream (plain launches; the CG loop is driven from the host one iteration ahead)
@@ -238,10 +281,10 @@ def run_gpu(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
 
-    # dominant HBM kernel: the CG SpMV y = m p + dtau K p with <p, y>
+    # dominant HBM kernel: the CG SpMV
     peak, peak_kind = _peaks()
-    spmv_bytes = 12 * s.nnz + 24 * s.n
-    n_spmv, ms_spmv = kt.get("k_cg_spmv", (0, 0.0))
+    spmv_bytes, spmv_name, spmv_desc = _spmv_bytes(args.precision, s.nnz, s.n)
+    n_spmv, ms_spmv = kt.get(spmv_name, (0, 0.0))
     ms_per_spmv = ms_spmv / max(n_spmv, 1)
     achieved = spmv_bytes / (ms_per_spmv * 1e-3) / 1e9 if n_spmv else 0.0
     kern_total = sum(v[1] for v in kt.values())
@@ -252,23 +295,32 @@ def run_gpu(args, rank, world):
     if rank != 0:
         return
     value = units_per_step * args.steps * world / (t_max * 1e-3)
+    srt = sorted(ms_steps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "precision": args.precision, "parallelism": f"replicas x{world}",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": desc,
+                   "precision": ("mixed: FP32 SpMV/CG on the correction inside FP64 iterative refinement, "
+                                 "FP64 residuals, quadratures and state" if args.precision == "mixed"
+                                 else "fp64 throughout"),
+                   "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "execution": "eager launches" if args.eager else "one CUDA graph per macro step"},
         "eta": args.steps * m.scheme.dt / (t_max * 1e-3),
-        "cg_iters_per_step": cg_iters,
+        "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "cg_iters_per_step": rep["cg_iters_total"],
+        "refinements_per_step": rep["refinements_total"],
         "contact_cluster": rep["contact_cluster"],
         "e2e": {"value": units_per_step * args.steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * s.n, "d2h_bytes_per_step": 8 * s.n,
                 "eta": args.steps * m.scheme.dt / e2e_s},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "k_cg_spmv (FP64 sliced-ELL SpMV + <p, y>)",
+                     "frac": achieved / peak if peak else None,
+                     "traffic": TRAFFIC.get((spmv_name, args.config)),
+                     "kernel": f"{spmv_name} ({spmv_desc})",
                      "algorithmic_bytes": spmv_bytes, "ms_per_launch": ms_per_spmv,
                      "launches_timed": n_spmv, "peak_kind": peak_kind,
                      "timing": "CUDA events around each launch of the eager timed steps"},
@@ -276,12 +328,33 @@ def run_gpu(args, rank, world):
         "eager_ms_per_step": sum(eager_ms) / len(eager_ms),
         "clocks": clk.summary(),
     }
+    if ms64 is not None:
+        v64 = units_per_step * args.steps / (sum(ms64) * 1e-3)
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": sum(ms64) / args.steps,
+                        "eta": args.steps * m.scheme.dt / (sum(ms64) * 1e-3),
+                        "cg_iters_per_step": rep64["cg_iters_total"]}
+        line["gain_vs_fp64"] = value / v64
+        line["accuracy"] = {"rel_l2_mixed_vs_fp64": rel_vs_fp64,
+                            "after_steps": args.warmup + args.steps + 1}
     if not args.no_cpu_baseline and world == 1:
         try:
-            res = _oracle_baseline(args.config, 1)
+            import tempfile
+
+            with tempfile.TemporaryDirectory() as tmp:
+                path = os.path.join(tmp, "oracle_T.npy")
+                res = _oracle_baseline(args.config, 1, save_to=path)
+                T_or = np.load(path)
             v = res["n"] * n_int * P / res["seconds"]
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": "one macro step of the same workload, single-threaded numpy/scipy"}
+            acc = line.setdefault("accuracy", {})
+            for prec in ([args.precision, "fp64"] if compare else [args.precision]):
+                g = make(prec)
+                g.set_execution(False)
+                g.step(report=True)
+                acc[f"rel_l2_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature(), T_or)
+                acc[f"rel_l2_rise_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature() - m.T0, T_or - m.T0)
+                g.close()
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": str(e)[:200]}
     print(json.dumps(line), flush=True)
@@ -293,7 +366,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
