@@ -360,6 +360,88 @@ def run_gpu(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """Batched workload: the 64 synthetic machines (uneven sizes) stepped
+    concurrently through one sdc_batch, each on its own stream; one "step" is
+    one macro step of every machine. Also times the same machines one after
+    another (each alone) for the gain of batching."""
+    import numpy as np
+    import torch
+
+    from paper_1707_03581_gb300 import Batch, Solver
+    from synth import machine_config
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    machines = machine_config(3, truncate=args.machines)
+    sc = machines[0].scheme
+    n_int = sc.M - 1 if sc.nodes == "lobatto" else sc.M
+    t_setup = time.perf_counter()
+    solvers = []
+    for mach in machines:
+        s = Solver(local, own_stream=True)
+        s.set_machine(mach, precision=args.precision)
+        solvers.append(s)
+    t_setup = time.perf_counter() - t_setup
+    dofs = np.array([s.n for s in solvers])
+    units_per_step = int(dofs.sum()) * n_int * sc.P
+    b = Batch(local)
+    for s in solvers:
+        b.add(s)
+
+    def timed(run, k):
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(torch.cuda.current_stream(local))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(k)
+        ends = []
+        for s in solvers:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(s.stream)
+            ends.append(e)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return max(start.elapsed_time(e) for e in ends), wall
+
+    b.step([args.warmup] * len(solvers), wait=True)
+    with ClockSampler(local) as clk:
+        ms, wall = timed(lambda k: b.step([k] * len(solvers), wait=False), args.steps)
+    b.synchronize()
+
+    def sequential(k):
+        for s in solvers:
+            s.run_horizon(k)
+
+    ms_seq, _ = timed(sequential, args.steps)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": units_per_step * args.steps * world / (ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"{len(machines)} machines r in {{16,24,32,48,64}} (stand r x r x 2.5r, stock "
+                               f"half resolution), {int(dofs.sum())} DOF in total ({int(dofs.min())}-"
+                               f"{int(dofs.max())} each), {sc.nodes} M={sc.M}, {sc.sweeps} sweeps, P={sc.P}, "
+                               f"dt={sc.dt} s", "precision": args.precision,
+                   "parallelism": f"one sdc_batch, {len(machines)} streams, replicas x{world}",
+                   "l2": "working set of all machines far larger than L2"},
+        "eta": args.steps * sc.dt / (ms * 1e-3),
+        "sequential": {"value": units_per_step * args.steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps,
+                       "note": "the same machines stepped one after another"},
+        "gain_vs_sequential": ms_seq / ms,
+        "host_wall_ms_per_step": 1e3 * wall / args.steps,
+        "setup_s": t_setup,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,7 +450,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=1,
+                    help="0/1/2: one machine (1 = the headline workload); 3: the batch of 64 machines")
+    ap.add_argument("--machines", type=int, default=None, help="config 3: use only the first machines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="plain kernel launches with host-driven CG loops (for kernel-level profilers)")
@@ -386,6 +470,8 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == 3:
+        run_batch(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

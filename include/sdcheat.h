@@ -100,6 +100,14 @@ typedef void (*sdc_free_fn)(void* ptr, void* user);
  * (a cudaStream_t; NULL = the legacy default stream). *out is set on success. */
 sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream);
 
+/* Create a context on `device` that creates and owns a non-blocking CUDA
+ * stream of its own (destroyed by sdc_destroy); for callers that need many
+ * distinct streams, e.g. the members of a batch. */
+sdc_status sdc_create_own_stream(sdc_ctx** out, int device);
+
+/* The context's stream (a cudaStream_t), e.g. to order the caller's work after it. */
+sdc_status sdc_get_stream(const sdc_ctx* ctx, void** stream);
+
 /* Free every device and host resource of the context (NULL is a no-op). */
 void sdc_destroy(sdc_ctx* ctx);
 
@@ -200,6 +208,41 @@ sdc_status sdc_run_horizon(sdc_ctx* ctx, int64_t n_steps, sdc_step_report* last)
 
 /* Wait for all enqueued work; returns the accumulated device status. */
 sdc_status sdc_synchronize(sdc_ctx* ctx);
+
+/* Non-blocking: *idle = 1 if every step enqueued on the context's stream has
+ * finished, else 0. Errors of finished steps surface at the next waiting call. */
+sdc_status sdc_poll(sdc_ctx* ctx, int* idle);
+
+/* ---------------------------------------------------------------- batches
+ * A batch runs the macro steps of several machines (contexts) concurrently on
+ * one GPU, the batched workloads and the serving loop of this library. Each
+ * member keeps its own device state and CUDA graph and must have its own
+ * stream (sdc_create); a batch step enqueues the members' step graphs
+ * round-robin so that their kernels and contact-loop clusters overlap on the
+ * device. Members share nothing, so every result equals the member run alone,
+ * bit for bit. The batch does not own its members: destroy them after
+ * removing them or destroying the batch. */
+typedef struct sdc_batch sdc_batch;
+
+sdc_status sdc_batch_create(sdc_batch** out, int device);
+void sdc_batch_destroy(sdc_batch* batch);
+const char* sdc_batch_last_error(const sdc_batch* batch);
+
+/* Add a ready context (assembled, scheme and temperature set) whose stream no
+ * other member uses; *index receives its position (may be NULL). */
+sdc_status sdc_batch_add(sdc_batch* batch, sdc_ctx* ctx, int32_t* index);
+
+/* Remove a member (waits for its enqueued work); positions after it shift down. */
+sdc_status sdc_batch_remove(sdc_batch* batch, sdc_ctx* ctx);
+
+sdc_status sdc_batch_size(const sdc_batch* batch, int32_t* n);
+
+/* Enqueue n_steps[i] macro steps of member i (NULL: one step each), round-robin
+ * over the members; if wait != 0, wait for all and return the first error. */
+sdc_status sdc_batch_step(sdc_batch* batch, const int64_t* n_steps, int wait);
+
+/* Wait for every member; returns the first member error. */
+sdc_status sdc_batch_synchronize(sdc_batch* batch);
 
 /* ---------------------------------------------------------------- results */
 

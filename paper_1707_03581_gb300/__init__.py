@@ -5,4 +5,4 @@ sm_103a, built in-tree by `build.build()`); `binding.Solver` is its Python
 face. Nothing here runs the simulation on the CPU.
 """
 
-from .binding import LIB_PATH, SdcError, Solver, load_library  # noqa: F401
+from .binding import LIB_PATH, Batch, SdcError, Solver, load_library  # noqa: F401

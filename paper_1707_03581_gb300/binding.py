@@ -57,6 +57,8 @@ FREE_FN = C.CFUNCTYPE(None, _vp, _vp)
 
 _SIGS = {
     "sdc_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
+    "sdc_create_own_stream": (C.c_int, [C.POINTER(_vp), C.c_int]),
+    "sdc_get_stream": (C.c_int, [_vp, C.POINTER(_vp)]),
     "sdc_destroy": (None, [_vp]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_set_allocator": (C.c_int, [_vp, ALLOC_FN, FREE_FN, _vp]),
@@ -86,6 +88,15 @@ _SIGS = {
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
+    "sdc_poll": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "sdc_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
+    "sdc_batch_destroy": (None, [_vp]),
+    "sdc_batch_last_error": (C.c_char_p, [_vp]),
+    "sdc_batch_add": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
+    "sdc_batch_remove": (C.c_int, [_vp, _vp]),
+    "sdc_batch_size": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    "sdc_batch_step": (C.c_int, [_vp, _i64p, C.c_int]),
+    "sdc_batch_synchronize": (C.c_int, [_vp]),
 }
 
 _LIB = None
@@ -126,7 +137,10 @@ def _i64(a):
 class Solver:
     """One simulation context on one GPU (wraps an sdc_ctx)."""
 
-    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True):
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True, own_stream: bool = False):
+        """stream: a torch.cuda.Stream to issue work on (default: the current stream);
+        own_stream=True: the library creates a private non-blocking stream instead
+        (PyTorch hands out pooled streams, which repeat after 32)."""
         import torch
 
         if not torch.cuda.is_available():
@@ -134,11 +148,20 @@ class Solver:
         self._torch = torch
         self.lib = load_library()
         self.device = device
-        if stream is None:
-            stream = torch.cuda.current_stream(device)
-        self.stream = stream
         h = _vp()
-        self._check_plain(self.lib.sdc_create(C.byref(h), device, _vp(stream.cuda_stream)))
+        if own_stream:
+            self._check_plain(self.lib.sdc_create_own_stream(C.byref(h), device))
+            ptr = _vp()
+            st = self.lib.sdc_get_stream(h, C.byref(ptr))
+            if st != SDC_OK:
+                self.lib.sdc_destroy(h)
+                raise SdcError(st, "sdc_get_stream failed")
+            stream = torch.cuda.ExternalStream(ptr.value, device=device)
+        else:
+            if stream is None:
+                stream = torch.cuda.current_stream(device)
+            self._check_plain(self.lib.sdc_create(C.byref(h), device, _vp(stream.cuda_stream)))
+        self.stream = stream
         self.h = h
         self._keep = []
         if torch_allocator:
@@ -339,6 +362,12 @@ class Solver:
         self._call("sdc_contact_flux", _vp(T.data_ptr()), float(t), _vp(out.data_ptr()))
         return out
 
+    def poll(self) -> bool:
+        """True once every step enqueued on this solver's stream has finished (non-blocking)."""
+        idle = C.c_int()
+        self._call("sdc_poll", C.byref(idle))
+        return bool(idle.value)
+
     def heat_totals_noalloc(self, T_ptr: int, out):
         """Stored heat of stand and stock of the device field at T_ptr, into the
         2-element float64 CUDA tensor `out`, without any device allocation
@@ -346,3 +375,63 @@ class Solver:
         concurrent calls on one device race)."""
         self._call("sdc_heat_totals_noalloc", _vp(int(T_ptr)), _vp(out.data_ptr()))
         return out
+
+
+class Batch:
+    """Several machines stepped concurrently on one GPU (wraps an sdc_batch).
+
+    Each member is a Solver with its own stream; members keep their own state,
+    so every result equals the member run alone. The batch does not own them."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = _vp()
+        st = self.lib.sdc_batch_create(C.byref(h), device)
+        if st != SDC_OK:
+            raise SdcError(st, "batch creation failed")
+        self.h = h
+        self.members = []
+
+    def _call(self, name, *args):
+        st = getattr(self.lib, name)(self.h, *args)
+        if st != SDC_OK:
+            msg = self.lib.sdc_batch_last_error(self.h)
+            raise SdcError(st, msg.decode() if msg else "")
+
+    def add(self, solver: "Solver") -> int:
+        idx = C.c_int32()
+        self._call("sdc_batch_add", solver.h, C.byref(idx))
+        self.members.append(solver)
+        return idx.value
+
+    def remove(self, solver: "Solver"):
+        self._call("sdc_batch_remove", solver.h)
+        self.members.remove(solver)
+
+    def __len__(self):
+        n = C.c_int32()
+        self._call("sdc_batch_size", C.byref(n))
+        return n.value
+
+    def step(self, n_steps=None, wait: bool = True):
+        """Enqueue n_steps[i] macro steps of member i (default one each), round-robin."""
+        if n_steps is None:
+            self._call("sdc_batch_step", None, 1 if wait else 0)
+        else:
+            arr, p = _i64(n_steps)
+            self._call("sdc_batch_step", p, 1 if wait else 0)
+
+    def synchronize(self):
+        self._call("sdc_batch_synchronize")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sdc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

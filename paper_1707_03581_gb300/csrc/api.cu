@@ -95,6 +95,7 @@ struct sdc_ctx {
     int eager = 0;                  // 1: plain launches, host-driven CG loop
     int eager_kernels = 0;          // kernels launched by the last eager step
     int* done_host = nullptr;       // pinned: CG iteration count, stop flag, SpMV runs
+    bool own_stream = false;        // stream created by sdc_create_own_stream
     cudaEvent_t done_ev = nullptr;  // marks the copy of the CG stop flag (eager loop)
 
     // per-kernel device times of eager steps (CUDA events around each launch)
@@ -1116,12 +1117,43 @@ sdc_status sdc_create(sdc_ctx** out, int device, void* cuda_stream) {
     return SDC_OK;
 }
 
+sdc_status sdc_create_own_stream(sdc_ctx** out, int device) {
+    if (!out) return SDC_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count || cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return SDC_ERR_CUDA;
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return SDC_ERR_CUDA;
+    }
+    const sdc_status r = sdc_create(out, device, st);
+    if (r != SDC_OK) {
+        cudaStreamDestroy(st);
+        return r;
+    }
+    (*out)->own_stream = true;
+    return SDC_OK;
+}
+
+sdc_status sdc_get_stream(const sdc_ctx* cc, void** stream) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(stream != nullptr, SDC_ERR_ARG, "stream is NULL");
+        *stream = (void*)c->stream;
+    });
+}
+
 void sdc_destroy(sdc_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     drop_graph(c);
     free_pool(c, c->pool_scheme);
     free_pool(c, c->pool_asm);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->done_host) cudaFreeHost(c->done_host);
     if (c->done_ev) cudaEventDestroy(c->done_ev);
@@ -1540,3 +1572,130 @@ extern "C" sdc_status sdc_heat_totals_noalloc(sdc_ctx* c, const double* T_dev, d
         SDC_CUDA_TRY(cudaGetLastError());
     });
 }
+
+// ============================================================================ batches
+
+struct sdc_batch {
+    int device = 0;
+    std::vector<sdc_ctx*> members;
+    std::string err;
+};
+
+extern "C" sdc_status sdc_poll(sdc_ctx* c, int* idle) {
+    return guarded(c, [&] {
+        require(idle != nullptr, SDC_ERR_ARG, "idle is NULL");
+        const cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaErrorNotReady) {
+            cudaGetLastError();
+            *idle = 0;
+            return;
+        }
+        SDC_CUDA_TRY(e);
+        *idle = 1;
+    });
+}
+
+namespace {
+
+template <class F>
+sdc_status batch_guarded(sdc_batch* b, F&& f) {
+    if (!b) return SDC_ERR_ARG;
+    try {
+        f();
+        return SDC_OK;
+    } catch (const ApiError& e) {
+        b->err = e.what;
+        return e.code;
+    } catch (const CudaError& e) {
+        cudaGetLastError();
+        b->err = e.what;
+        return e.code == cudaErrorMemoryAllocation ? SDC_ERR_OOM : SDC_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        b->err = "host allocation failed";
+        return SDC_ERR_OOM;
+    }
+}
+
+// a member call failed: carry its message into the batch
+void member_check(sdc_ctx* c, sdc_status st, int i) {
+    if (st != SDC_OK) throw ApiError(st, "member " + std::to_string(i) + ": " + c->err);
+}
+
+}  // namespace
+
+extern "C" sdc_status sdc_batch_create(sdc_batch** out, int device) {
+    if (!out) return SDC_ERR_ARG;
+    *out = nullptr;
+    sdc_batch* b = new (std::nothrow) sdc_batch();
+    if (!b) return SDC_ERR_OOM;
+    b->device = device;
+    *out = b;
+    return SDC_OK;
+}
+
+extern "C" void sdc_batch_destroy(sdc_batch* b) { delete b; }
+
+extern "C" const char* sdc_batch_last_error(const sdc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" sdc_status sdc_batch_add(sdc_batch* b, sdc_ctx* c, int32_t* index) {
+    return batch_guarded(b, [&] {
+        require(c != nullptr, SDC_ERR_ARG, "null context");
+        require(c->device == b->device, SDC_ERR_ARG, "the context is on another device");
+        require(c->assembled && c->scheme_set && c->temp_set, SDC_ERR_STATE,
+                "a member must be assembled, with scheme and temperature set");
+        for (sdc_ctx* m : b->members) {
+            require(m != c, SDC_ERR_ARG, "the context is already a member");
+            require(m->stream != c->stream, SDC_ERR_ARG, "every member needs its own stream");
+        }
+        b->members.push_back(c);
+        if (index) *index = (int32_t)b->members.size() - 1;
+    });
+}
+
+extern "C" sdc_status sdc_batch_remove(sdc_batch* b, sdc_ctx* c) {
+    return batch_guarded(b, [&] {
+        auto it = std::find(b->members.begin(), b->members.end(), c);
+        require(it != b->members.end(), SDC_ERR_ARG, "not a member");
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        b->members.erase(it);
+    });
+}
+
+extern "C" sdc_status sdc_batch_size(const sdc_batch* cb, int32_t* n) {
+    sdc_batch* b = const_cast<sdc_batch*>(cb);
+    return batch_guarded(b, [&] {
+        require(n != nullptr, SDC_ERR_ARG, "n is NULL");
+        *n = (int32_t)b->members.size();
+    });
+}
+
+extern "C" sdc_status sdc_batch_step(sdc_batch* b, const int64_t* n_steps, int wait) {
+    return batch_guarded(b, [&] {
+        const size_t nm = b->members.size();
+        int64_t most = 0;
+        for (size_t i = 0; i < nm; ++i) {
+            const int64_t k = n_steps ? n_steps[i] : 1;
+            require(k >= 0, SDC_ERR_ARG, "negative step count");
+            most = std::max(most, k);
+        }
+        for (size_t i = 0; i < nm; ++i) {  // graphs and buffers first, outside the launch sweep
+            sdc_ctx* c = b->members[i];
+            if ((n_steps ? n_steps[i] : 1) > 0) member_check(c, guarded(c, [&] { ensure_ready(c); }), (int)i);
+        }
+        for (int64_t s = 0; s < most; ++s)
+            for (size_t i = 0; i < nm; ++i) {
+                sdc_ctx* c = b->members[i];
+                if (s < (n_steps ? n_steps[i] : 1)) member_check(c, guarded(c, [&] { launch_step(c); }), (int)i);
+            }
+        if (wait)
+            for (size_t i = 0; i < nm; ++i) member_check(b->members[i], sdc_synchronize(b->members[i]), (int)i);
+    });
+}
+
+extern "C" sdc_status sdc_batch_synchronize(sdc_batch* b) {
+    return batch_guarded(b, [&] {
+        for (size_t i = 0; i < b->members.size(); ++i)
+            member_check(b->members[i], sdc_synchronize(b->members[i]), (int)i);
+    });
+}
+
