@@ -442,6 +442,59 @@ def run_batch(args, rank, world):
         s.close()
 
 
+def run_serving(args, rank, world):
+    """Serving workload: Poisson arrivals (rate --lam) of look-ahead requests, each a
+    machine of the 64-machine pool with horizon ~ U(30, 600) s from its resident
+    state; continuous batching on one GPU. Mixed precision and plain FP64 serve
+    the same request list; reports latency percentiles, per-request look-ahead
+    factors and aggregate throughput."""
+    import torch
+
+    from paper_1707_03581_gb300.serving import LookAheadServer, Request, summarize
+    from synth import machine_config
+    from synth.machines import serving_requests
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    machines = machine_config(3)
+    sched = serving_requests(args.lam, n_requests=args.requests, seed=0, pool=len(machines))
+    out = {}
+    for prec in ("mixed", "fp64"):
+        server = LookAheadServer(machines, device=local, precision=prec, max_active=args.max_active)
+        reqs = [Request(r["arrival_s"], round(r["horizon_s"]), r["machine_index"]) for r in sched]
+        with ClockSampler(local) as clk:
+            server.run(reqs)
+        n_dof = [m.n_dof for m in machines]
+        st = summarize(reqs, machines, n_dof)
+        st["slots"] = server.slots_made
+        st["footprint_gb"] = server.footprint / 1e9
+        st["clocks"] = clk.summary()
+        out[prec] = st
+        server.close()
+    if rank != 0:
+        return
+    mx, f64 = out["mixed"], out["fp64"]
+    line = {
+        "metric": METRIC, "value": mx["dof_substeps_per_s"] * world, "unit": UNIT, "n_gpus": world,
+        "steps": sum(round(r["horizon_s"]) for r in sched), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"serving: {args.requests} Poisson arrivals at {args.lam}/s of look-ahead requests "
+                               f"(horizon ~ U(30,600) s rounded to whole macro steps) on a pool of 64 machines "
+                               f"(12.9k-734k DOF), warm-start state kept on the device",
+                   "precision": "mixed vs fp64, same requests", "parallelism": f"continuous batching, up to "
+                   f"{args.max_active} requests in flight, replicas x{world}"},
+        "latency_s": mx["latency_s"], "eta_per_request": mx["eta_per_request"],
+        "offered_simulated_s_per_s": args.lam * sum(round(r["horizon_s"]) for r in sched) / len(sched),
+        "served_simulated_s_per_s": mx["simulated_s_per_s"],
+        "mixed": mx, "fp64": f64,
+        "gain_vs_fp64": {"throughput": mx["dof_substeps_per_s"] / f64["dof_substeps_per_s"],
+                         "p99_latency": f64["latency_s"]["p99"] / mx["latency_s"]["p99"],
+                         "p50_latency": f64["latency_s"]["p50"] / mx["latency_s"]["p50"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,8 +504,12 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
     ap.add_argument("--config", type=int, default=1,
-                    help="0/1/2: one machine (1 = the headline workload); 3: the batch of 64 machines")
+                    help="0/1/2: one machine (1 = the headline workload); 3: the batch of 64 machines; "
+                         "4: serving (Poisson arrivals)")
     ap.add_argument("--machines", type=int, default=None, help="config 3: use only the first machines")
+    ap.add_argument("--lam", type=float, default=10.0, help="config 4: arrival rate [requests/s]")
+    ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
+    ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="plain kernel launches with host-driven CG loops (for kernel-level profilers)")
@@ -472,6 +529,8 @@ def main():
         run_reference(args, rank, world)
     elif args.config == 3:
         run_batch(args, rank, world)
+    elif args.config == 4:
+        run_serving(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

@@ -202,6 +202,10 @@ sdc_status sdc_set_temperature(sdc_ctx* ctx, const double* T, double T_uniform, 
  * errors surface at the next synchronising call. */
 sdc_status sdc_step(sdc_ctx* ctx, sdc_step_report* rep);
 
+/* Enqueue n_steps macro steps on the context's stream and return at once
+ * (errors surface at the next waiting call, e.g. sdc_synchronize). */
+sdc_status sdc_step_async(sdc_ctx* ctx, int64_t n_steps);
+
 /* Enqueue n_steps macro steps back to back, then wait once; *last (if not
  * NULL) receives the report of the final step. */
 sdc_status sdc_run_horizon(sdc_ctx* ctx, int64_t n_steps, sdc_step_report* last);
@@ -245,6 +249,9 @@ sdc_status sdc_batch_step(sdc_batch* batch, const int64_t* n_steps, int wait);
 sdc_status sdc_batch_synchronize(sdc_batch* batch);
 
 /* ---------------------------------------------------------------- results */
+
+/* Device bytes the context holds (assembled system, state and scheme buffers). */
+sdc_status sdc_get_footprint(const sdc_ctx* ctx, int64_t* bytes);
 
 /* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
 sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,

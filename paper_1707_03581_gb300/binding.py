@@ -89,6 +89,8 @@ _SIGS = {
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
     "sdc_poll": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "sdc_step_async": (C.c_int, [_vp, C.c_int64]),
+    "sdc_get_footprint": (C.c_int, [_vp, _i64p]),
     "sdc_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
     "sdc_batch_destroy": (None, [_vp]),
     "sdc_batch_last_error": (C.c_char_p, [_vp]),
@@ -361,6 +363,16 @@ class Solver:
         out = self._torch.empty_like(T)
         self._call("sdc_contact_flux", _vp(T.data_ptr()), float(t), _vp(out.data_ptr()))
         return out
+
+    def step_async(self, n_steps: int = 1):
+        """Enqueue n_steps macro steps on this solver's stream and return at once."""
+        self._call("sdc_step_async", int(n_steps))
+
+    def footprint(self) -> int:
+        """Device bytes held by this context."""
+        b = C.c_int64()
+        self._call("sdc_get_footprint", C.byref(b))
+        return b.value
 
     def poll(self) -> bool:
         """True once every step enqueued on this solver's stream has finished (non-blocking)."""

@@ -28,6 +28,7 @@ struct sdc_ctx {
     sdc_free_fn free_fn = nullptr;
     void* user = nullptr;
     std::vector<void*> pool_asm, pool_scheme;
+    std::vector<size_t> pool_asm_bytes, pool_scheme_bytes;
 
     // inputs
     BodyInput body[2];
@@ -58,6 +59,8 @@ struct sdc_ctx {
     float *Dl = nullptr, *Rl = nullptr, *Ul = nullptr, *Pl = nullptr, *Wl = nullptr, *Sl = nullptr,
           *Dinv = nullptr;
     float* mass32 = nullptr;
+    float* Dsum = nullptr;          // FP32 accumulated correction of the current solve (x - x0)
+    float* dTv = nullptr;           // FP32 increment T_m - T_{m-1} of the current interval
     MixState* ms = nullptr;
     CouplingOp E1{};                // one slot, for sdc_contact_flux
     double* Ti1 = nullptr;
@@ -78,6 +81,7 @@ struct sdc_ctx {
     // per-scheme device buffers
     std::vector<double*> Tstd;      // M+1, Tstd[0] = Tn
     double* FI[2][MAX_M] = {{nullptr}};
+    double* Fn = nullptr;           // F^I(T_n) + g, formed once per macro step
     double* fe[2] = {nullptr, nullptr};
     double* ihat[2] = {nullptr, nullptr};
     double *cpre = nullptr, *fst = nullptr;
@@ -128,6 +132,7 @@ void* dalloc(sdc_ctx* c, std::vector<void*>& pool, size_t bytes) {
         }
     }
     pool.push_back(p);
+    (&pool == &c->pool_asm ? c->pool_asm_bytes : c->pool_scheme_bytes).push_back(bytes);
     return p;
 }
 
@@ -151,6 +156,7 @@ void free_pool(sdc_ctx* c, std::vector<void*>& pool) {
         else cudaFree(p);
     }
     pool.clear();
+    (&pool == &c->pool_asm ? c->pool_asm_bytes : c->pool_scheme_bytes).clear();
 }
 
 void drop_graph(sdc_ctx* c) {
@@ -442,6 +448,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.Wl = c->Wl;
     a.Sl = c->Sl;
     a.Dinv = c->Dinv;
+    a.Dsum = c->Dsum;
     a.cg = c->cgs;
     a.ms = c->ms;
     a.loop_kernels = &c->st->loop_kernels;
@@ -648,6 +655,8 @@ void do_assemble(sdc_ctx* c) {
     c->Pl = dalloc_n<float>(c, c->pool_asm, N);
     c->Wl = dalloc_n<float>(c, c->pool_asm, N);
     c->Sl = dalloc_n<float>(c, c->pool_asm, N);
+    c->Dsum = dalloc_n<float>(c, c->pool_asm, N);
+    c->dTv = dalloc_n<float>(c, c->pool_asm, N);
     c->Dinv = dalloc_n<float>(c, c->pool_asm, N);
     {
         std::vector<float> m32(c->mass_h.begin(), c->mass_h.end());
@@ -736,11 +745,12 @@ void alloc_scheme_buffers(sdc_ctx* c) {
         const bool degenerate = std::find(c->nondeg.begin(), c->nondeg.end(), m) == c->nondeg.end();
         c->Tstd[m] = degenerate ? c->Tstd[m - 1] : dalloc_n<double>(c, c->pool_scheme, N);
     }
+    c->Fn = dalloc_n<double>(c, c->pool_scheme, N);
     for (int s = 0; s < 2; ++s)
         for (int j = 0; j < M; ++j) {
             const bool degenerate = std::find(c->nondeg.begin(), c->nondeg.end(), j + 1) == c->nondeg.end();
-            if (s == 1 && degenerate) c->FI[1][j] = c->FI[0][j];  // T_j = T_n: same in every iterate
-            else c->FI[s][j] = dalloc_n<double>(c, c->pool_scheme, N);
+            // a zero-length first interval: T_1 = T_n in every iterate
+            c->FI[s][j] = degenerate ? c->Fn : dalloc_n<double>(c, c->pool_scheme, N);
         }
     for (int s = 0; s < 2; ++s) {
         c->fe[s] = dalloc_n<double>(c, c->pool_scheme, (size_t)n_int * (P + 1) * NI);
@@ -794,10 +804,39 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.chunk = c->iface_chunk;
     ch.kernel_2d(k_iface_geom, dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
 
-    // F^I at a standard node that coincides with t_n (Lobatto)
-    for (int j = 1; j <= M; ++j)
-        if (std::find(c->nondeg.begin(), c->nondeg.end(), j) == c->nondeg.end())
-            ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->FI[0][j - 1]);
+    // F^I(T_n) + g in FP64 (the only pass over K in FP64 of a mixed-precision step); a
+    // standard node at t_n (Lobatto) shares it
+    ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->Fn);
+    const bool mixed = c->precision == SDC_MIXED_FP32;
+    // F^I + g at standard node j (0 = t_n) of iterate set s
+    auto F_at = [&](int j, int set) -> const double* { return j == 0 ? c->Fn : c->FI[set][j - 1]; };
+    // mixed precision forms F^I at the nodes from the previous node's value and an FP32 SpMV of
+    // the increment; with the FP64 SDC residual enabled every F^I is a full FP64 pass instead
+    const bool fi_increment = mixed && !c->residuals;
+    auto fi = [&](int m, int set) {
+        if (fi_increment) {
+            FiDevArgs fa{};
+            fa.A = c->A;
+            fa.Fprev = F_at(m - 1, set);
+            fa.dT = c->dTv;
+            fa.F = c->FI[set][m - 1];
+            fa.n = c->n;
+            ch.kernel(k_fi_mx, row_grid(c, k_fi_mx), (unsigned)RED_BLOCK, fa);
+        } else {
+            ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv,
+                      (const double*)c->Tstd[m], c->FI[set][m - 1]);
+        }
+    };
+    auto bulk = [&](BulkArgs& b, const double* Fx0) {
+        if (mixed) {
+            b.dX = c->Dsum;
+            b.Fx0 = Fx0;
+            b.dT = c->dTv;
+            ch.kernel(k_bulk_endpoint_mx, row_grid(c, k_bulk_endpoint_mx), (unsigned)RED_BLOCK, b);
+        } else {
+            ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
+        }
+    };
 
     auto sdt_row = [&](int m, double* out) {
         for (int j = 0; j < MAX_M; ++j) out[j] = j < M ? dt * W.S[(size_t)(m - 1) * M + j] : 0.0;
@@ -847,6 +886,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.base = c->fe_base;
         ia.chunk = c->iface_chunk;
         ia.status = &c->st->status;
+        ia.dT = c->precision == SDC_MIXED_FP32 ? c->dTv : nullptr;
         ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk),
                           (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
                           (unsigned)c->iface_cluster, ia);
@@ -881,6 +921,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         r.Tprev = c->Tstd[m - 1];
         r.g = c->d_genv;
         r.x0 = c->Tstd[m - 1];
+        r.Fx0 = F_at(m - 1, 0);
         r.pos = c->C.pos;
         add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
         BulkArgs b{};
@@ -895,9 +936,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         b.n = c->n;
         b.pos = c->C.pos;
         b.fstar_I = c->fst;
-        ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
+        bulk(b, F_at(m - 1, 0));
         substeps(ii, m, RHS_PRED, 0, 0);
-        ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m], c->FI[0][m - 1]);
+        fi(m, 0);
     }
     // ---- Algorithm 2 (sweeps)
     for (int k = 1; k <= K; ++k) {
@@ -917,6 +958,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             r.ihat = c->ihat[so] + (size_t)ii * NI;
             r.pos = c->C.pos;
             r.x0 = c->Tstd[m];
+            r.Fx0 = c->FI[so][m - 1];
             add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
             BulkArgs b{};
             b.A = c->A;
@@ -934,11 +976,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.n = c->n;
             b.pos = c->C.pos;
             b.fstar_I = c->fst;
-            ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
+            bulk(b, c->FI[so][m - 1]);
             substeps(ii, m, RHS_SWEEP, so, sn);
-            if (k < K || c->residuals)
-                ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tstd[m],
-                          c->FI[sn][m - 1]);
+            if (k < K || c->residuals) fi(m, sn);
         }
     }
     if (c->residuals) residual(K & 1, K);
@@ -1043,6 +1083,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
         {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_update, "k_mx_update"},
         {(const void*)k_mx_refine, "k_mx_refine"},
+        {(const void*)k_bulk_endpoint_mx, "k_bulk_endpoint_mx"}, {(const void*)k_fi_mx, "k_fi_mx"},
     };
     for (const auto& n : names)
         if (n.first == f) return n.second;
@@ -1361,6 +1402,25 @@ sdc_status sdc_run_horizon(sdc_ctx* c, int64_t n_steps, sdc_step_report* last) {
         ensure_ready(c);
         for (int64_t i = 0; i < n_steps; ++i) launch_step(c);
         read_state(c, last);
+    });
+}
+
+sdc_status sdc_step_async(sdc_ctx* c, int64_t n_steps) {
+    return guarded(c, [&] {
+        require(n_steps >= 0, SDC_ERR_ARG, "n_steps must be >= 0");
+        ensure_ready(c);
+        for (int64_t i = 0; i < n_steps; ++i) launch_step(c);
+    });
+}
+
+sdc_status sdc_get_footprint(const sdc_ctx* cc, int64_t* bytes) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(bytes != nullptr, SDC_ERR_ARG, "bytes is NULL");
+        size_t t = 0;
+        for (size_t b : c->pool_asm_bytes) t += b;
+        for (size_t b : c->pool_scheme_bytes) t += b;
+        *bytes = (int64_t)t;
     });
 }
 

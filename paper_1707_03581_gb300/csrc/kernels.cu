@@ -204,7 +204,8 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
                 b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
             }
             const double x0 = r.x0[i];
-            const double Ax = fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
+            const double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            const double Ax = fma(a.dtau, Kx0, m * x0);
             const double res = b - Ax;
             const double d = 1.0 / (m + a.dtau * a.diagK[i]);
             a.X[i] = x0;
@@ -315,10 +316,12 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
                 b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
             }
             const double x0 = r.x0[i];
-            const double res = b - fma(a.dtau, ell_row(a.A, i, r.x0), m * x0);
+            const double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            const double res = b - fma(a.dtau, Kx0, m * x0);
             a.B[i] = b;
             a.X[i] = x0;
             a.R[i] = res;
+            a.Dsum[i] = 0.0f;
             a.Dinv[i] = 1.0f / (float)(m + a.dtau * a.diagK[i]);
             v[0] += b * b;
             v[1] += res * res;
@@ -425,22 +428,23 @@ __global__ void k_mx_update(MixArgs a) {
     }
 }
 
-// FP64 row of K applied to the FP32 correction
-__device__ __forceinline__ double ell_row_f32in(const EllDev& A, int64_t row, const float* __restrict__ x) {
-    return ell_row_t<8, double, float>(A.slice_ptr, A.col, A.val, row, x);
-}
-
-// FP64 end of a refinement pass: x += d; r -= (m d + dtau K d), i.e. the
-// residual b - A x of the corrected iterate, formed in FP64; outer stop test.
+// End of a refinement pass: x += d and r -= A d, with r and x in FP64. The
+// residual r = b - A x of the corrected iterate is thereby carried as
+//   r = r0 - A (x - x0),
+// r0 = b - A x0 formed in FP64 (k_mx_init); only the correction-sized term
+// A d of a pass is applied with the FP32 operator (an FP32 SpMV of d), so its
+// rounding is relative to the correction, not to b. Outer stop test.
 __global__ void k_mx_refine(MixArgs a) {
     double v[1] = {0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
-            const double d = (double)a.Dl[i];
-            a.X[i] += d;
-            const double res = a.R[i] - fma(a.dtau, ell_row_f32in(a.A, i, a.Dl), a.mass[i] * d);
-            a.R[i] = res;
-            v[0] += res * res;
+        const float d = a.Dl[i];
+        a.X[i] += (double)d;
+        a.Dsum[i] += d;
+        const float Ad = fmaf((float)a.dtau, ell_row32(a.A, i, a.Dl), a.mass32[i] * d);
+        const double res = a.R[i] - (double)Ad;
+        a.R[i] = res;
+        v[0] += res * res;
     }
     double out[1];
     if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
@@ -484,6 +488,38 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
         const int pa = a.pos[i];
         if (pa >= 0) a.fstar_I[pa] = fstar;
     }
+}
+
+// Mixed precision form of k_bulk_endpoint (see BulkArgs): with T* = x0 + dX,
+//   predictor: f*_m = F^I(T*) + g = F(x0) - K dX
+//   sweep:     f*_m = f^I(T*) - f^I(T^k_m) = -K dX          (x0 = T^k_m)
+// K dX as an FP32 SpMV; the increment of every row goes to dT for k_fi_mx.
+__global__ void k_bulk_endpoint_mx(BulkArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
+        const double KdX = (double)ell_row32(a.A, i, a.dX);
+        double incr, fstar;
+        if (a.mode == RHS_PRED) {
+            fstar = a.Fx0[i] - KdX;
+            incr = a.dtau * fstar;
+        } else {
+            fstar = -KdX;
+            double I = 0.0;
+            for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
+            incr = fma(a.dtau, fstar, I);
+        }
+        const double dT = incr * a.minv[i];
+        a.Tout[i] = a.Tprev[i] + dT;
+        a.dT[i] = (float)dT;
+        const int pa = a.pos[i];
+        if (pa >= 0) a.fstar_I[pa] = fstar;
+    }
+}
+
+// F^I(T_m) + g = F^I(T_prev) + g - K dT (mixed precision; FP32 SpMV of the increment)
+__global__ void k_fi_mx(FiDevArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) a.F[i] = a.Fprev[i] - (double)ell_row32(a.A, i, a.dT);
 }
 
 // ------------------------------------------------------------------ contact geometry
@@ -994,6 +1030,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         const int i = own[r];
         if (i < 0) continue;
         a.Tout[C.dof[i]] = T[r];
+        if (a.dT) a.dT[C.dof[i]] = (float)(T[r] - T0[r]);
         a.ihat_new[i] = ih[r];
     }
     // no CTA may exit while its shared memory can still be a copy destination

@@ -48,6 +48,7 @@ struct MixArgs {
     int64_t n;
     double *X, *R, *B;              // FP64 iterate, residual, right-hand side
     float *Dl, *Rl, *Ul, *Pl, *Wl, *Sl, *Dinv;   // FP32 correction, residual, u, direction, A u, A p, 1/diag
+    float* Dsum;                    // FP32 sum of the corrections of all passes (x - x0)
     int* loop_kernels;              // StepState::loop_kernels
     CgState* cg;                    // inner scalars (bb holds the inner initial ||r||^2)
     MixState* ms;                   // outer scalars
@@ -76,6 +77,9 @@ struct RhsArgs {
     const double* ihat;             // sum_q dt shat_{m,q} f^E(T^k_{m,q}) on contact DOFs (sweep)
     const int32_t* pos;             // DOF -> contact index or -1
     const double* x0;               // initial guess
+    // F^I(x0) + g if known (NULL: form m x0 + dtau K x0 with an SpMV). Then
+    // m x0 + dtau K x0 = m x0 - dtau (F^I(x0) + g - g) needs no pass over K.
+    const double* Fx0;
 };
 
 // Bulk endpoint update after the solve (see k_bulk_endpoint).
@@ -95,6 +99,21 @@ struct BulkArgs {
     int64_t n;
     const int32_t* pos;             // DOF -> contact index or -1
     double* fstar_I;                // [NI] f*_m on the contact DOFs (output)
+    // mixed precision (k_bulk_endpoint_mx): T* = x0 + dX with dX the solve's accumulated FP32
+    // correction, so K T* = K x0 + K dX with K x0 known through F^I(x0); the pass over K is
+    // an FP32 SpMV of dX. The output increment T_m - T_{m-1} goes to dT (FP32).
+    const float* dX;
+    const double* Fx0;              // F^I(x0) + g (x0 = T_{m-1} in the predictor, T^k_m in a sweep)
+    float* dT;
+};
+
+// F^I(T_m) + g = F^I(T_prev) + g - K (T_m - T_prev) with the increment dT in FP32 (mixed precision).
+struct FiDevArgs {
+    EllDev A;
+    const double* Fprev;
+    const float* dT;
+    double* F;
+    int64_t n;
 };
 
 // Precomputed coupling operator f^E(T, tau_s)_a = cst[s][a] + sum_k coef[s][k][a] T_I[idx[s][k][a]].
@@ -171,6 +190,7 @@ struct IfaceArgs {
     double* ihat_new;               // [NI]
     const double* base;             // mixed: [(P+1)][NI] f^E(T_{m-1}, tau_{m,q}) from k_iface_prep
     int chunk;                      // replica slots per CTA (the cluster size is the grid)
+    float* dT;                      // mixed: T_m - T_{m-1} on the contact rows (output), or NULL
     int* status;                    // sticky status word (SDC_ERR_TIMEOUT if an exchange wait gives up)
 };
 
@@ -201,6 +221,8 @@ __global__ void k_mx_spmv(MixArgs a);
 __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_refine(MixArgs a);
 __global__ void k_bulk_endpoint(BulkArgs a);
+__global__ void k_bulk_endpoint_mx(BulkArgs a);
+__global__ void k_fi_mx(FiDevArgs a);
 __global__ void k_iface_geom(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,
                                 int phase);
