@@ -176,6 +176,12 @@ sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
  * debugging. Results are identical. */
 sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
 
+/* Placement of the contact substep loop's replicas of the contact temperatures:
+ * 0 (default) = shared memory of each CTA of the loop's cluster when they fit,
+ * else global memory; 1 = always global memory (for tests and tuning).
+ * Results are identical. */
+sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
+
 /* Measurement aid for eager execution (sdc_set_execution(ctx, 1)): when on,
  * every kernel launch of a step is bracketed by CUDA events on the
  * context's stream and each step waits for its launches, summing the

@@ -88,6 +88,9 @@ struct sdc_ctx {
     double* fe_base = nullptr;      // mixed: f^E(T_{m-1}) at the interval's embedded nodes
     int iface_cluster = 0;          // CTAs of the substep-loop cluster
     int iface_chunk = 0;            // replica slots per CTA of that cluster
+    bool iface_global = false;      // replicas in global memory (large interfaces)
+    int force_global = 0;           // sdc_set_contact_replicas
+    void* iface_rep = nullptr;      // their buffers
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
     double *w_Stil = nullptr, *w_Semb = nullptr, *w_Shat = nullptr, *w_emb = nullptr, *w_slot = nullptr;
@@ -566,8 +569,7 @@ void do_assemble(sdc_ctx* c) {
     C = ContactDev{};
     C.n_iface = (int)H.dof.size();
     require(C.n_iface <= IFACE_MAX_NI, SDC_ERR_ARG,
-            "the contact interface has more than 14,336 DOFs (the substep loop keeps two replicas of it in "
-            "each CTA's shared memory)");
+            "the contact interface has more than 32,768 DOFs (16 CTAs x 512 threads x 4 DOFs of the substep loop)");
     C.n_iface_fix = H.n_iface_fix;
     C.nq_fix = H.nq_fix;
     C.nq_mov = H.nq_mov;
@@ -680,36 +682,55 @@ void do_assemble(sdc_ctx* c) {
     c->assembled = true;
 }
 
-// The substep-loop kernel for a precision and a chunk size (one DOF per
-// thread when the chunk fits the block).
+// The substep-loop kernel for a precision, a chunk size and the replica placement
+// (one DOF per thread when the chunk fits the block; global replicas when two
+// shared-memory replicas do not fit in a CTA).
 using IfaceKernel = void (*)(IfaceArgs);
-IfaceKernel iface_loop_kernel(bool mixed, int chunk) {
+IfaceKernel iface_loop_kernel(bool mixed, int chunk, bool global) {
+    if (global) return mixed ? k_iface_loop_mx_gl : k_iface_loop_gl;
     const bool one = chunk <= IFACE_THREADS;
     if (mixed) return one ? k_iface_loop_mx1 : k_iface_loop_mx;
     return one ? k_iface_loop1 : k_iface_loop;
 }
 
-// Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule with the
-// substep loop's shared-memory replicas and that has room for every contact
-// DOF. A CTA owns `chunk` replica slots (a multiple of 4, so that every
-// chunk is a whole number of 16-byte units for the bulk copies).
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule for the
+// substep loop with room for every contact DOF. A CTA owns `chunk` replica
+// slots (a multiple of 4, so that every chunk is a whole number of 16-byte
+// units for the bulk copies); the replicas live in shared memory when both
+// buffers fit, else in global memory.
 void pick_iface_cluster(sdc_ctx* c) {
     const int NI = std::max(c->C.n_iface, 1);
     const bool mixed = c->precision == SDC_MIXED_FP32;
     const size_t esz = mixed ? sizeof(float) : sizeof(double);
-    // the largest size any context may use, so that contexts with different interfaces coexist
-    const int max_chunk = ((IFACE_MAX_NI + IFACE_MAX_CLUSTER - 1) / IFACE_MAX_CLUSTER + 3) & ~3;
-    for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_mx,
-                          (const void*)k_iface_loop_mx1}) {
-        SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(2 * IFACE_MAX_CLUSTER * max_chunk * sizeof(double))));
+    // dynamic shared memory a loop CTA may use: the device's opt-in limit per block less the
+    // kernels' static shared memory (their mbarriers)
+    int optin = 0;
+    SDC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    size_t smem_cap = (size_t)optin;
+    for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
+                          (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
+                          (const void*)k_iface_loop_mx_gl}) {
+        cudaFuncAttributes fa{};
+        SDC_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+        smem_cap = std::min(smem_cap, (size_t)optin - fa.sharedSizeBytes);
+    }
+    for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
+                          (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
+                          (const void*)k_iface_loop_mx_gl}) {
+        SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
     for (int cs = IFACE_MAX_CLUSTER; cs >= 1; cs /= 2) {
         const int chunk = ((NI + cs - 1) / cs + 3) & ~3;
-        if (chunk > IFACE_THREADS * IFACE_PER_THREAD) break;
-        const size_t smem = 2 * (size_t)cs * chunk * esz;
-        const void* kern = (const void*)iface_loop_kernel(mixed, chunk);
+        const size_t rep_bytes = 2 * (size_t)cs * chunk * esz;
+        bool global;
+        if (!c->force_global && chunk <= IFACE_THREADS * IFACE_PER_THREAD &&
+            rep_bytes <= smem_cap)
+            global = false;
+        else if (chunk <= IFACE_THREADS * IFACE_PER_THREAD_GL) global = true;
+        else break;
+        const size_t smem = global ? 0 : rep_bytes;
+        const void* kern = (const void*)iface_loop_kernel(mixed, chunk, global);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(IFACE_THREADS);
@@ -726,6 +747,8 @@ void pick_iface_cluster(sdc_ctx* c) {
             c->iface_cluster = cs;
             c->iface_chunk = chunk;
             c->iface_smem = smem;
+            c->iface_global = global;
+            c->iface_rep = global ? dalloc(c, c->pool_scheme, rep_bytes) : nullptr;
             return;
         }
         cudaGetLastError();
@@ -763,9 +786,9 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     const size_t slots = (size_t)n_int * (P + 1);
     c->E.cnt = dalloc_n<int32_t>(c, c->pool_scheme, slots * NI);
     c->E.idx = dalloc_n<int32_t>(c, c->pool_scheme, slots * MAXE * NI);
-    c->E.coef = dalloc_n<double>(c, c->pool_scheme, slots * MAXE * NI);
-    c->E.cst = dalloc_n<double>(c, c->pool_scheme, slots * NI);
     const bool mixed = c->precision == SDC_MIXED_FP32;
+    c->E.coef = mixed ? nullptr : dalloc_n<double>(c, c->pool_scheme, slots * MAXE * NI);
+    c->E.cst = dalloc_n<double>(c, c->pool_scheme, slots * NI);
     c->E.coef32 = mixed ? dalloc_n<float>(c, c->pool_scheme, slots * MAXE * NI) : nullptr;
     c->fe_base = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)(P + 1) * NI) : nullptr;
     // dt-scaled weights
@@ -802,7 +825,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.loop_kernels = &c->st->loop_kernels;
     ga.cs = c->iface_cluster;
     ga.chunk = c->iface_chunk;
-    ch.kernel_2d(k_iface_geom, dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
+    ch.kernel_2d(c->precision == SDC_MIXED_FP32 ? k_iface_geom_mx : k_iface_geom,
+                 dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
 
     // F^I(T_n) + g in FP64 (the only pass over K in FP64 of a mixed-precision step); a
     // standard node at t_n (Lobatto) shares it
@@ -887,7 +911,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.chunk = c->iface_chunk;
         ia.status = &c->st->status;
         ia.dT = c->precision == SDC_MIXED_FP32 ? c->dTv : nullptr;
-        ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk),
+        ia.rep_global = c->iface_rep;
+        ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global),
                           (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
                           (unsigned)c->iface_cluster, ia);
     };
@@ -1075,9 +1100,11 @@ const char* kernel_name(const void* f) {
         {(const void*)k_cg_init, "k_cg_init"},         {(const void*)k_cg_spmv, "k_cg_spmv"},
         {(const void*)k_cg_update, "k_cg_update"},
         {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
+        {(const void*)k_iface_geom_mx, "k_iface_geom_mx"},
         {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_loop, "k_iface_loop"},
         {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
+        {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
         {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
@@ -1333,6 +1360,14 @@ sdc_status sdc_set_scheme(sdc_ctx* c, sdc_nodes nodes, int M, int P, int sweeps,
 sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
     return guarded(c, [&] {
         c->eager = eager ? 1 : 0;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
+    return guarded(c, [&] {
+        c->force_global = global ? 1 : 0;
+        c->buffers_ready = false;
         c->graph_ready = false;
     });
 }

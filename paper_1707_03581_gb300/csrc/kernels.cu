@@ -533,7 +533,8 @@ __device__ __forceinline__ void motion_at(const ContactDev& C, double tau, doubl
 }
 
 // Merge c into the row's entry for `node` (entry k of this thread at idx[k * GEOM_THREADS]).
-__device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, int node, double c, bool& overflow) {
+template <typename R>
+__device__ __forceinline__ void add_entry(int32_t* idx, R* coef, int& n, int node, R c, bool& overflow) {
     for (int k = 0; k < n; ++k)
         if (idx[k * GEOM_THREADS] == node) {
             coef[k * GEOM_THREADS] += c;
@@ -557,7 +558,14 @@ __device__ __forceinline__ void add_entry(int32_t* idx, double* coef, int& n, in
 // of v, and the 2x2 rule is the product of two 2-point rules, so every
 // coefficient is a product of two one-dimensional sums:
 //   int phi^Q_a phi^X_c = [sum_g w_g l^Q_a(u_g) l^X_c(u_g)] [sum_g w_g l^Q_a(v_g) l^X_c(v_g)].
-__global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
+// The search for overlapping faces and the overlap bounds are FP64. The
+// integrals take coordinates relative to the low corner of Q (formed in
+// FP64) and run in R: FP64 for the FP64 path; FP32 for mixed precision,
+// whose coefficients enter only through products with temperature
+// differences (see k_iface_prep), on GB300's wide FP32 pipes instead of
+// its narrow FP64 pipe.
+template <typename R>
+__device__ __forceinline__ void iface_geom_impl(const GeomArgs& g) {
     const ContactDev& C = g.C;
     const int NI = C.n_iface;
     const int s = (int)blockIdx.y;
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
     // the slot's motion, once per block
     __shared__ double mot[3];
     __shared__ int32_t s_idx[MAXE * GEOM_THREADS];
-    __shared__ double s_coef[MAXE * GEOM_THREADS];
+    __shared__ R s_coef[MAXE * GEOM_THREADS];
     if (threadIdx.x == 0) {
         double tau;
         if (g.use_fixed) {
@@ -579,11 +587,12 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
     }
     __syncthreads();
     if (a >= NI) return;
-    const double du = mot[0], dv = mot[1], q = mot[2];
+    const double du = mot[0], dv = mot[1];
+    const R q = (R)mot[2];
     int32_t* idx = s_idx + threadIdx.x;
-    double* coef = s_coef + threadIdx.x;
+    R* coef = s_coef + threadIdx.x;
     const bool stock = a >= C.n_iface_fix;
-    const double h_c = C.h_c;
+    const R h_c = (R)C.h_c;
     {
         // no face of this DOF can touch the other body's contact faces: empty row
         Rect4 mine = C.dof_box[a], other = stock ? C.box_fix : C.box_mov;
@@ -599,11 +608,11 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
             return;
         }
     }
-    const double gp = 0.57735026918962576451;  // 1/sqrt(3)
+    const R gp = (R)0.57735026918962576451;  // 1/sqrt(3)
 
     int n = 0;
     bool overflow = false;
-    double cst = 0.0;
+    R cst = 0;
     const BinsDev& B = stock ? C.bins_fix : C.bins_mov;
     for (int e = C.inc_ptr[a]; e < C.inc_ptr[a + 1]; ++e) {
         const int Qf = C.inc_quad[e];
@@ -614,6 +623,8 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
             Q.x += du; Q.z += du; Q.y += dv; Q.w += dv;
         }
         const double2 qi = C.rinv[Qf];
+        const R qix = (R)qi.x, qiy = (R)qi.y;
+        const R qwu = (R)(Q.z - Q.x), qwv = (R)(Q.w - Q.y);
         const int4 qn = C.qnode[Qf];
         // query rectangle in the partner body's frame (stock partners are in reference position)
         const double su = stock ? 0.0 : du, sv = stock ? 0.0 : dv;
@@ -629,42 +640,37 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
                 const int bin = iv * B.nu + iu;
                 for (int t = B.ptr[bin]; t < B.ptr[bin + 1]; ++t) {
                     const int Rf = B.item[t];
-                    Rect4 R = C.rect[Rf];
-                    {
-                        // FP32 prefilter (a margin of 1e-4 of the face size keeps it conservative);
-                        // the exact FP64 test follows
-                        const float su_ = stock ? 0.f : (float)du, sv_ = stock ? 0.f : (float)dv;
-                        const float mu = 1e-4f * (float)(Q.z - Q.x), mv = 1e-4f * (float)(Q.w - Q.y);
-                        const float ra = fmaxf((float)Q.x, (float)R.x + su_), rb = fminf((float)Q.z, (float)R.z + su_);
-                        const float sa = fmaxf((float)Q.y, (float)R.y + sv_), sb = fminf((float)Q.w, (float)R.w + sv_);
-                        if (rb < ra - mu || sb < sa - mv) continue;
-                    }
+                    Rect4 Rr = C.rect[Rf];
                     if (!stock) {
-                        R.x += du; R.z += du; R.y += dv; R.w += dv;
+                        Rr.x += du; Rr.z += du; Rr.y += dv; Rr.w += dv;
                     }
-                    const double ua = fmax(Q.x, R.x), ub = fmin(Q.z, R.z);
-                    const double va = fmax(Q.y, R.y), vb = fmin(Q.w, R.w);
+                    const double ua = fmax(Q.x, Rr.x), ub = fmin(Q.z, Rr.z);
+                    const double va = fmax(Q.y, Rr.y), vb = fmin(Q.w, Rr.w);
                     if (!(ub > ua && vb > va)) continue;
+                    // coordinates relative to the low corner of Q
+                    const R ua_ = (R)(ua - Q.x), ub_ = (R)(ub - Q.x), va_ = (R)(va - Q.y), vb_ = (R)(vb - Q.y);
+                    const R rlu = (R)(Rr.x - Q.x), rhu = (R)(Rr.z - Q.x), rlv = (R)(Rr.y - Q.y), rhv = (R)(Rr.w - Q.y);
                     const double2 ri = C.rinv[Rf];
+                    const R rix = (R)ri.x, riy = (R)ri.y;
                     const int4 rn = C.qnode[Rf];
-                    const double hu = 0.5 * (ub - ua), hv = 0.5 * (vb - va);
-                    const double cu = 0.5 * (ua + ub), cv = 0.5 * (va + vb);
-                    const double u[2] = {cu - gp * hu, cu + gp * hu};
-                    const double v[2] = {cv - gp * hv, cv + gp * hv};
+                    const R hu = R(0.5) * (ub_ - ua_), hv = R(0.5) * (vb_ - va_);
+                    const R cu = R(0.5) * (ua_ + ub_), cv = R(0.5) * (va_ + vb_);
+                    const R u[2] = {cu - gp * hu, cu + gp * hu};
+                    const R v[2] = {cv - gp * hv, cv + gp * hv};
                     // linear factors at the Gauss abscissae: index 0 = low-side node, 1 = high-side node
-                    double lqu[2][2], lru[2][2], lqv[2][2], lrv[2][2];
+                    R lqu[2][2], lru[2][2], lqv[2][2], lrv[2][2];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        lqu[1][k] = (u[k] - Q.x) * qi.x;
-                        lqu[0][k] = (Q.z - u[k]) * qi.x;
-                        lru[1][k] = (u[k] - R.x) * ri.x;
-                        lru[0][k] = (R.z - u[k]) * ri.x;
-                        lqv[1][k] = (v[k] - Q.y) * qi.y;
-                        lqv[0][k] = (Q.w - v[k]) * qi.y;
-                        lrv[1][k] = (v[k] - R.y) * ri.y;
-                        lrv[0][k] = (R.w - v[k]) * ri.y;
+                        lqu[1][k] = u[k] * qix;
+                        lqu[0][k] = (qwu - u[k]) * qix;
+                        lru[1][k] = (u[k] - rlu) * rix;
+                        lru[0][k] = (rhu - u[k]) * rix;
+                        lqv[1][k] = v[k] * qiy;
+                        lqv[0][k] = (qwv - v[k]) * qiy;
+                        lrv[1][k] = (v[k] - rlv) * riy;
+                        lrv[0][k] = (rhv - v[k]) * riy;
                     }
-                    double iqu[2], iru[2], iqv[2], irv[2];
+                    R iqu[2], iru[2], iqv[2], irv[2];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         iqu[c] = hu * fma(lqu[au][0], lqu[c][0], lqu[au][1] * lqu[c][1]);
@@ -672,13 +678,13 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
                         iqv[c] = hv * fma(lqv[av][0], lqv[c][0], lqv[av][1] * lqv[c][1]);
                         irv[c] = hv * fma(lqv[av][0], lrv[c][0], lqv[av][1] * lrv[c][1]);
                     }
-                    cst += 0.5 * q * (hu * (lqu[au][0] + lqu[au][1])) * (hv * (lqv[av][0] + lqv[av][1]));
+                    cst += R(0.5) * q * (hu * (lqu[au][0] + lqu[au][1])) * (hv * (lqv[av][0] + lqv[av][1]));
                     const int qnc[4] = {qn.x, qn.y, qn.z, qn.w};
                     const int rnc[4] = {rn.x, rn.y, rn.z, rn.w};
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        add_entry(idx, coef, n, qnc[c], -h_c * iqu[c & 1] * iqv[c >> 1], overflow);
-                        add_entry(idx, coef, n, rnc[c], h_c * iru[c & 1] * irv[c >> 1], overflow);
+                        add_entry<R>(idx, coef, n, qnc[c], -h_c * iqu[c & 1] * iqv[c >> 1], overflow);
+                        add_entry<R>(idx, coef, n, rnc[c], h_c * iru[c & 1] * irv[c >> 1], overflow);
                     }
                 }
             }
@@ -686,16 +692,20 @@ __global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) {
     if (overflow) atomicExch(g.status, (int)SDC_ERR_ARG);
     const size_t so = (size_t)s * NI + a;
     g.E.cnt[so] = n;
-    g.E.cst[so] = cst;
+    g.E.cst[so] = (double)cst;
     for (int k = 0; k < n; ++k) {
         const size_t o = ((size_t)s * MAXE + k) * NI + a;
         const int j = idx[k * GEOM_THREADS];
         g.E.idx[o] = g.cs ? (j % g.cs) * g.chunk + j / g.cs : j;
-        const double cf = coef[k * GEOM_THREADS];
-        g.E.coef[o] = cf;
+        const R cf = coef[k * GEOM_THREADS];
+        if (g.E.coef) g.E.coef[o] = (double)cf;
         if (g.E.coef32) g.E.coef32[o] = (float)cf;
     }
 }
+
+__global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom(GeomArgs g) { iface_geom_impl<double>(g); }
+
+__global__ void __launch_bounds__(GEOM_THREADS) k_iface_geom_mx(GeomArgs g) { iface_geom_impl<float>(g); }
 
 __device__ __forceinline__ double apply_coupling(const CouplingOp& E, int slot, int NI, int a, const double* T) {
     const size_t so = (size_t)slot * NI + a;
@@ -736,14 +746,21 @@ __device__ __forceinline__ void coupling_prefetch(const CouplingOp& E, int slot,
 // cst + sum_k coef_k T[idx_k] on a replica of T_I in this CTA's shared memory,
 // in entry order; the entries past the prefetched batch are fetched 16 at a
 // time with all loads of a round issued together.
-template <int B>
+// replica element: shared memory, or global memory written by other CTAs (read through L2)
+template <bool GL, typename V>
+__device__ __forceinline__ V rep_load(const V* p) {
+    if constexpr (GL) return __ldcg(p);
+    else return *p;
+}
+
+template <int B, bool GL = false>
 __device__ __forceinline__ double coupling_apply_shared(const CouplingOp& E, int slot, int NI, int a,
                                                         const CouplingRowT<B>& r, const double* Tsh) {
     constexpr int B2 = 16;  // later rounds
     double acc = r.cst;
 #pragma unroll
     for (int k = 0; k < B; ++k)
-        if (k < r.n) acc = fma(r.coef[k], Tsh[r.idx[k]], acc);
+        if (k < r.n) acc = fma(r.coef[k], rep_load<GL>(Tsh + r.idx[k]), acc);
     for (int k0 = B; k0 < r.n; k0 += B2) {
         int id[B2];
         double cf[B2];
@@ -758,7 +775,7 @@ __device__ __forceinline__ double coupling_apply_shared(const CouplingOp& E, int
         }
 #pragma unroll
         for (int j = 0; j < B2; ++j)
-            if (k0 + j < r.n) acc = fma(cf[j], Tsh[id[j]], acc);
+            if (k0 + j < r.n) acc = fma(cf[j], rep_load<GL>(Tsh + id[j]), acc);
     }
     return acc;
 }
@@ -783,14 +800,14 @@ __device__ __forceinline__ void coupling_prefetch32(const CouplingOp& E, int slo
 }
 
 // sum_k coef32_k dT[idx_k] in FP32 on a shared-memory replica of the deviations dT
-template <int B>
+template <int B, bool GL = false>
 __device__ __forceinline__ float coupling_apply_shared32(const CouplingOp& E, int slot, int NI, int a,
                                                          const CouplingRow32T<B>& r, const float* dT) {
     constexpr int B2 = 16;
     float acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < B; ++k)
-        if (k < r.n) acc = fmaf(r.coef[k], dT[r.idx[k]], acc);
+        if (k < r.n) acc = fmaf(r.coef[k], rep_load<GL>(dT + r.idx[k]), acc);
     for (int k0 = B; k0 < r.n; k0 += B2) {
         int id[B2];
         float cf[B2];
@@ -805,7 +822,7 @@ __device__ __forceinline__ float coupling_apply_shared32(const CouplingOp& E, in
         }
 #pragma unroll
         for (int j = 0; j < B2; ++j)
-            if (k0 + j < r.n) acc = fmaf(cf[j], dT[id[j]], acc);
+            if (k0 + j < r.n) acc = fmaf(cf[j], rep_load<GL>(dT + id[j]), acc);
     }
     return acc;
 }
@@ -836,16 +853,20 @@ __global__ void k_iface_prep(PrepArgs a) {
     if (gid >= (int64_t)NI * (a.P + 1)) return;
     const int p = (int)(gid / NI), i = (int)(gid % NI);
     if (a.base) {
-        // f^E(T_{m-1}, tau_{m,p}) in FP64: the part of the coupling the substeps do not change
+        // f^E(T_{m-1}, tau_{m,p}) in FP64 from the FP32 coefficients: the exchange
+        // coefficients of a row sum to zero (both bodies' shape functions are partitions of
+        // unity on every overlap), so f^E = cst + sum_k coef_k (T_k - T_a) exactly, and the
+        // coefficients' rounding multiplies temperature differences, not the temperature
         const int slot = a.slot0 + p;
         const size_t so = (size_t)slot * NI + i;
         const int n = a.E.cnt[so];
+        const double Ta = a.Tprev[a.C.dof[i]];
         double acc = a.E.cst[so];
         for (int k = 0; k < n; ++k) {
             const size_t o = ((size_t)slot * MAXE + k) * NI + i;
             const int pos = a.E.idx[o];
             const int j = pos / a.chunk + a.cs * (pos % a.chunk);  // replica position -> contact DOF
-            acc = fma(a.E.coef[o], a.Tprev[a.C.dof[j]], acc);
+            acc = fma((double)a.E.coef32[o], a.Tprev[a.C.dof[j]] - Ta, acc);
         }
         a.base[(size_t)p * NI + i] = acc;
     }
@@ -906,10 +927,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 //   stays FP64.
 // Every f^E of the current iterate is stored for the next sweep, and
 // ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m) is accumulated.
-template <bool MIX, int PER>
+template <bool MIX, int PER, bool GL>
 __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     // one contact DOF per thread leaves registers to prefetch a whole typical row
-    constexpr int B = PER == 1 ? (MIX ? 24 : 16) : IFACE_BATCH;
+    constexpr int B = PER == 1 ? (MIX ? 24 : 16) : (PER == 2 ? IFACE_BATCH : 4);
     using V = typename std::conditional<MIX, float, double>::type;
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ __align__(8) unsigned long long mbar[2];
@@ -920,7 +941,9 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     const int rank = (int)cluster.block_rank();
     const int chunk = a.chunk;
     const int P = a.P;
-    V* rep = reinterpret_cast<V*>(dyn);  // [2][cs * chunk]
+    // [2][cs * chunk]: shared memory, or (GL) global memory for interfaces whose replicas do not
+    // fit in shared memory; then owners store their chunk and a cluster barrier publishes it
+    V* rep = GL ? (V*)a.rep_global : reinterpret_cast<V*>(dyn);
     const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
 
     int own[PER], slot[PER];
@@ -934,9 +957,16 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         ih[r] = 0.0;
     }
     // buffer 0 = the replica at tau_{m,0}: T_{m-1} (FP64) or zero deviations (mixed)
-    for (int pos = threadIdx.x; pos < cs * chunk; pos += IFACE_THREADS) {
-        const int j = pos / chunk + cs * (pos % chunk);
-        rep[pos] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
+    if constexpr (GL) {
+        for (int sl = threadIdx.x; sl < chunk; sl += IFACE_THREADS) {
+            const int j = rank + cs * sl;
+            rep[rank * chunk + sl] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
+        }
+    } else {
+        for (int pos = threadIdx.x; pos < cs * chunk; pos += IFACE_THREADS) {
+            const int j = pos / chunk + cs * (pos % chunk);
+            rep[pos] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
+        }
     }
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[b])), "r"(1));
@@ -959,7 +989,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             } else {
                 CouplingRowT<B> row;
                 coupling_prefetch(a.E, a.slot0, NI, i, row);
-                f0 = coupling_apply_shared(a.E, a.slot0, NI, i, row, rep);
+                f0 = coupling_apply_shared<B, GL>(a.E, a.slot0, NI, i, row, rep);
             }
         } else {
             f0 = a.first ? a.fe_old[i] : a.fe_prev_end[i];
@@ -993,6 +1023,9 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             T[r] = fma(fma(dtp, fe[r], cp), mi[r], T[r]);
             buf[rank * chunk + slot[r]] = MIX ? (V)(T[r] - T0[r]) : (V)T[r];
         }
+        if constexpr (GL) {
+            cluster.sync();  // the chunks of this substep are in global memory
+        } else {
         // generic-proxy writes of the own chunk become visible to the bulk copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -1014,12 +1047,13 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         }
         if (!timed_out && !mbar_wait(smem_addr(&mbar[b]), phase[b])) timed_out = true;
         phase[b] ^= 1u;
+        }
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
             const int i = own[r];
             if (i < 0) continue;
-            if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32(a.E, a.slot0 + p, NI, i, row[r], buf);
-            else fe[r] = coupling_apply_shared(a.E, a.slot0 + p, NI, i, row[r], buf);
+            if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
+            else fe[r] = coupling_apply_shared<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
             a.fe_new[(size_t)p * NI + i] = fe[r];
             ih[r] = fma(a.Shat[p - 1], fe[r], ih[r]);
         }
@@ -1037,15 +1071,14 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     cluster.sync();
 }
 
-// one contact DOF per thread (chunk <= IFACE_THREADS) / up to IFACE_PER_THREAD
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop1(IfaceArgs a) { iface_loop_impl<false, 1>(a); }
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) {
-    iface_loop_impl<false, IFACE_PER_THREAD>(a);
-}
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx1(IfaceArgs a) { iface_loop_impl<true, 1>(a); }
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx(IfaceArgs a) {
-    iface_loop_impl<true, IFACE_PER_THREAD>(a);
-}
+// shared-memory replicas with one (chunk <= IFACE_THREADS) or two contact DOFs per thread;
+// global replicas with up to four (interfaces too large for shared memory)
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop1(IfaceArgs a) { iface_loop_impl<false, 1, false>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop(IfaceArgs a) { iface_loop_impl<false, 2, false>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_gl(IfaceArgs a) { iface_loop_impl<false, 4, true>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx1(IfaceArgs a) { iface_loop_impl<true, 1, false>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx(IfaceArgs a) { iface_loop_impl<true, 2, false>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx_gl(IfaceArgs a) { iface_loop_impl<true, 4, true>(a); }
 
 // ------------------------------------------------------------------ diagnostics
 

@@ -9,10 +9,11 @@ constexpr int MAXE = 32;            // coupling entries per contact DOF and subs
 constexpr int GEOM_THREADS = 64;    // threads per block of k_iface_geom (one slot per block row)
 constexpr int IFACE_MAX_CLUSTER = 16;   // CTAs of the substep-loop cluster (at most)
 constexpr int IFACE_THREADS = 512;      // threads per CTA of that cluster
-constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of the loop can own
+constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of a shared-memory-replica loop owns
+constexpr int IFACE_PER_THREAD_GL = 4;  // the same for the global-replica loop
 constexpr int IFACE_BATCH = 8;          // coupling entries fetched per round
-// largest contact interface the loop takes: two shared-memory replicas of T_I per CTA
-constexpr int IFACE_MAX_NI = 14336;
+// largest contact interface the loop takes (global replicas, 16 CTAs x 512 threads x 4)
+constexpr int IFACE_MAX_NI = 32768;
 
 enum RhsMode { RHS_GIVEN = 0, RHS_PRED = 1, RHS_SWEEP = 2 };
 
@@ -191,6 +192,7 @@ struct IfaceArgs {
     const double* base;             // mixed: [(P+1)][NI] f^E(T_{m-1}, tau_{m,q}) from k_iface_prep
     int chunk;                      // replica slots per CTA (the cluster size is the grid)
     float* dT;                      // mixed: T_m - T_{m-1} on the contact rows (output), or NULL
+    void* rep_global;               // [2][cs * chunk] replica buffers of the global-replica loop
     int* status;                    // sticky status word (SDC_ERR_TIMEOUT if an exchange wait gives up)
 };
 
@@ -224,13 +226,16 @@ __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_bulk_endpoint_mx(BulkArgs a);
 __global__ void k_fi_mx(FiDevArgs a);
 __global__ void k_iface_geom(GeomArgs g);
+__global__ void k_iface_geom_mx(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,
                                 int phase);
 __global__ void k_iface_prep(PrepArgs a);
 __global__ void k_iface_loop(IfaceArgs a);
 __global__ void k_iface_loop1(IfaceArgs a);
+__global__ void k_iface_loop_gl(IfaceArgs a);
 __global__ void k_iface_loop_mx(IfaceArgs a);
 __global__ void k_iface_loop_mx1(IfaceArgs a);
+__global__ void k_iface_loop_mx_gl(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,
                        unsigned int* counter, double* heat);

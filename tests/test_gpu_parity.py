@@ -304,3 +304,20 @@ def test_mixed_eager_matches_graph(torch):
     assert ra["kernel_launches"] == rb["kernel_launches"]
     kt = b.kernel_times()
     assert kt["k_mx_spmv"][0] > 0 and "k_cg_spmv" not in kt
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
+    # the loop form for interfaces too large for shared memory, forced on a small machine
+    mach = machine_config(0)
+    a = _solver(mach, precision=precision)
+    b = _solver(mach, precision=precision)
+    b.set_contact_replicas(True)
+    for _ in range(3):
+        a.step(report=True)
+        b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    b.set_execution(True)
+    b.set_kernel_timing(True)
+    b.step(report=True)
+    assert any(k.endswith("_gl") for k in b.kernel_times())
