@@ -52,7 +52,9 @@ struct sdc_ctx {
     StepState* st_host = nullptr;   // pinned
     CgState* cgs = nullptr;
     double* partials = nullptr;
+    double* gpartials = nullptr;    // group totals of the two-level reduction
     unsigned int* counter = nullptr;
+    size_t n_counters = 0;
     double *X = nullptr, *R = nullptr, *U = nullptr, *P = nullptr, *Wv = nullptr, *S = nullptr, *D = nullptr;
     // mixed precision: FP64 right-hand side, FP32 inner vectors, FP32 mass, outer scalars
     double* Bv = nullptr;
@@ -335,6 +337,7 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
     a.cg = c->cgs;
     a.loop_kernels = &c->st->loop_kernels;
     a.partials = c->partials;
+    a.gpartials = c->gpartials;
     a.counter = c->counter;
     a.iters_out = &c->st->cg_iters[solve_idx];
     a.status = &c->st->status;
@@ -456,6 +459,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.ms = c->ms;
     a.loop_kernels = &c->st->loop_kernels;
     a.partials = c->partials;
+    a.gpartials = c->gpartials;
     a.counter = c->counter;
     a.iters_out = &c->st->cg_iters[solve_idx];
     a.refine_out = &c->st->refinements[solve_idx];
@@ -669,8 +673,11 @@ void do_assemble(sdc_ctx* c) {
     c->cgs = dalloc_n<CgState>(c, c->pool_asm, 1);
     c->max_blocks = (int)blocks_for(c->n, RED_BLOCK) + 1;
     c->partials = dalloc_n<double>(c, c->pool_asm, (size_t)4 * c->max_blocks);
-    c->counter = dalloc_n<unsigned int>(c, c->pool_asm, 4);
-    SDC_CUDA_TRY(cudaMemsetAsync(c->counter, 0, 4 * sizeof(unsigned int), c->stream));
+    const size_t n_groups = (size_t)c->max_blocks / 64 + 2;  // groups of the two-level reduction
+    c->gpartials = dalloc_n<double>(c, c->pool_asm, 4 * n_groups);
+    c->n_counters = 1 + n_groups;
+    c->counter = dalloc_n<unsigned int>(c, c->pool_asm, c->n_counters);
+    SDC_CUDA_TRY(cudaMemsetAsync(c->counter, 0, c->n_counters * sizeof(unsigned int), c->stream));
     SDC_CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->stream));
     const size_t NI = (size_t)C.n_iface;
     c->E1.cnt = dalloc_n<int32_t>(c, c->pool_asm, NI);

@@ -162,6 +162,120 @@ __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const f
     return ell_row_t<8, float, float>(A.slice_ptr, A.col, A.val32, row, x);
 }
 
+// Two-level form of reduce_last for the CG kernels. Block totals go to
+// partials; the last block of each group of RED_GROUP blocks (a per-group
+// arrival counter) sums its group with one warp, two loads per lane, into
+// gpartials; the last group to finish sums the group totals with the whole
+// block. Both combinations read their inputs with loads issued together, so
+// the tail of the kernel is two short memory round trips, not a serial walk
+// over every block's partial. Fixed order throughout.
+// counters[0] counts finished groups, counters[1 + g] the blocks of group g.
+constexpr int RED_GROUP = 64;
+
+template <int NQ, typename W>
+__device__ bool reduce_last2(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out) {
+    __shared__ double sh[NQ][32];
+    __shared__ int am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if constexpr (sizeof(W) == sizeof(float)) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sh[q][warp] = (double)v[q];
+        __syncthreads();
+        if (warp == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double t = lane < nw ? sh[q][lane] : 0.0;
+                sh[q][lane] = warp_sum(t);
+            }
+    } else {
+        __shared__ double colv[NQ][RED_BLOCK];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) colv[q][threadIdx.x] = v[q];
+        __syncthreads();
+        if (warp == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                double t = colv[q][lane];
+                for (int w = 1; w < nw; ++w) t += colv[q][lane + 32 * w];
+                sh[q][lane] = warp_sum(t);
+            }
+    }
+    const unsigned int g = blockIdx.x / RED_GROUP;
+    const unsigned int ng = (gridDim.x + RED_GROUP - 1) / RED_GROUP;
+    const unsigned int gsize = min((unsigned int)RED_GROUP, gridDim.x - g * RED_GROUP);
+    if (warp == 0 && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) partials[(size_t)q * gridDim.x + blockIdx.x] = sh[q][0];
+        __threadfence();
+        am_last = atomicAdd(&counters[1 + g], 1u) == gsize - 1;
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double pv[RED_GROUP / 32];
+#pragma unroll
+            for (int c = 0; c < RED_GROUP / 32; ++c) {
+                const unsigned int k = lane + 32 * c;
+                pv[c] = k < gsize ? __ldcg(partials + (size_t)q * gridDim.x + g * RED_GROUP + k) : 0.0;
+            }
+            double t = 0.0;
+#pragma unroll
+            for (int c = 0; c < RED_GROUP / 32; ++c) t += pv[c];
+            t = warp_sum(t);
+            if (lane == 0) gpartials[(size_t)q * ng + g] = t;
+        }
+        if (lane == 0) {
+            counters[1 + g] = 0u;
+            __threadfence();
+            am_last = atomicAdd(&counters[0], 1u) == ng - 1;
+        }
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    constexpr int G = 4;
+    double dv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dv[q] = 0.0;
+    for (unsigned int base = threadIdx.x; base < ng; base += G * blockDim.x) {
+        double pv[NQ][G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            const unsigned int i = base + c * blockDim.x;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) pv[q][c] = i < ng ? __ldcg(gpartials + (size_t)q * ng + i) : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < G; ++c)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) dv[q] += pv[q][c];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dv[q] = warp_sum(dv[q]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q][warp] = dv[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[q][w];
+            out[q] = t;
+        }
+        counters[0] = 0u;
+    }
+    __syncthreads();
+    return true;
+}
+
 // ------------------------------------------------------------------ operator
 
 // y = m .* x + dtau K x
@@ -216,7 +330,7 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
             v[1] += res * res;
     }
     double out[2];
-    if (reduce_last<2, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<2>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
         s->bb = out[0];
         s->rr = out[1];
@@ -247,7 +361,7 @@ __global__ void k_cg_spmv(CgArgs a) {
             v[2] += res * res;
     }
     double out[3];
-    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
         s->runs += 1;
         *a.loop_kernels += 2;
@@ -327,7 +441,7 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
             v[1] += res * res;
     }
     double out[2];
-    if (reduce_last<2, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<2>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         MixState* s = a.ms;
         s->bb = out[0];
         s->rr = out[1];
@@ -355,7 +469,7 @@ __global__ void k_mx_inner_init(MixArgs a) {
             v[0] += res * res;
     }
     double out[1];
-    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<1>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
         s->bb = fmax(a.inner_rtol2 * out[0], 0.1 * a.rtol2 * a.ms->bb);
         s->rr = out[0];
@@ -383,7 +497,7 @@ __global__ void k_mx_spmv(MixArgs a) {
             v[2] += res * res;
     }
     double out[3];
-    if (reduce_last<3, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
         s->runs += 1;
         *a.loop_kernels += 2;
@@ -447,7 +561,7 @@ __global__ void k_mx_refine(MixArgs a) {
         v[0] += res * res;
     }
     double out[1];
-    if (reduce_last<1, false>(v, a.partials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2<1>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         MixState* s = a.ms;
         s->rr = out[0];
         s->passes += 1;

@@ -30,7 +30,8 @@ struct CgArgs {
     CgState* cg;
     int* loop_kernels;              // StepState::loop_kernels
     double* partials;
-    unsigned int* counter;
+    double* gpartials;              // group totals of the two-level reduction
+    unsigned int* counter;          // [0] groups done, [1 + g] blocks of group g done
     int* iters_out;                 // iteration count of this solve
     int* status;                    // sticky status word
     int max_iter;
@@ -54,7 +55,8 @@ struct MixArgs {
     CgState* cg;                    // inner scalars (bb holds the inner initial ||r||^2)
     MixState* ms;                   // outer scalars
     double* partials;
-    unsigned int* counter;
+    double* gpartials;              // group totals of the two-level reduction
+    unsigned int* counter;          // [0] groups done, [1 + g] blocks of group g done
     int* iters_out;                 // inner iterations of this solve (all passes)
     int* refine_out;                // refinement passes of this solve
     int* status;
