@@ -55,6 +55,7 @@ struct sdc_ctx {
     double* gpartials = nullptr;    // group totals of the two-level reduction
     unsigned int* counter = nullptr;
     size_t n_counters = 0;
+    unsigned update_grid = 1;       // grid of the deferred FP32 update (one wave)
     double *X = nullptr, *R = nullptr, *U = nullptr, *P = nullptr, *Wv = nullptr, *S = nullptr, *D = nullptr;
     // mixed precision: FP64 right-hand side, FP32 inner vectors, FP32 mass, outer scalars
     double* Bv = nullptr;
@@ -385,8 +386,9 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
             if (c->done_host[1]) break;
             ch.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
             eager_cg_loop(c, ch, [&] {
-                ch.kernel(k_mx_spmv, row_grid(c, k_mx_spmv), RED_BLOCK, a);
-                ch.kernel(k_mx_update, row_grid(c, k_mx_update), RED_BLOCK, a);
+                ch.kernel(a.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, a);
+                ch.kernel(a.defer ? k_mx_update : k_mx_update_red, a.defer ? c->update_grid : row_grid(c, k_mx_update),
+                          RED_BLOCK, a);
             });
             ch.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
         }
@@ -403,8 +405,9 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     a.h_inner = (unsigned long long)hi;
     outer.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
     Chain inner(outer.while_node(hi));
-    inner.kernel(k_mx_spmv, row_grid(c, k_mx_spmv), RED_BLOCK, a);
-    inner.kernel(k_mx_update, row_grid(c, k_mx_update), RED_BLOCK, a);
+    inner.kernel(a.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, a);
+    inner.kernel(a.defer ? k_mx_update : k_mx_update_red, a.defer ? c->update_grid : row_grid(c, k_mx_update),
+                 RED_BLOCK, a);
     outer.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
 }
 
@@ -464,6 +467,8 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.iters_out = &c->st->cg_iters[solve_idx];
     a.refine_out = &c->st->refinements[solve_idx];
     a.status = &c->st->status;
+    a.part_blocks = (int)row_grid(c, k_mx_spmv);
+    a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
     a.max_iter = std::min(max_iter, MIX_INNER_MAX);
     a.max_refine = MIX_MAX_REFINE;
     a.rtol2 = rtol * rtol;
@@ -678,6 +683,14 @@ void do_assemble(sdc_ctx* c) {
     c->n_counters = 1 + n_groups;
     c->counter = dalloc_n<unsigned int>(c, c->pool_asm, c->n_counters);
     SDC_CUDA_TRY(cudaMemsetAsync(c->counter, 0, c->n_counters * sizeof(unsigned int), c->stream));
+    // one wave of the deferred FP32 update (rows strided)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_update, RED_BLOCK, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    c->update_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * c->n_sms, blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK)));
     SDC_CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->stream));
     const size_t NI = (size_t)C.n_iface;
     c->E1.cnt = dalloc_n<int32_t>(c, c->pool_asm, NI);
@@ -1115,7 +1128,8 @@ const char* kernel_name(const void* f) {
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
         {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
-        {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_update, "k_mx_update"},
+        {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_spmv_red, "k_mx_spmv_red"},
+        {(const void*)k_mx_update, "k_mx_update"},     {(const void*)k_mx_update_red, "k_mx_update_red"},
         {(const void*)k_mx_refine, "k_mx_refine"},
         {(const void*)k_bulk_endpoint_mx, "k_bulk_endpoint_mx"}, {(const void*)k_fi_mx, "k_fi_mx"},
     };

@@ -135,7 +135,8 @@ struct CgState {
     int iter;                  // updates applied
     int done;                  // stop flag (converged or capped)
     int runs;                  // executions of the SpMV kernel that did work
-    int pad;
+    int pending;               // FP32 loop: nx_* hold an update's step lengths not yet committed
+    double nx_gamma, nx_alpha;
 };
 
 // Outer scalars of one mixed-precision solve (FP64 iterative refinement).

@@ -42,13 +42,13 @@ __device__ __forceinline__ V ell_row_t(const int64_t* __restrict__ slice_ptr, co
     V acc = V(0);
     for (int64_t k0 = b + lane; k0 < e; k0 += (int64_t)CH * SLICE) {
         V v[CH];
-        int c[CH];
+        int64_t c[CH];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             const int64_t k = k0 + (int64_t)j * SLICE;
             const bool in = k < e;
             v[j] = in ? __ldg(val + k) : V(0);
-            c[j] = in ? __ldg(col + k) : 0;
+            c[j] = in ? (int64_t)__ldg(col + k) : 0;
         }
         X xv[CH];
 #pragma unroll
@@ -478,24 +478,180 @@ __global__ void k_mx_inner_init(MixArgs a) {
         s->runs = 0;
         const bool zero = !(out[0] > 0.0);
         s->done = zero ? 1 : 0;
+        s->pending = 0;
         if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, zero ? 0u : 1u);
     }
 }
 
-// FP32: w = m u + dtau K32 u; gamma, delta, rr; inner stop test or step lengths
+// Sums of FP32 values over a block, fixed order (warp butterflies, then warp 0
+// over the warp totals); thread 0 writes them to partials[q * gridDim.x + block].
+template <int NQ>
+__device__ __forceinline__ void block_partials_f32(float (&v)[NQ], float* partials) {
+    __shared__ float sh[NQ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        v[q] = warp_sum(v[q]);
+        if (lane == 0) sh[q][warp] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float t = warp_sum(lane < nw ? sh[q][lane] : 0.0f);
+            if (lane == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = t;
+        }
+}
+
+// Totals of G block partials partials[q * G + b] (written by the previous
+// launch), in the same fixed order in every block (thread-strided sums, warp
+// butterflies, warp 0 over the warp totals), so that all blocks of a launch
+// obtain bitwise the same values; valid in thread 0.
+template <int NQ>
+__device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G, float (&out)[NQ]) {
+    __shared__ float sh[NQ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float t[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) t[q] = 0.0f;
+    constexpr int BATCH = 8;  // loads issued together, then added in index order
+    for (int k0 = threadIdx.x; k0 < G; k0 += BATCH * blockDim.x) {
+        float x[NQ][BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int k = k0 + j * (int)blockDim.x;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) x[q][j] = k < G ? __ldcg(partials + (size_t)q * G + k) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) t[q] += x[q][j];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        t[q] = warp_sum(t[q]);
+        if (lane == 0) sh[q][warp] = t[q];
+    }
+    __syncthreads();
+    if (warp == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[q] = warp_sum(lane < nw ? sh[q][lane] : 0.0f);
+    __syncthreads();  // sh is reused by the next call
+}
+
+// FP32 CG iteration in two launches (Chronopoulos-Gear form); the kernel
+// boundary serves as the grid-wide barrier. Step lengths (FP64):
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev).
+// Two forms, chosen by the SpMV grid:
+//  * deferred (a.defer, at most MIX_DEFER_MAX_BLOCKS blocks): k_mx_spmv leaves
+//    per-block partials of the three dots; every block of k_mx_update (one
+//    wave, rows strided) sums all of them in the same order, takes the stop
+//    decision and forms the step lengths, so that no kernel has a last-block
+//    reduction. The blocks of an update all read the previous step lengths,
+//    so block 0 of the next k_mx_spmv commits the new ones;
+//  * last-block (larger grids, where every block reading every partial would
+//    cost more than that tail): the last block of k_mx_spmv_red sums the
+//    partials (two-level), decides and commits; k_mx_update_red reads the step
+//    lengths.
+
+// FP32 SpMV row i: w = m u + dtau K32 u, and its terms of (r,u), (w,u), (r,r).
+__device__ __forceinline__ void mx_spmv_row(const MixArgs& a, int64_t i, float (&v)[3]) {
+    const float u = a.Ul[i];
+    const float w = fmaf((float)a.dtau, ell_row32(a.A, i, a.Ul), a.mass32[i] * u);
+    const float res = a.Rl[i];
+    a.Wl[i] = w;
+    v[0] = res * u;
+    v[1] = w * u;
+    v[2] = res * res;
+}
+
+// FP32 update of row i: p = u + beta p; s = w + beta s; d += alpha p;
+// r -= alpha s; u = D r (p = u, s = w in the first iteration).
+__device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float alpha, float beta, bool first) {
+    const float u = a.Ul[i], w = a.Wl[i];
+    const float p = first ? u : fmaf(beta, a.Pl[i], u);
+    const float sp = first ? w : fmaf(beta, a.Sl[i], w);
+    a.Pl[i] = p;
+    a.Sl[i] = sp;
+    a.Dl[i] = fmaf(alpha, p, a.Dl[i]);
+    const float res = fmaf(-alpha, sp, a.Rl[i]);
+    a.Rl[i] = res;
+    a.Ul[i] = res * a.Dinv[i];
+}
+
 __global__ void k_mx_spmv(MixArgs a) {
+    CgState* s = a.cg;
+    if (s->done) return;  // an iteration queued after convergence (host-driven loop)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s->pending) {
+        s->gamma = s->nx_gamma;
+        s->alpha = s->nx_alpha;
+        s->iter += 1;
+        s->pending = 0;
+    }
+    float v[3] = {0.0f, 0.0f, 0.0f};
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) mx_spmv_row(a, i, v);
+    block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials));
+}
+
+__global__ void k_mx_update(MixArgs a) {
+    CgState* s = a.cg;
+    __shared__ float step[2];
+    __shared__ int stop, skip;
+    // Block 0 of this launch may set the stop flag while later blocks start:
+    // one read per block, so that a block returns or proceeds as a whole.
+    if (threadIdx.x == 0) skip = s->done;
+    __syncthreads();
+    if (skip) return;
+    float out[3];
+    all_blocks_sum_f32<3>(reinterpret_cast<const float*>(a.partials), a.part_blocks, out);
+    const int iter = s->iter;
+    if (threadIdx.x == 0) {
+        const double gamma = out[0], delta = out[1], rr = out[2];
+        const bool st = rr <= s->bb || iter >= a.max_iter;
+        double alpha = 0.0, beta = 0.0;
+        if (!st) {
+            if (iter == 0) {
+                alpha = gamma / delta;
+            } else {
+                beta = gamma / s->gamma;
+                alpha = gamma / (delta - beta * gamma / s->alpha);
+            }
+        }
+        stop = st;
+        step[0] = (float)alpha;
+        step[1] = (float)beta;
+        if (blockIdx.x == 0) {
+            s->runs += 1;
+            *a.loop_kernels += 2;
+            s->rr = rr;
+            if (st) {
+                s->done = 1;
+                if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+            } else {
+                s->nx_gamma = gamma;
+                s->nx_alpha = alpha;
+                s->beta = beta;
+                s->delta = delta;
+                s->pending = 1;
+                *a.iters_out += 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (stop) return;
+    const float alpha = step[0], beta = step[1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+        mx_update_row(a, i, alpha, beta, iter == 0);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {
     if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) {
-            const float u = a.Ul[i];
-            const float w = fmaf((float)a.dtau, ell_row32(a.A, i, a.Ul), a.mass32[i] * u);
-            const float res = a.Rl[i];
-            a.Wl[i] = w;
-            v[0] += res * u;
-            v[1] += w * u;
-            v[2] += res * res;
-    }
+    if (i < a.n) mx_spmv_row(a, i, v);
     double out[3];
     if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
@@ -523,23 +679,10 @@ __global__ void k_mx_spmv(MixArgs a) {
     }
 }
 
-// FP32: p = u + beta p; s = w + beta s; d += alpha p; r -= alpha s; u = D r
-__global__ void k_mx_update(MixArgs a) {
+__global__ void k_mx_update_red(MixArgs a) {
     if (a.cg->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) {
-        const float alpha = (float)a.cg->alpha, beta = (float)a.cg->beta;
-        const bool first = a.cg->iter == 1;
-        const float u = a.Ul[i], w = a.Wl[i];
-        const float p = first ? u : fmaf(beta, a.Pl[i], u);
-        const float sp = first ? w : fmaf(beta, a.Sl[i], w);
-        a.Pl[i] = p;
-        a.Sl[i] = sp;
-        a.Dl[i] = fmaf(alpha, p, a.Dl[i]);
-        const float res = fmaf(-alpha, sp, a.Rl[i]);
-        a.Rl[i] = res;
-        a.Ul[i] = res * a.Dinv[i];
-    }
+    if (i < a.n) mx_update_row(a, i, (float)a.cg->alpha, (float)a.cg->beta, a.cg->iter == 1);
 }
 
 // End of a refinement pass: x += d and r -= A d, with r and x in FP64. The

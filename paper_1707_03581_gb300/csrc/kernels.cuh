@@ -41,6 +41,10 @@ struct CgArgs {
 
 // One mixed-precision solve of (diag(m) + dtau K) x = b: FP64 residuals
 // r = b - A x around FP32 Jacobi-PCG solves of A d = r (iterative refinement).
+// Largest grid of the FP32 SpMV whose dot partials every block of the update
+// sums itself (above it: last-block reduction in the SpMV).
+constexpr int MIX_DEFER_MAX_BLOCKS = 2048;
+
 struct MixArgs {
     EllDev A;                       // val (FP64) for residuals, val32 for the inner solves
     const double* mass;
@@ -60,6 +64,8 @@ struct MixArgs {
     int* iters_out;                 // inner iterations of this solve (all passes)
     int* refine_out;                // refinement passes of this solve
     int* status;
+    int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_*_red
+    int part_blocks;                // grid of k_mx_spmv: number of its block partials
     int max_iter;                   // per inner solve
     int max_refine;
     double rtol2;                   // outer: ||b - A x||^2 <= rtol2 ||b||^2
@@ -222,7 +228,9 @@ __global__ void k_cg_update(CgArgs a);
 __global__ void k_mx_init(MixArgs a, RhsArgs r);
 __global__ void k_mx_inner_init(MixArgs a);
 __global__ void k_mx_spmv(MixArgs a);
+__global__ void k_mx_spmv_red(MixArgs a);
 __global__ void k_mx_update(MixArgs a);
+__global__ void k_mx_update_red(MixArgs a);
 __global__ void k_mx_refine(MixArgs a);
 __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_bulk_endpoint_mx(BulkArgs a);

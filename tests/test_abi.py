@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "sdcheat.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sdc_[a-z_]+)\s*\(", src)) - {"sdc_alloc_fn", "sdc_free_fn"})
+    return sorted(set(re.findall(r"\b(sdc_[a-z0-9_]+)\s*\(", src)) - {"sdc_alloc_fn", "sdc_free_fn"})
 
 
 def test_library_exports_every_declared_symbol():

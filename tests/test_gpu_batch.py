@@ -86,3 +86,27 @@ def test_batch_rejects_shared_stream_and_unready_member(torch):
     b.close()
     for s in (a, c, fresh):
         s.close()
+
+
+def test_batch_of_large_machines_equals_members_alone(torch):
+    # Members large enough that their CG kernels take several waves of blocks,
+    # stepped concurrently: blocks of one launch start at different times.
+    from paper_1707_03581_gb300 import Batch
+
+    machines = machine_config(3, truncate=12)
+    alone = []
+    for mach in machines:
+        s = _solver(torch, mach, "mixed")
+        s.run_horizon(2)
+        alone.append(s.temperature())
+        s.close()
+    members = [_solver(torch, m, "mixed") for m in machines]
+    b = Batch(0)
+    for s in members:
+        b.add(s)
+    b.step([2] * len(members), wait=True)
+    for s, ref in zip(members, alone):
+        assert np.array_equal(s.temperature(), ref)
+    b.close()
+    for s in members:
+        s.close()

@@ -303,7 +303,45 @@ def test_mixed_eager_matches_graph(torch):
     assert ra["refinements_total"] == rb["refinements_total"]
     assert ra["kernel_launches"] == rb["kernel_launches"]
     kt = b.kernel_times()
-    assert kt["k_mx_spmv"][0] > 0 and "k_cg_spmv" not in kt
+    assert kt["k_mx_spmv"][0] == kt["k_mx_update"][0] > 0 and "k_cg_spmv" not in kt
+
+
+def test_mixed_large_grid_matches_fp64(torch):
+    # 733,586 DOFs: grids above the deferred-dot limit, where the SpMV's last
+    # block hands the dots to the update; the FP64 path is the oracle-pinned one.
+    mach = machine_config(3, truncate=1)[0]
+    a = _solver(mach, precision="mixed")
+    b = _solver(mach, precision="fp64")
+    for _ in range(2):
+        a.step(report=True)
+        b.step(report=True)
+    Ta, Tb = a.temperature(), b.temperature()
+    assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb) <= 1e-9
+    assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb - mach.T0) <= REL_MIXED
+    a.set_execution(True)
+    a.set_kernel_timing(True)
+    a.step(report=True)
+    kt = a.kernel_times()
+    assert kt["k_mx_spmv_red"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_spmv" not in kt
+    a.close()
+    b.close()
+
+
+def test_mixed_eager_kernel_timing_counts_every_launch(torch):
+    mach = machine_config(0)
+    s = _solver(mach, precision="mixed")
+    s.set_execution(True)
+    s.step(report=True)
+    s.set_kernel_timing(True)
+    rep = s.step(report=True)
+    kt = s.kernel_times()
+    assert sum(n for n, _ in kt.values()) == rep["kernel_launches"]
+    # one SpMV per update; the last update of each inner solve only stops it
+    n_pass = rep["refinements_total"]
+    assert kt["k_mx_spmv"][0] == kt["k_mx_update"][0]
+    assert kt["k_mx_spmv"][0] == rep["cg_iters_total"] + kt["k_mx_inner_init"][0]
+    assert kt["k_mx_inner_init"][0] == kt["k_mx_refine"][0] == n_pass
+    s.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
