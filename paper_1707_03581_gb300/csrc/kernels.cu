@@ -597,26 +597,47 @@ __global__ void k_mx_spmv(MixArgs a) {
 
 __global__ void k_mx_update(MixArgs a) {
     CgState* s = a.cg;
+    __shared__ double prev[3];  // gamma_prev, alpha_prev, bb
     __shared__ float step[2];
-    __shared__ int stop, skip;
+    __shared__ int iter_sh, stop, skip;
     // Block 0 of this launch may set the stop flag while later blocks start:
     // one read per block, so that a block returns or proceeds as a whole.
-    if (threadIdx.x == 0) skip = s->done;
+    if (threadIdx.x == 0) {
+        skip = s->done;
+        iter_sh = s->iter;
+        prev[0] = s->gamma;
+        prev[1] = s->alpha;
+        prev[2] = s->bb;
+    }
+    // the first row's operands are loaded before the dot sums and the step
+    // lengths, so that their latency overlaps that chain
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float u0 = 0.0f, w0 = 0.0f, p0 = 0.0f, s0 = 0.0f, d0 = 0.0f, r0 = 0.0f, q0 = 0.0f;
+    if (i0 < a.n) {
+        u0 = a.Ul[i0];
+        w0 = a.Wl[i0];
+        p0 = a.Pl[i0];
+        s0 = a.Sl[i0];
+        d0 = a.Dl[i0];
+        r0 = a.Rl[i0];
+        q0 = a.Dinv[i0];
+    }
     __syncthreads();
     if (skip) return;
     float out[3];
     all_blocks_sum_f32<3>(reinterpret_cast<const float*>(a.partials), a.part_blocks, out);
-    const int iter = s->iter;
+    const int iter = iter_sh;
     if (threadIdx.x == 0) {
         const double gamma = out[0], delta = out[1], rr = out[2];
-        const bool st = rr <= s->bb || iter >= a.max_iter;
+        const bool st = rr <= prev[2] || iter >= a.max_iter;
         double alpha = 0.0, beta = 0.0;
         if (!st) {
             if (iter == 0) {
                 alpha = gamma / delta;
             } else {
-                beta = gamma / s->gamma;
-                alpha = gamma / (delta - beta * gamma / s->alpha);
+                beta = gamma / prev[0];
+                alpha = gamma / (delta - beta * gamma / prev[1]);
             }
         }
         stop = st;
@@ -642,9 +663,18 @@ __global__ void k_mx_update(MixArgs a) {
     __syncthreads();
     if (stop) return;
     const float alpha = step[0], beta = step[1];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-        mx_update_row(a, i, alpha, beta, iter == 0);
+    const bool first = iter == 0;
+    if (i0 < a.n) {
+        const float p = first ? u0 : fmaf(beta, p0, u0);
+        const float sp = first ? w0 : fmaf(beta, s0, w0);
+        a.Pl[i0] = p;
+        a.Sl[i0] = sp;
+        a.Dl[i0] = fmaf(alpha, p, d0);
+        const float res = fmaf(-alpha, sp, r0);
+        a.Rl[i0] = res;
+        a.Ul[i0] = res * q0;
+    }
+    for (int64_t i = i0 + stride; i < a.n; i += stride) mx_update_row(a, i, alpha, beta, first);
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {
