@@ -182,6 +182,12 @@ sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
  * Results are identical. */
 sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
 
+/* Upper bound on the CTAs of the contact substep loop's thread-block cluster
+ * (1..16; 0 = automatic). The loop takes the largest power of two within the
+ * bound whose cluster fits on the device. For tuning and tests: results are
+ * identical for every cluster size. */
+sdc_status sdc_set_contact_cluster(sdc_ctx* ctx, int max_ctas);
+
 /* Measurement aid for eager execution (sdc_set_execution(ctx, 1)): when on,
  * every kernel launch of a step is bracketed by CUDA events on the
  * context's stream and each step waits for its launches, summing the

@@ -74,6 +74,7 @@ _SIGS = {
     "sdc_set_execution": (C.c_int, [_vp, C.c_int]),
     "sdc_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "sdc_set_contact_replicas": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_contact_cluster": (C.c_int, [_vp, C.c_int]),
     "sdc_get_kernel_times": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int32),
                                        _f64p, C.POINTER(C.c_int32)]),
     "sdc_set_temperature": (C.c_int, [_vp, _vp, C.c_double, C.c_double]),
@@ -248,6 +249,10 @@ class Solver:
     def set_contact_replicas(self, global_memory: bool):
         """Force the contact loop's replicas into global memory (True) or choose automatically."""
         self._call("sdc_set_contact_replicas", 1 if global_memory else 0)
+
+    def set_contact_cluster(self, max_ctas: int):
+        """Cap the CTAs of the contact substep loop's cluster (0: automatic)."""
+        self._call("sdc_set_contact_cluster", int(max_ctas))
 
     def set_kernel_timing(self, on: bool):
         """Eager steps time every kernel launch with CUDA events (see sdc_set_kernel_timing)."""

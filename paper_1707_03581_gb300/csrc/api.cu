@@ -93,6 +93,7 @@ struct sdc_ctx {
     int iface_chunk = 0;            // replica slots per CTA of that cluster
     bool iface_global = false;      // replicas in global memory (large interfaces)
     int force_global = 0;           // sdc_set_contact_replicas
+    int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     void* iface_rep = nullptr;      // their buffers
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
@@ -740,7 +741,18 @@ void pick_iface_cluster(sdc_ctx* c) {
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
-    for (int cs = IFACE_MAX_CLUSTER; cs >= 1; cs /= 2) {
+    int cs_max = IFACE_MAX_CLUSTER;
+    while (c->max_cluster > 0 && cs_max > c->max_cluster) cs_max /= 2;
+    // Preferred size: about IFACE_TARGET_CHUNK contact DOFs per CTA. Measured on GB300
+    // (intervals of 20 substeps): 440 DOFs ran fastest on 4 CTAs (36 us against 43 on 16),
+    // 990 on 8 (56 against 64), 3,950 and 7,000 on 16. Then larger clusters (smaller chunks
+    // fit more easily), then smaller ones.
+    int pref = 1;
+    while (pref < cs_max && (int64_t)pref * IFACE_TARGET_CHUNK < NI) pref *= 2;
+    std::vector<int> order;
+    for (int cs = pref; cs <= cs_max; cs *= 2) order.push_back(cs);
+    for (int cs = pref / 2; cs >= 1; cs /= 2) order.push_back(cs);
+    for (int cs : order) {
         const int chunk = ((NI + cs - 1) / cs + 3) & ~3;
         const size_t rep_bytes = 2 * (size_t)cs * chunk * esz;
         bool global;
@@ -748,7 +760,7 @@ void pick_iface_cluster(sdc_ctx* c) {
             rep_bytes <= smem_cap)
             global = false;
         else if (chunk <= IFACE_THREADS * IFACE_PER_THREAD_GL) global = true;
-        else break;
+        else continue;
         const size_t smem = global ? 0 : rep_bytes;
         const void* kern = (const void*)iface_loop_kernel(mixed, chunk, global);
         cudaLaunchConfig_t cfg{};
@@ -1388,6 +1400,15 @@ sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
 sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
     return guarded(c, [&] {
         c->force_global = global ? 1 : 0;
+        c->buffers_ready = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_contact_cluster(sdc_ctx* c, int max_ctas) {
+    return guarded(c, [&] {
+        require(max_ctas >= 0 && max_ctas <= IFACE_MAX_CLUSTER, SDC_ERR_ARG, "max_ctas out of range");
+        c->max_cluster = max_ctas;
         c->buffers_ready = false;
         c->graph_ready = false;
     });

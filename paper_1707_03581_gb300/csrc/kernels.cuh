@@ -8,6 +8,7 @@ namespace sdc {
 constexpr int MAXE = 32;            // coupling entries per contact DOF and substep time
 constexpr int GEOM_THREADS = 64;    // threads per block of k_iface_geom (one slot per block row)
 constexpr int IFACE_MAX_CLUSTER = 16;   // CTAs of the substep-loop cluster (at most)
+constexpr int IFACE_TARGET_CHUNK = 128;  // preferred contact DOFs per CTA of the loop
 constexpr int IFACE_THREADS = 512;      // threads per CTA of that cluster
 constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of a shared-memory-replica loop owns
 constexpr int IFACE_PER_THREAD_GL = 4;  // the same for the global-replica loop

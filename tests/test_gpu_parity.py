@@ -345,6 +345,26 @@ def test_mixed_eager_kernel_timing_counts_every_launch(torch):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_contact_cluster_sizes_are_bitwise_equal(torch, precision):
+    # the automatic size and forced 16-, 2- and 1-CTA clusters of the substep loop
+    mach = machine_config(0)
+    ref = None
+    for cs in (0, 16, 2, 1):
+        s = _solver(mach, precision=precision)
+        s.set_contact_cluster(cs)
+        for _ in range(3):
+            rep = s.step(report=True)
+        if cs:
+            assert 1 <= rep["contact_cluster"] <= cs
+        T = s.temperature()
+        if ref is None:
+            ref = T
+        else:
+            assert np.array_equal(T, ref), cs
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
     # the loop form for interfaces too large for shared memory, forced on a small machine
     mach = machine_config(0)
