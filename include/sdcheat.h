@@ -182,6 +182,14 @@ sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
  * Results are identical. */
 sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
 
+/* Side branches in the macro-step graph (1, default): the contact coupling
+ * operator of the step and each interval's k_iface_prep, which do not depend
+ * on the interval's implicit solve, run beside it instead of before or after
+ * it. 0: one chain. Members of a batch (sdc_batch_add) run as one chain while
+ * they are members: their concurrency comes from the batch. Results are
+ * identical. */
+sdc_status sdc_set_graph_branches(sdc_ctx* ctx, int on);
+
 /* Upper bound on the CTAs of the contact substep loop's thread-block cluster
  * (1..16; 0 = automatic). The loop takes the largest power of two within the
  * bound whose cluster fits on the device. For tuning and tests: results are

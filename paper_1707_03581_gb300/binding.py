@@ -75,6 +75,7 @@ _SIGS = {
     "sdc_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "sdc_set_contact_replicas": (C.c_int, [_vp, C.c_int]),
     "sdc_set_contact_cluster": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_graph_branches": (C.c_int, [_vp, C.c_int]),
     "sdc_get_kernel_times": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int32),
                                        _f64p, C.POINTER(C.c_int32)]),
     "sdc_set_temperature": (C.c_int, [_vp, _vp, C.c_double, C.c_double]),
@@ -249,6 +250,10 @@ class Solver:
     def set_contact_replicas(self, global_memory: bool):
         """Force the contact loop's replicas into global memory (True) or choose automatically."""
         self._call("sdc_set_contact_replicas", 1 if global_memory else 0)
+
+    def set_graph_branches(self, on: bool):
+        """Run solve-independent kernels beside the implicit solves (True) or in one chain."""
+        self._call("sdc_set_graph_branches", 1 if on else 0)
 
     def set_contact_cluster(self, max_ctas: int):
         """Cap the CTAs of the contact substep loop's cluster (0: automatic)."""

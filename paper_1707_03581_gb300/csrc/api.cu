@@ -94,6 +94,8 @@ struct sdc_ctx {
     bool iface_global = false;      // replicas in global memory (large interfaces)
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
+    int branches = 1;               // sdc_set_graph_branches
+    int in_batch = 0;               // batches holding this context (their members run without side branches)
     void* iface_rep = nullptr;      // their buffers
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
@@ -193,7 +195,45 @@ struct Chain {
     cudaStream_t eager = nullptr;   // non-null: launch immediately instead of recording
     bool is_eager = false;
     sdc_ctx* timer = nullptr;       // eager only: record CUDA events around every launch
+    std::vector<cudaGraphNode_t> joins;  // side branches the next node waits for as well
+    bool allow_branches = true;          // false: side-branch kernels join the chain in place
     explicit Chain(cudaGraph_t gg) : g(gg) {}
+    // dependencies of the next node on the chain: the last node and every pending join
+    std::vector<cudaGraphNode_t> take_deps() {
+        std::vector<cudaGraphNode_t> d;
+        if (last) d.push_back(last);
+        d.insert(d.end(), joins.begin(), joins.end());
+        joins.clear();
+        return d;
+    }
+    // The next node on the chain also waits for side-branch node n (graph mode; a
+    // no-op in eager mode, where side-branch kernels were launched in stream order).
+    void join(cudaGraphNode_t n) {
+        if (n) joins.push_back(n);
+    }
+    // Side branch: a kernel node that waits only for `on` (null entries ignored), and
+    // that the chain does not wait for until join(). Eager mode launches it at once.
+    template <typename... KArgs>
+    cudaGraphNode_t branch_kernel(std::initializer_list<cudaGraphNode_t> on, void (*f)(KArgs...), dim3 grid,
+                                  dim3 block, KArgs... args) {
+        if (is_eager || !allow_branches) {
+            kernel_2d(f, grid, block, args...);
+            return nullptr;
+        }
+        void* params[] = {(void*)&args...};
+        ++kernels;
+        std::vector<cudaGraphNode_t> d;
+        for (cudaGraphNode_t n : on)
+            if (n) d.push_back(n);
+        cudaKernelNodeParams p{};
+        p.func = (void*)f;
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.kernelParams = params;
+        cudaGraphNode_t nd;
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
+        return nd;
+    }
     int begin_timed(const void* f) {
         if (!timer) return -1;
         const int ev = next_event();
@@ -237,7 +277,8 @@ struct Chain {
         p.sharedMemBytes = 0;
         p.kernelParams = params;
         cudaGraphNode_t nd;
-        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
         last = nd;
     }
     template <typename... KArgs>
@@ -256,7 +297,8 @@ struct Chain {
         p.blockDim = block;
         p.kernelParams = params;
         cudaGraphNode_t nd;
-        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
         last = nd;
     }
     // Launch with dynamic shared memory and a thread-block cluster of `cluster` CTAs along x.
@@ -290,7 +332,8 @@ struct Chain {
         p.sharedMemBytes = (unsigned)smem;
         p.kernelParams = params;
         cudaGraphNode_t nd;
-        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, last ? &last : nullptr, last ? 1 : 0, &p));
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
         cudaLaunchAttributeValue v{};
         v.clusterDim.x = cluster;
         v.clusterDim.y = 1;
@@ -304,8 +347,8 @@ struct Chain {
             return;
         }
         cudaGraphNode_t nd;
-        SDC_CUDA_TRY(cudaGraphAddMemcpyNode1D(&nd, g, last ? &last : nullptr, last ? 1 : 0, dst, src, bytes,
-                                              cudaMemcpyDeviceToDevice));
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddMemcpyNode1D(&nd, g, d.data(), d.size(), dst, src, bytes, cudaMemcpyDeviceToDevice));
         last = nd;
     }
     // WHILE node driven by handle h; returns the body graph.
@@ -316,7 +359,8 @@ struct Chain {
         np.conditional.type = cudaGraphCondTypeWhile;
         np.conditional.size = 1;
         cudaGraphNode_t nd;
-        SDC_CUDA_TRY(cudaGraphAddNode(&nd, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np));
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddNode(&nd, g, d.data(), nullptr, d.size(), &np));
         last = nd;
         return np.conditional.phGraph_out[0];
     }
@@ -854,15 +898,19 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.use_fixed = 0;
     ga.n_slots = n_int * (P + 1);
     ga.status = &c->st->status;
-    ga.loop_kernels = &c->st->loop_kernels;
     ga.cs = c->iface_cluster;
     ga.chunk = c->iface_chunk;
-    ch.kernel_2d(c->precision == SDC_MIXED_FP32 ? k_iface_geom_mx : k_iface_geom,
-                 dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
+    // side branch: nothing reads the coupling operator before the first interval's
+    // k_iface_prep, so it forms while the first implicit solve runs
+    const cudaGraphNode_t geom = ch.branch_kernel(
+        {ch.last}, c->precision == SDC_MIXED_FP32 ? k_iface_geom_mx : k_iface_geom,
+        dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
 
     // F^I(T_n) + g in FP64 (the only pass over K in FP64 of a mixed-precision step); a
-    // standard node at t_n (Lobatto) shares it
-    ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->Fn);
+    // standard node at t_n (Lobatto) shares it. It also zeroes the step's count of CG-loop
+    // kernels (no kernel that counts runs before or beside it).
+    ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->Fn,
+              &c->st->loop_kernels);
     const bool mixed = c->precision == SDC_MIXED_FP32;
     // F^I + g at standard node j (0 = t_n) of iterate set s
     auto F_at = [&](int j, int set) -> const double* { return j == 0 ? c->Fn : c->FI[set][j - 1]; };
@@ -880,7 +928,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             ch.kernel(k_fi_mx, row_grid(c, k_fi_mx), (unsigned)RED_BLOCK, fa);
         } else {
             ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv,
-                      (const double*)c->Tstd[m], c->FI[set][m - 1]);
+                      (const double*)c->Tstd[m], c->FI[set][m - 1], (int*)nullptr);
         }
     };
     auto bulk = [&](BulkArgs& b, const double* Fx0) {
@@ -898,8 +946,10 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         for (int j = 0; j < MAX_M; ++j) out[j] = j < M ? dt * W.S[(size_t)(m - 1) * M + j] : 0.0;
     };
     int solve = 0;
-    // substeps of interval ii (standard node m): k_iface_prep, then the cluster loop
-    auto substeps = [&](int ii, int m, int mode, int set_old, int set_new) {
+    // k_iface_prep of interval ii (standard node m) as a side branch that waits for
+    // `on` only: it reads T_{m-1}, the previous iterate and the coupling operator, not
+    // the interval's implicit solve, and runs beside it; substeps() joins it
+    auto prep = [&](int ii, int m, int mode, int set_old, std::initializer_list<cudaGraphNode_t> on) {
         PrepArgs pa{};
         pa.C = c->C;
         pa.mode = mode;
@@ -907,7 +957,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         pa.dt = dt;
         pa.st = c->st;
         pa.emb = c->w_emb + (size_t)(m - 1) * (P + 1);
-        pa.fstar = c->fst;
         for (int j = 0; j < M; ++j) pa.FI[j] = c->FI[set_old][j];
         pa.nFI = M;
         pa.Stil = c->w_Stil + (size_t)(m - 1) * P * M;
@@ -920,7 +969,11 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         pa.Tprev = c->Tstd[m - 1];
         pa.cs = c->iface_cluster;
         pa.chunk = c->iface_chunk;
-        ch.kernel(k_iface_prep, blocks_for((int64_t)(P + 1) * NI, 256), 256u, pa);
+        return ch.branch_kernel(on, k_iface_prep, dim3(blocks_for((int64_t)(P + 1) * NI, 256)), dim3(256u), pa);
+    };
+    // the cluster loop of interval ii, after the bulk endpoint and the interval's prep
+    auto substeps = [&](int ii, int m, int mode, int set_old, int set_new, cudaGraphNode_t prep_node) {
+        ch.join(prep_node);
         IfaceArgs ia{};
         ia.C = c->C;
         ia.mode = mode;
@@ -932,6 +985,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.Tprev = c->Tstd[m - 1];
         ia.Tout = c->Tstd[m];
         ia.cpre = c->cpre;
+        ia.fstar = c->fst;
         ia.Shat = c->w_Shat + (size_t)(m - 1) * P;
         ia.E = c->E;
         ia.slot0 = ii * (P + 1);
@@ -973,6 +1027,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     for (int ii = 0; ii < n_int; ++ii) {
         const int m = c->nondeg[ii];
         const double dtau = dt * (W.c[m] - W.c[m - 1]);
+        const cudaGraphNode_t pn = prep(ii, m, RHS_PRED, 0, {ch.last, ii == 0 ? geom : nullptr});
         RhsArgs r{};
         r.mode = RHS_PRED;
         r.Tprev = c->Tstd[m - 1];
@@ -994,7 +1049,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         b.pos = c->C.pos;
         b.fstar_I = c->fst;
         bulk(b, F_at(m - 1, 0));
-        substeps(ii, m, RHS_PRED, 0, 0);
+        substeps(ii, m, RHS_PRED, 0, 0, pn);
         fi(m, 0);
     }
     // ---- Algorithm 2 (sweeps)
@@ -1004,6 +1059,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         for (int ii = 0; ii < n_int; ++ii) {
             const int m = c->nondeg[ii];
             const double dtau = dt * (W.c[m] - W.c[m - 1]);
+            const cudaGraphNode_t pn = prep(ii, m, RHS_SWEEP, so, {ch.last});
             RhsArgs r{};
             r.mode = RHS_SWEEP;
             r.Tprev = c->Tstd[m - 1];
@@ -1034,7 +1090,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.pos = c->C.pos;
             b.fstar_I = c->fst;
             bulk(b, c->FI[so][m - 1]);
-            substeps(ii, m, RHS_SWEEP, so, sn);
+            substeps(ii, m, RHS_SWEEP, so, sn, pn);
             if (k < K || c->residuals) fi(m, sn);
         }
     }
@@ -1049,6 +1105,7 @@ void build_step_graph(sdc_ctx* c) {
     drop_graph(c);
     SDC_CUDA_TRY(cudaGraphCreate(&c->graph, 0));
     Chain ch(c->graph);
+    ch.allow_branches = c->branches && !c->in_batch;
     emit_step(c, ch);
     SDC_CUDA_TRY(cudaGraphInstantiate(&c->exec, c->graph, 0));
     c->fixed_kernels = ch.kernels;
@@ -1401,6 +1458,13 @@ sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
     return guarded(c, [&] {
         c->force_global = global ? 1 : 0;
         c->buffers_ready = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_graph_branches(sdc_ctx* c, int on) {
+    return guarded(c, [&] {
+        c->branches = on ? 1 : 0;
         c->graph_ready = false;
     });
 }
@@ -1785,6 +1849,8 @@ extern "C" sdc_status sdc_batch_add(sdc_batch* b, sdc_ctx* c, int32_t* index) {
             require(m->stream != c->stream, SDC_ERR_ARG, "every member needs its own stream");
         }
         b->members.push_back(c);
+        c->in_batch += 1;
+        c->graph_ready = false;
         if (index) *index = (int32_t)b->members.size() - 1;
     });
 }
@@ -1795,6 +1861,8 @@ extern "C" sdc_status sdc_batch_remove(sdc_batch* b, sdc_ctx* c) {
         require(it != b->members.end(), SDC_ERR_ARG, "not a member");
         SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
         b->members.erase(it);
+        c->in_batch -= 1;
+        c->graph_ready = false;
     });
 }
 

@@ -288,8 +288,10 @@ __global__ void k_apply_operator(EllDev A, const double* __restrict__ mass, doub
 }
 
 // F = -K T + g   (f^I(T) + g of Eq. ivp)
-__global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F) {
+__global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F,
+                     int* step_counts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (step_counts && i == 0) *step_counts = 0;  // step start: kernels launched in the CG loops
     if (i < A.n) {
         F[i] = g[i] - ell_row(A, i, T);
     }
@@ -857,7 +859,6 @@ __device__ __forceinline__ void iface_geom_impl(const GeomArgs& g) {
     const int NI = C.n_iface;
     const int s = (int)blockIdx.y;
     const int a = (int)(blockIdx.x * GEOM_THREADS + threadIdx.x);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && g.loop_kernels) *g.loop_kernels = 0;  // step start
     // the slot's motion, once per block
     __shared__ double mot[3];
     __shared__ int32_t s_idx[MAXE * GEOM_THREADS];
@@ -1157,23 +1158,18 @@ __global__ void k_iface_prep(PrepArgs a) {
         }
         a.base[(size_t)p * NI + i] = acc;
     }
-    if (p == 0) return;
+    if (p == 0 || a.mode == RHS_PRED) return;  // Algorithm 1: c_p = dt_p f*_m (formed by the loop)
     const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
     const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
-    double c;
-    if (a.mode == RHS_PRED) {
-        c = dtp * a.fstar[i];
-    } else {
-        const int row = a.C.dof[i];
-        double I = 0.0;
-        for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
-        for (int qq = 1; qq <= a.P; ++qq) {
-            const double wq = a.Semb[(size_t)(p - 1) * a.P + (qq - 1)];
-            if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)qq * NI + i], I);
-        }
-        c = fma(dtp, a.fstar[i] - a.fe_old[(size_t)(p - 1) * NI + i], I);
+    const int row = a.C.dof[i];
+    double I = 0.0;
+    for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
+    for (int qq = 1; qq <= a.P; ++qq) {
+        const double wq = a.Semb[(size_t)(p - 1) * a.P + (qq - 1)];
+        if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)qq * NI + i], I);
     }
-    a.cpre[(size_t)(p - 1) * NI + i] = c;
+    // Algorithm 2: c_p = dt_p (f*_m - f^E(T^k_{m,p-1})) + I_p; the loop adds dt_p f*_m
+    a.cpre[(size_t)(p - 1) * NI + i] = fma(-dtp, a.fe_old[(size_t)(p - 1) * NI + i], I);
 }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -1283,7 +1279,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         }
         fe[r] = f0;
         a.fe_new[i] = f0;
-        cn[r] = a.cpre[i];
+        cn[r] = a.mode == RHS_PRED ? 0.0 : a.cpre[i];
         if constexpr (MIX) bn[r] = a.base[(size_t)NI + i];
     }
     unsigned phase[2] = {0u, 0u};
@@ -1301,10 +1297,10 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             if (i < 0) continue;
             if constexpr (MIX) coupling_prefetch32(a.E, a.slot0 + p, NI, i, row[r]);
             else coupling_prefetch(a.E, a.slot0 + p, NI, i, row[r]);
-            const double cp = cn[r];
+            const double cp = fma(dtp, __ldg(a.fstar + i), cn[r]);  // c_p (Algorithms 1 and 2)
             bp[r] = bn[r];
             if (p < P) {  // inputs of the next substep, loaded one substep ahead
-                cn[r] = a.cpre[(size_t)p * NI + i];
+                cn[r] = a.mode == RHS_PRED ? 0.0 : a.cpre[(size_t)p * NI + i];
                 if constexpr (MIX) bn[r] = a.base[(size_t)(p + 1) * NI + i];
             }
             T[r] = fma(fma(dtp, fe[r], cp), mi[r], T[r]);

@@ -144,7 +144,6 @@ struct GeomArgs {
     int use_fixed;
     int n_slots;
     int* status;
-    int* loop_kernels;        // reset here (the step's first kernel); NULL outside a step
     // 0: coupling indices are contact-DOF ids; else replica positions of the substep loop
     // for a cluster of `cs` CTAs with `chunk` slots each (DOF j -> (j % cs) * chunk + j / cs)
     int cs, chunk;
@@ -163,13 +162,12 @@ struct PrepArgs {
     double dt;
     const StepState* st;
     const double* emb;              // P+1 unit-step positions of this interval's embedded nodes
-    const double* fstar;            // [NI]
     const double* FI[MAX_M];
     int nFI;
     const double* Stil;             // [P][nFI] dt stil_{m,p,j}
     const double* Semb;             // [P][P]  dt s_{m,p,q}
     const double* fe_old;           // [(P+1)][NI] previous iterate (sweep)
-    double* cpre;                   // [P][NI] output
+    double* cpre;                   // [P][NI] output (Algorithm 2): c_p - dt_p f*_m
     // mixed precision: base_q = f^E(T_{m-1}, tau_{m,q}) for q = 0..P (output), from
     // the interval's slots of the coupling operator and T_{m-1} = Tprev
     double* base;                   // [(P+1)][NI] or NULL
@@ -190,7 +188,8 @@ struct IfaceArgs {
     const double* emb;              // P+1 unit-step positions of this interval's embedded nodes
     const double* Tprev;            // T_{m-1} (N)
     double* Tout;                   // T_m (N), contact rows written here
-    const double* cpre;             // [P][NI]
+    const double* cpre;             // [P][NI] c_p less dt_p f*_m (Algorithm 2; unread in Algorithm 1)
+    const double* fstar;            // [NI] f*_m of the interval
     const double* Shat;             // [P]     dt shat_{m,q}
     CouplingOp E;                   // slots of this interval start at slot0
     int slot0;
@@ -222,7 +221,7 @@ struct ResidualArgs {
 
 // kernels (defined in kernels.cu)
 __global__ void k_apply_operator(EllDev A, const double* mass, double dtau, const double* x, double* y);
-__global__ void k_fi(EllDev A, const double* g, const double* T, double* F);
+__global__ void k_fi(EllDev A, const double* g, const double* T, double* F, int* step_counts);
 __global__ void k_cg_init(CgArgs a, RhsArgs r);
 __global__ void k_cg_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);

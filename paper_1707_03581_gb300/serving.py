@@ -95,6 +95,8 @@ class LookAheadServer:
 
         s = Solver(self.device, own_stream=True)
         s.set_machine(self.machines[i], precision=self.precision)
+        # slots overlap one another; a slot's own graph runs as one chain
+        s.set_graph_branches(False)
         b = s.footprint()
         self.slot_bytes[i] = b
         self.footprint += b

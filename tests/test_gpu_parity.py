@@ -345,6 +345,22 @@ def test_mixed_eager_kernel_timing_counts_every_launch(torch):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_side_branches_equal_one_chain(torch, precision):
+    # geometry and k_iface_prep beside the implicit solves, or all in one chain
+    mach = machine_config(0)
+    a = _solver(mach, precision=precision)
+    b = _solver(mach, precision=precision)
+    b.set_graph_branches(False)
+    for _ in range(3):
+        ra = a.step(report=True)
+        rb = b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    assert ra["kernel_launches"] == rb["kernel_launches"]
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_contact_cluster_sizes_are_bitwise_equal(torch, precision):
     # the automatic size and forced 16-, 2- and 1-CTA clusters of the substep loop
     mach = machine_config(0)
