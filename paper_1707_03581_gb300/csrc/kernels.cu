@@ -371,6 +371,7 @@ __global__ void k_cg_spmv(CgArgs a) {
         s->rr = out[2];
         const bool conv = out[2] <= a.rtol2 * s->bb;
         if (conv || s->iter >= a.max_iter) {
+            *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
             s->done = 1;
             if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
             if (a.handle) cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, 0u);
@@ -650,6 +651,7 @@ __global__ void k_mx_update(MixArgs a) {
             *a.loop_kernels += 2;
             s->rr = rr;
             if (st) {
+                *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
                 s->done = 1;
                 if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
             } else {
@@ -692,6 +694,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {
         const double gamma = out[0], delta = out[1];
         s->rr = out[2];
         if (out[2] <= s->bb || s->iter >= a.max_iter) {
+            *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
             s->done = 1;
             if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
             return;

@@ -36,6 +36,7 @@ struct CgArgs {
     int* iters_out;                 // iteration count of this solve
     int* status;                    // sticky status word
     int max_iter;
+    int tail_pairs;                 // (spmv, update) pairs after this one in the graph's loop body
     double rtol2;
     unsigned long long handle;      // cudaGraphConditionalHandle of the enclosing while node
 };
@@ -68,6 +69,7 @@ struct MixArgs {
     int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_*_red
     int part_blocks;                // grid of k_mx_spmv: number of its block partials
     int max_iter;                   // per inner solve
+    int tail_pairs;                 // (spmv, update) pairs after this one in the graph's loop body
     int max_refine;
     double rtol2;                   // outer: ||b - A x||^2 <= rtol2 ||b||^2
     double inner_rtol2;             // inner: ||r||^2 <= inner_rtol2 ||r_0||^2
