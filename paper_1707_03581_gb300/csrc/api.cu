@@ -414,7 +414,8 @@ void eager_cg_loop(sdc_ctx* c, Chain& ch, Iter iteration, int pairs) {
         SDC_CUDA_TRY(cudaEventSynchronize(c->done_ev));
         if (c->done_host[1]) break;
     }
-    const int idle = queued - (c->done_host[2] + pairs - 1) / pairs;
+    // the first body always counts: in a pass with nothing to solve it only stops the loop
+    const int idle = queued - std::max(1, (c->done_host[2] + pairs - 1) / pairs);
     ch.kernels -= KPI * idle;
     if (ch.timer)
         for (size_t k = ch.timer->launches.size() - (size_t)KPI * idle; k < ch.timer->launches.size(); ++k)
@@ -442,7 +443,6 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                                          ch.eager));
             SDC_CUDA_TRY(cudaStreamSynchronize(ch.eager));
             if (c->done_host[1]) break;
-            ch.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
             eager_cg_loop(
                 c, ch,
                 [&] {
@@ -463,10 +463,11 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     a.h_inner = 0;
     ch.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
     Chain outer(ch.while_node(ho));
+    // the inner loop's condition: 1 at each graph launch (first pass), and set to 1 again by
+    // k_mx_refine for every later pass
     cudaGraphConditionalHandle hi;
-    SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, outer.g, 0u, 0));
+    SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, outer.g, 1u, cudaGraphCondAssignDefault));
     a.h_inner = (unsigned long long)hi;
-    outer.kernel(k_mx_inner_init, row_grid(c, k_mx_inner_init), RED_BLOCK, a);
     Chain inner(outer.while_node(hi));
     for (int u = 0; u < unroll; ++u) {
         MixArgs au = a;
@@ -1228,7 +1229,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
-        {(const void*)k_mx_init, "k_mx_init"},         {(const void*)k_mx_inner_init, "k_mx_inner_init"},
+        {(const void*)k_mx_init, "k_mx_init"},
         {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_spmv_red, "k_mx_spmv_red"},
         {(const void*)k_mx_update, "k_mx_update"},     {(const void*)k_mx_update_red, "k_mx_update_red"},
         {(const void*)k_mx_refine, "k_mx_refine"},

@@ -413,6 +413,39 @@ __global__ void k_cg_update(CgArgs a) {
 
 // ------------------------------------------------------------------ mixed precision (iterative refinement)
 
+// Start of one refinement pass, by the kernel that formed its FP64 residual
+// r (k_mx_init, k_mx_refine): r32 = r and u = D r32 on every row, and here, in
+// that kernel's last block, the inner state. The inner target is the larger of
+// a fixed FP32 reduction and what the outer test still needs (with a margin for
+// the FP32 recurrence), so a pass stops as soon as one more FP64 residual can
+// meet ||b - A x|| <= rtol ||b||. The pass's first update sets d (d = alpha p,
+// or 0 when the pass stops before it).
+__device__ __forceinline__ void mx_begin_pass(const MixArgs& a, double rr) {
+    CgState* s = a.cg;
+    s->bb = fmax(a.inner_rtol2 * rr, 0.1 * a.rtol2 * a.ms->bb);
+    s->rr = rr;
+    s->beta = 0.0;
+    s->iter = 0;
+    s->runs = 0;
+    s->done = rr > 0.0 ? 0 : 1;
+    s->pending = 0;
+    // the inner loop's condition starts at 1 with each step's graph launch; the
+    // refinement (in the same graph as that loop) sets it again for each later pass
+    if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 1u);
+}
+
+// A CG-loop SpMV that finds its solve done on entry. If no kernel of this pass
+// has run (the pass had nothing to solve), the first one counts the loop body
+// and stops the loop (whose condition is 1 at the start of every pass).
+__device__ __forceinline__ void mx_done_on_entry(const MixArgs& a) {
+    CgState* s = a.cg;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s->runs == 0) {
+        s->runs = -1;
+        *a.loop_kernels += 2 * (1 + a.tail_pairs);
+        if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+    }
+}
+
 // FP64: b of the implicit stage (as k_cg_init), x = x0, r = b - A x0, and
 // the outer stop test; FP32 inverse diagonal for the inner solves.
 __global__ void k_mx_init(MixArgs a, RhsArgs r) {
@@ -439,7 +472,10 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
             a.X[i] = x0;
             a.R[i] = res;
             a.Dsum[i] = 0.0f;
-            a.Dinv[i] = 1.0f / (float)(m + a.dtau * a.diagK[i]);
+            const float dinv = 1.0f / (float)(m + a.dtau * a.diagK[i]);
+            a.Dinv[i] = dinv;
+            a.Rl[i] = (float)res;  // the first pass's FP32 residual and u
+            a.Ul[i] = (float)res * dinv;
             v[0] += b * b;
             v[1] += res * res;
     }
@@ -454,35 +490,7 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
         const bool conv = out[1] <= a.rtol2 * out[0];
         s->done = conv ? 1 : 0;
         if (conv && a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
-    }
-}
-
-// Start of one refinement pass: r32 = r, d = 0, u = D r32. The inner target
-// is the larger of a fixed FP32 reduction and what the outer test still
-// needs (with a margin for the FP32 recurrence), so a pass stops as soon as
-// one more FP64 residual can meet ||b - A x|| <= rtol ||b||.
-__global__ void k_mx_inner_init(MixArgs a) {
-    float v[1] = {0.0f};
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) {
-            const float res = (float)a.R[i];
-            a.Rl[i] = res;
-            a.Dl[i] = 0.0f;
-            a.Ul[i] = res * a.Dinv[i];
-            v[0] += res * res;
-    }
-    double out[1];
-    if (reduce_last2<1>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
-        CgState* s = a.cg;
-        s->bb = fmax(a.inner_rtol2 * out[0], 0.1 * a.rtol2 * a.ms->bb);
-        s->rr = out[0];
-        s->beta = 0.0;
-        s->iter = 0;
-        s->runs = 0;
-        const bool zero = !(out[0] > 0.0);
-        s->done = zero ? 1 : 0;
-        s->pending = 0;
-        if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, zero ? 0u : 1u);
+        if (!conv) mx_begin_pass(a, out[1]);
     }
 }
 
@@ -577,7 +585,7 @@ __device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float
     const float sp = first ? w : fmaf(beta, a.Sl[i], w);
     a.Pl[i] = p;
     a.Sl[i] = sp;
-    a.Dl[i] = fmaf(alpha, p, a.Dl[i]);
+    a.Dl[i] = first ? alpha * p : fmaf(alpha, p, a.Dl[i]);
     const float res = fmaf(-alpha, sp, a.Rl[i]);
     a.Rl[i] = res;
     a.Ul[i] = res * a.Dinv[i];
@@ -585,7 +593,10 @@ __device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float
 
 __global__ void k_mx_spmv(MixArgs a) {
     CgState* s = a.cg;
-    if (s->done) return;  // an iteration queued after convergence (host-driven loop)
+    if (s->done) {  // an iteration after the stop (rest of the loop body, host-driven lookahead)
+        mx_done_on_entry(a);
+        return;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0 && s->pending) {
         s->gamma = s->nx_gamma;
         s->alpha = s->nx_alpha;
@@ -598,7 +609,7 @@ __global__ void k_mx_spmv(MixArgs a) {
     block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials));
 }
 
-__global__ void k_mx_update(MixArgs a) {
+__global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     CgState* s = a.cg;
     __shared__ double prev[3];  // gamma_prev, alpha_prev, bb
     __shared__ float step[2];
@@ -627,7 +638,11 @@ __global__ void k_mx_update(MixArgs a) {
         q0 = a.Dinv[i0];
     }
     __syncthreads();
-    if (skip) return;
+    if (skip) {
+        if (iter_sh == 0)  // the pass stopped before its first update: d = 0
+            for (int64_t i = i0; i < a.n; i += stride) a.Dl[i] = 0.0f;
+        return;
+    }
     float out[3];
     all_blocks_sum_f32<3>(reinterpret_cast<const float*>(a.partials), a.part_blocks, out);
     const int iter = iter_sh;
@@ -665,7 +680,11 @@ __global__ void k_mx_update(MixArgs a) {
         }
     }
     __syncthreads();
-    if (stop) return;
+    if (stop) {
+        if (iter == 0)  // the pass stopped before its first update: d = 0
+            for (int64_t i = i0; i < a.n; i += stride) a.Dl[i] = 0.0f;
+        return;
+    }
     const float alpha = step[0], beta = step[1];
     const bool first = iter == 0;
     if (i0 < a.n) {
@@ -673,7 +692,7 @@ __global__ void k_mx_update(MixArgs a) {
         const float sp = first ? w0 : fmaf(beta, s0, w0);
         a.Pl[i0] = p;
         a.Sl[i0] = sp;
-        a.Dl[i0] = fmaf(alpha, p, d0);
+        a.Dl[i0] = first ? alpha * p : fmaf(alpha, p, d0);
         const float res = fmaf(-alpha, sp, r0);
         a.Rl[i0] = res;
         a.Ul[i0] = res * q0;
@@ -682,7 +701,10 @@ __global__ void k_mx_update(MixArgs a) {
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {
-    if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
+    if (a.cg->done) {  // an iteration queued after convergence (host-driven loop)
+        mx_done_on_entry(a);
+        return;
+    }
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) mx_spmv_row(a, i, v);
@@ -715,8 +737,11 @@ __global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {
 }
 
 __global__ void k_mx_update_red(MixArgs a) {
-    if (a.cg->done) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.cg->done) {
+        if (a.cg->iter == 0 && i < a.n) a.Dl[i] = 0.0f;  // the pass stopped before its first update
+        return;
+    }
     if (i < a.n) mx_update_row(a, i, (float)a.cg->alpha, (float)a.cg->beta, a.cg->iter == 1);
 }
 
@@ -736,6 +761,8 @@ __global__ void k_mx_refine(MixArgs a) {
         const float Ad = fmaf((float)a.dtau, ell_row32(a.A, i, a.Dl), a.mass32[i] * d);
         const double res = a.R[i] - (double)Ad;
         a.R[i] = res;
+        a.Rl[i] = (float)res;  // the next pass's FP32 residual and u (unread if none follows)
+        a.Ul[i] = (float)res * a.Dinv[i];
         v[0] += res * res;
     }
     double out[1];
@@ -743,13 +770,15 @@ __global__ void k_mx_refine(MixArgs a) {
         MixState* s = a.ms;
         s->rr = out[0];
         s->passes += 1;
-        *a.loop_kernels += 2;
+        *a.loop_kernels += 1;
         *a.refine_out = s->passes;
         const bool conv = out[0] <= a.rtol2 * s->bb;
         if (conv || s->passes >= a.max_refine) {
             s->done = 1;
             if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
             if (a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
+        } else {
+            mx_begin_pass(a, out[0]);
         }
     }
 }

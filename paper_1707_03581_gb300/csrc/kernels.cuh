@@ -228,7 +228,6 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r);
 __global__ void k_cg_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);
 __global__ void k_mx_init(MixArgs a, RhsArgs r);
-__global__ void k_mx_inner_init(MixArgs a);
 __global__ void k_mx_spmv(MixArgs a);
 __global__ void k_mx_spmv_red(MixArgs a);
 __global__ void k_mx_update(MixArgs a);

@@ -346,7 +346,7 @@ def test_mixed_eager_kernel_timing_counts_every_launch(torch):
     assert kt["k_mx_spmv"][0] == kt["k_mx_update"][0]
     assert kt["k_mx_spmv"][0] % 3 == 0
     assert rep["cg_iters_total"] + n_pass <= kt["k_mx_spmv"][0] <= rep["cg_iters_total"] + 3 * n_pass
-    assert kt["k_mx_inner_init"][0] == kt["k_mx_refine"][0] == n_pass
+    assert kt["k_mx_refine"][0] == n_pass and "k_mx_inner_init" not in kt
     s.close()
 
 
