@@ -192,7 +192,7 @@ def _rel_l2(a, b):
 # DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
 # capture of the current kernel on the named workload (summary under profiles/);
 # reported only for that workload, and to be cleared whenever the kernel changes.
-TRAFFIC = {("k_mx_spmv", 1): 70.5125e6 + 0.7048e6}
+TRAFFIC = {("k_mx_spmv", 1): 70.511872e6 + 0.678144e6}
 
 
 def _dominant_kernel(s, precision, kt, reps):

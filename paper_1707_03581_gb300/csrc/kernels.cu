@@ -624,11 +624,13 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
         prev[2] = s->bb;
     }
     // the first row's operands are loaded before the dot sums and the step
-    // lengths, so that their latency overlaps that chain
+    // lengths, so that their latency overlaps that chain; not by a thread that
+    // already sees the stop flag (set by an earlier kernel, or by this one's block
+    // 0 when it stops the solve, in which case no block updates rows)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float u0 = 0.0f, w0 = 0.0f, p0 = 0.0f, s0 = 0.0f, d0 = 0.0f, r0 = 0.0f, q0 = 0.0f;
-    if (i0 < a.n) {
+    if (i0 < a.n && !s->done) {
         u0 = a.Ul[i0];
         w0 = a.Wl[i0];
         p0 = a.Pl[i0];
