@@ -215,6 +215,44 @@ def _dominant_kernel(s, precision, kt, reps):
             work, kt.get("k_cg_spmv", (0, 0.0)))
 
 
+def _stationary_start(m, local, torch):
+    """The paper's initial state (Sec. 5): the same machine at rest with a 40 degC floor
+    under the stand (h = 500 W/m^2K) besides the 20 degC environment, solved for
+    K T0 = b_env on the device (FP64 Jacobi-PCG to 1e-12). Timed with CUDA events on the
+    solver's stream around the call; its relative residual is checked on the host from
+    the assembled system."""
+    import numpy as np
+    import scipy.sparse as sp
+
+    from paper_1707_03581_gb300 import Solver
+    from synth.machines import build_machine
+
+    f = build_machine(m.name + "-floor", m.stand.mesh.n, m.stock.mesh.n, floor=(500.0, 40.0), scheme=m.scheme,
+                      amp=m.amp, period=m.period, z0=m.z0, q0=m.q0, k_per_hex_stand=m.stand.k_per_hex,
+                      k_per_hex_stock=m.stock.k_per_hex)
+    s = Solver(local)
+    s.set_machine(f, precision="fp64")
+    st = s.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    iters = s.set_stationary_state(t0=f.t0, rtol=1e-12)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    T = s.temperature()
+    rp, col, val, _, genv = s.system()
+    K = sp.csr_matrix((val, col, rp), shape=(s.n, s.n))
+    res = float(np.linalg.norm(genv - K @ T) / np.linalg.norm(genv))
+    nf = f.stand.mesh.n_nodes
+    out = {"workload": f"{m.n_dof}-DOF machine at rest, stand on a 40 degC floor (h = 500 W/m^2K), "
+                       "20 degC environment (h = 10 W/m^2K)",
+           "ms": ms, "cg_iterations": iters, "ms_per_iteration": ms / max(iters, 1), "rel_residual": res,
+           "T_stand_range": [float(T[:nf].min()), float(T[:nf].max())]}
+    s.close()
+    return out
+
+
 def run_gpu(args, rank, world):
     import numpy as np
     import torch
@@ -353,6 +391,8 @@ def run_gpu(args, rank, world):
         line["gain_vs_fp64"] = value / v64
         line["accuracy"] = {"rel_l2_mixed_vs_fp64": rel_vs_fp64,
                             "after_steps": args.warmup + args.steps + 1}
+    if not args.no_stationary:
+        line["stationary_start"] = _stationary_start(m, local, torch)
     if not args.no_cpu_baseline and world == 1:
         try:
             import tempfile
@@ -528,6 +568,8 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stationary", action="store_true",
+                    help="skip the stationary-start measurement (Sec. 5 initial state)")
     ap.add_argument("--eager", action="store_true",
                     help="plain kernel launches with host-driven CG loops (for kernel-level profilers)")
     args = ap.parse_args()

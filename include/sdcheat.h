@@ -137,6 +137,14 @@ sdc_status sdc_set_body(sdc_ctx* ctx, int body, const double* xyz, int64_t n_nod
 sdc_status sdc_set_robin(sdc_ctx* ctx, int body, const int64_t* quad4, int64_t n_faces,
                          double h, double T_env);
 
+/* One more group of Robin faces of a body, with its own heat transfer
+ * coefficient and temperature (Sec. 2: B_env and b_env sum over the parts of
+ * the boundary that exchange heat with the environment, the floor or cooling
+ * equipment, each at its own temperature). sdc_set_robin replaces all groups
+ * of the body with one; sdc_add_robin appends one. Same arguments. */
+sdc_status sdc_add_robin(sdc_ctx* ctx, int body, const int64_t* quad4, int64_t n_faces,
+                         double h, double T_env);
+
 /* Contact between the stand's rail (stand_quads, per-body ids) and the stock
  * (stock_quads, per-body ids in the stock's reference position); Sec. 2,
  * Gamma_R(t), M_B, C_B (Eq. defCB) and b_X(t). Faces must be axis-aligned
@@ -298,6 +306,17 @@ sdc_status sdc_get_system(const sdc_ctx* ctx, int64_t* row_ptr, int64_t* col, do
 
 /* y = m .* x + dtau K x (the implicit-stage operator of Algorithms 1 and 2). */
 sdc_status sdc_apply_operator(sdc_ctx* ctx, double dtau, const double* x_dev, double* y_dev);
+
+/* Stationary initial state (Sec. 5: the machine at rest, in thermal exchange
+ * with the environment and cooling equipment only, 0 = f^I(T0) + g, i.e.
+ * K T0 = b_env). Solves it with Jacobi-PCG in FP64 on the device, from the
+ * current temperature (zero if none was set), to ||b_env - K T0||_2 <= rtol
+ * ||b_env||_2, and makes T0 the temperature at time t0 (as sdc_set_temperature
+ * does). K is nonsingular when every body has Robin faces with h > 0. Waits;
+ * *iters receives the CG iterations (may be NULL). SDC_ERR_NOT_CONVERGED after
+ * max_iter iterations (the state is then the last iterate). Uses n_dof doubles
+ * of device memory for the duration of the call. */
+sdc_status sdc_set_stationary_state(sdc_ctx* ctx, double t0, double rtol, int32_t max_iter, int32_t* iters);
 
 /* Solve (diag(m) + dtau K) x = b with Jacobi-PCG in the scheme's precision;
  * x_dev holds the initial guess on entry. Waits; *iters receives the

@@ -129,8 +129,14 @@ def robin_terms(xyz, quads, h, T_env):
     return B, b
 
 
-def body_system(xyz, hex8, k, rho, c, robin_quads, h, T_env, k_per_hex=None):
-    """K = -(A + B_env), lumped mass m and g = b_env of one body."""
+def body_system(xyz, hex8, k, rho, c, robin_quads, h, T_env, k_per_hex=None, robin_extra=()):
+    """K = -(A + B_env), lumped mass m and g = b_env of one body. B_env and b_env
+    sum over the Robin groups: (robin_quads, h, T_env) and each (quads, h, T_env)
+    of robin_extra."""
     A_neg, m = assemble_body(xyz, hex8, k, rho, c, k_per_hex)
     B_neg, b = robin_terms(xyz, robin_quads, h, T_env)
+    for quads, hg, Tg in robin_extra:
+        Bg, bg = robin_terms(xyz, quads, hg, Tg)
+        B_neg = B_neg + Bg
+        b = b + bg
     return (A_neg + B_neg).tocsr(), m, b

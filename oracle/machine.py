@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import contact as ct
 from . import fem
@@ -25,9 +26,11 @@ class MachineProblem:
     def __init__(self, machine, rtol=None, max_iter=None, solver="pcg", with_contact=True):
         st, sk = machine.stand, machine.stock
         Kf, mf, bf = fem.body_system(st.mesh.xyz, st.mesh.hex8, st.k, st.rho, st.c,
-                                     st.robin_quads, st.h, st.T_env, st.k_per_hex)
+                                     st.robin_quads, st.h, st.T_env, st.k_per_hex,
+                                     getattr(st, "robin_extra", ()))
         Km, mm, bm = fem.body_system(sk.mesh.xyz, sk.mesh.hex8, sk.k, sk.rho, sk.c,
-                                     sk.robin_quads, sk.h, sk.T_env, sk.k_per_hex)
+                                     sk.robin_quads, sk.h, sk.T_env, sk.k_per_hex,
+                                     getattr(sk, "robin_extra", ()))
         self.n_fix = st.mesh.n_nodes
         self.n = st.mesh.n_nodes + sk.mesh.n_nodes
         self.K = sp.block_diag([Kf, Km], format="csr")
@@ -48,6 +51,13 @@ class MachineProblem:
             raise ValueError("stand and stock contact faces lie in different planes")
         self.fe_calls = 0
         self.cg_total = 0
+
+    # ---- the stationary initial state of Sec. 5 ----
+    def stationary_state(self):
+        """T0 with 0 = f^I(T0) + g: the machine at rest, exchanging heat only with
+        the environment and cooling equipment (the contact term is not part of the
+        slow split), i.e. the sparse direct solve of K T0 = b_env."""
+        return spla.spsolve(self.K.tocsc(), self.genv)
 
     # ---- the split of Eq. ivp ----
     def fI(self, T):

@@ -65,6 +65,8 @@ _SIGS = {
     "sdc_set_body": (C.c_int, [_vp, C.c_int, _f64p, C.c_int64, _i64p, C.c_int64, _f64p,
                                C.c_double, C.c_double, C.c_double]),
     "sdc_set_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
+    "sdc_add_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
+    "sdc_set_stationary_state": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
     "sdc_set_contact": (C.c_int, [_vp, _i64p, C.c_int64, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_set_motion": (C.c_int, [_vp, _f64p, C.c_double, C.c_double, C.c_double]),
     "sdc_assemble": (C.c_int, [_vp]),
@@ -223,6 +225,18 @@ class Solver:
         q, pq = _i64(quads)
         self._call("sdc_set_robin", body, pq, q.shape[0], h, T_env)
 
+    def add_robin(self, body, quads, h, T_env):
+        """One more Robin group of the body (sdc_add_robin)."""
+        q, pq = _i64(quads)
+        self._call("sdc_add_robin", body, pq, q.shape[0], h, T_env)
+
+    def set_stationary_state(self, t0: float = 0.0, rtol: float = 1e-12, max_iter: int = 50000) -> int:
+        """Make the stationary state K T0 = b_env (Sec. 5) the temperature at t0; returns
+        the CG iterations (sdc_set_stationary_state)."""
+        it = C.c_int32()
+        self._call("sdc_set_stationary_state", float(t0), float(rtol), int(max_iter), C.byref(it))
+        return it.value
+
     def set_contact(self, stand_quads, stock_quads, h_c, q0):
         a, pa = _i64(stand_quads)
         b, pb = _i64(stock_quads)
@@ -294,6 +308,9 @@ class Solver:
                       m.stock.k_per_hex)
         self.set_robin(0, m.stand.robin_quads, m.stand.h, m.stand.T_env)
         self.set_robin(1, m.stock.robin_quads, m.stock.h, m.stock.T_env)
+        for b, body in enumerate((m.stand, m.stock)):
+            for quads, h, T_env in getattr(body, "robin_extra", ()):
+                self.add_robin(b, quads, h, T_env)
         self.set_contact(m.stand_contact, m.stock_contact, m.h_c, m.q0)
         self.set_motion(m.motion_dir, m.z0, m.amp, m.period)
         self.assemble()

@@ -1395,9 +1395,25 @@ sdc_status sdc_set_robin(sdc_ctx* c, int body, const int64_t* quad4, int64_t n_f
         require(n_faces >= 0 && (n_faces == 0 || quad4), SDC_ERR_ARG, "bad face list");
         require(h >= 0, SDC_ERR_ARG, "h must be >= 0");
         BodyInput& b = c->body[body];
-        b.robin.assign(quad4, quad4 + 4 * n_faces);
-        b.h = h;
-        b.T_env = T_env;
+        b.robin.assign(1, BodyInput::RobinGroup{});
+        b.robin[0].quads.assign(quad4, quad4 + 4 * n_faces);
+        b.robin[0].h = h;
+        b.robin[0].T_env = T_env;
+        c->assembled = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_add_robin(sdc_ctx* c, int body, const int64_t* quad4, int64_t n_faces, double h, double T_env) {
+    return guarded(c, [&] {
+        require(body == 0 || body == 1, SDC_ERR_ARG, "body must be 0 or 1");
+        require(n_faces >= 0 && (n_faces == 0 || quad4), SDC_ERR_ARG, "bad face list");
+        require(h >= 0, SDC_ERR_ARG, "h must be >= 0");
+        BodyInput::RobinGroup grp;
+        grp.quads.assign(quad4, quad4 + 4 * n_faces);
+        grp.h = h;
+        grp.T_env = T_env;
+        c->body[body].robin.push_back(std::move(grp));
         c->assembled = false;
         c->graph_ready = false;
     });
@@ -1707,6 +1723,67 @@ sdc_status sdc_solve(sdc_ctx* c, double dtau, const double* b, double* x, int32_
         SDC_CUDA_TRY(cudaMemcpy(&it, &c->st->cg_iters[0], sizeof(int), cudaMemcpyDeviceToHost));
         if (iters) *iters = it;
         read_state(c, nullptr);
+    });
+}
+
+sdc_status sdc_set_stationary_state(sdc_ctx* c, double t0, double rtol, int32_t max_iter, int32_t* iters) {
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(rtol > 0.0 && max_iter > 0, SDC_ERR_ARG, "rtol and max_iter must be positive");
+        const size_t bytes = (size_t)c->n * sizeof(double);
+        // K T0 = g is the implicit-stage system with zero mass and dtau = 1: a device vector of
+        // zeros stands in for m for this one solve
+        void* zero = nullptr;
+        if (c->alloc) {
+            zero = c->alloc(bytes, c->user);
+            if (!zero) throw ApiError(SDC_ERR_OOM, "device allocation of the zero mass vector failed");
+        } else if (cudaMalloc(&zero, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            throw ApiError(SDC_ERR_OOM, "cudaMalloc of the zero mass vector failed");
+        }
+        auto release = [&] {
+            cudaStreamSynchronize(c->stream);
+            if (c->alloc) c->free_fn(zero, c->user);
+            else cudaFree(zero);
+        };
+        try {
+            SDC_CUDA_TRY(cudaMemsetAsync(zero, 0, bytes, c->stream));
+            if (!c->temp_set) SDC_CUDA_TRY(cudaMemsetAsync(c->Tn, 0, bytes, c->stream));  // initial guess 0
+            // the time of the state, and a clear status for the solve to report into
+            StepState* h = c->st_host;
+            std::memset(h, 0, sizeof(StepState));
+            h->t0 = t0;
+            h->dt = c->scheme_set ? c->dt : 1.0;
+            SDC_CUDA_TRY(cudaMemcpyAsync(c->st, h, sizeof(StepState), cudaMemcpyHostToDevice, c->stream));
+            cudaGraph_t g;
+            SDC_CUDA_TRY(cudaGraphCreate(&g, 0));
+            std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> guard(g, &cudaGraphDestroy);
+            Chain ch(g);
+            CgArgs a = cg_args(c, 1.0, 0, rtol, max_iter);
+            a.mass = static_cast<const double*>(zero);
+            RhsArgs r{};
+            r.mode = RHS_GIVEN;
+            r.b_in = c->d_genv;
+            r.x0 = c->Tn;
+            r.pos = c->C.pos;
+            add_solve(c, ch, a, r);
+            ch.copy(c->Tn, c->X, bytes);
+            cudaGraphExec_t ex;
+            SDC_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+            cudaError_t e = cudaGraphLaunch(ex, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            cudaGraphExecDestroy(ex);
+            SDC_CUDA_TRY(e);
+            int it = 0;
+            SDC_CUDA_TRY(cudaMemcpy(&it, &c->st->cg_iters[0], sizeof(int), cudaMemcpyDeviceToHost));
+            if (iters) *iters = it;
+            c->temp_set = true;
+            read_state(c, nullptr);
+        } catch (...) {
+            release();
+            throw;
+        }
+        release();
     });
 }
 

@@ -26,8 +26,11 @@ struct BodyInput {
     std::vector<int64_t> hex8;    // n_hex x 8
     std::vector<double> k_hex;    // n_hex (empty = uniform)
     double k = 0, rho = 0, c = 0;
-    std::vector<int64_t> robin;   // n_faces x 4
-    double h = 0, T_env = 0;
+    struct RobinGroup {
+        std::vector<int64_t> quads;  // n_faces x 4
+        double h = 0, T_env = 0;
+    };
+    std::vector<RobinGroup> robin;   // Robin face groups (environment, cooling, floor ...)
     int64_t n_nodes() const { return (int64_t)xyz.size() / 3; }
     int64_t n_hex() const { return (int64_t)hex8.size() / 8; }
 };

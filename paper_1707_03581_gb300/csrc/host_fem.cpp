@@ -115,8 +115,9 @@ void assemble_body(const BodyInput& B, HostCSR& K, std::vector<double>& mass, st
     if (n >= (int64_t)std::numeric_limits<int32_t>::max()) throw ApiError(SDC_ERR_ARG, "too many nodes");
     for (int64_t v : B.hex8)
         if (v < 0 || v >= n) throw ApiError(SDC_ERR_ARG, "hexahedron node id out of range");
-    for (int64_t v : B.robin)
-        if (v < 0 || v >= n) throw ApiError(SDC_ERR_ARG, "Robin face node id out of range");
+    for (const auto& grp : B.robin)
+        for (int64_t v : grp.quads)
+            if (v < 0 || v >= n) throw ApiError(SDC_ERR_ARG, "Robin face node id out of range");
 
     // node -> element incidence
     std::vector<int64_t> inc_ptr(n + 1, 0), inc(ne * 8);
@@ -189,22 +190,23 @@ void assemble_body(const BodyInput& B, HostCSR& K, std::vector<double>& mass, st
         mass[i] = mi;
     }
 
-    // Robin faces: h int phi phi into K, h T_env int phi into genv
+    // Robin faces, group by group: h int phi phi into K, h T_env int phi into genv
     genv.assign(n, 0.0);
-    const int64_t nf = (int64_t)B.robin.size() / 4;
-    if (B.h != 0.0) {
+    for (const auto& grp : B.robin) {
+        if (grp.h == 0.0) continue;
+        const int64_t nf = (int64_t)grp.quads.size() / 4;
         for (int64_t f = 0; f < nf; ++f) {
             double X[4][3], Fe[16], fe[4];
             for (int a = 0; a < 4; ++a)
-                for (int i = 0; i < 3; ++i) X[a][i] = B.xyz[B.robin[f * 4 + a] * 3 + i];
+                for (int i = 0; i < 3; ++i) X[a][i] = B.xyz[grp.quads[f * 4 + a] * 3 + i];
             quad_face(X, Fe, fe);
             for (int a = 0; a < 4; ++a) {
-                const int64_t ra = B.robin[f * 4 + a];
-                genv[ra] += B.h * B.T_env * fe[a];
+                const int64_t ra = grp.quads[f * 4 + a];
+                genv[ra] += grp.h * grp.T_env * fe[a];
                 for (int b = 0; b < 4; ++b) {
-                    const int64_t p = find_col(K, ra, B.robin[f * 4 + b]);
+                    const int64_t p = find_col(K, ra, grp.quads[f * 4 + b]);
                     if (p < 0) throw ApiError(SDC_ERR_ARG, "Robin face is not a face of a hexahedron");
-                    K.val[p] += B.h * Fe[a * 4 + b];
+                    K.val[p] += grp.h * Fe[a * 4 + b];
                 }
             }
         }

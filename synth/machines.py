@@ -127,6 +127,8 @@ class Body:
     h: float
     T_env: float
     k_per_hex: Optional[np.ndarray] = None
+    # further Robin groups (quads, h, T_env): floor, cooling equipment ...
+    robin_extra: tuple = ()
 
 
 @dataclass
@@ -188,11 +190,13 @@ def build_machine(
     scheme: Optional[Scheme] = None,
     T0: float = 20.0,
     horizon: float = 60.0,
+    floor: Optional[tuple] = None,
 ) -> Machine:
     """Assemble the input arrays of one synthetic machine.
 
     stand_n must have nx divisible by 4 so that the rail strip x in [0.1, 0.3]
-    lies on mesh lines of the stand.
+    lies on mesh lines of the stand. floor = (h, T): the stand's y = 0 face
+    exchanges heat with a floor at T through h, as a Robin group of its own.
     """
     stand_n = tuple(int(v) for v in stand_n)
     stock_n = tuple(int(v) for v in stock_n)
@@ -204,9 +208,13 @@ def build_machine(
     # Stand: rail strip on y = 0.4 (ymax) is the contact; the rest of ymax and
     # all other sides are Robin faces.
     robin_stand = []
+    stand_extra = ()
     rail = None
     for side in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax"):
         quads, lo, hi = stand.side_quads(side)
+        if side == "ymin" and floor is not None:
+            stand_extra = ((quads, float(floor[0]), float(floor[1])),)
+            continue
         if side == "ymax":
             on_rail = (lo[:, 0] >= RAIL_X[0] - 1e-12) & (hi[:, 0] <= RAIL_X[1] + 1e-12)
             rail = quads[on_rail]
@@ -227,7 +235,7 @@ def build_machine(
 
     return Machine(
         name=name,
-        stand=Body(stand, k, rho, c, robin_stand, h, T_env, k_per_hex_stand),
+        stand=Body(stand, k, rho, c, robin_stand, h, T_env, k_per_hex_stand, stand_extra),
         stock=Body(stock, k, rho, c, robin_stock, h, T_env, k_per_hex_stock),
         stand_contact=rail,
         stock_contact=contact_stock,
