@@ -964,15 +964,22 @@ void emit_step(sdc_ctx* c, Chain& ch) {
                       (const double*)c->Tstd[m], c->FI[set][m - 1], (int*)nullptr);
         }
     };
-    auto bulk = [&](BulkArgs& b, const double* Fx0) {
+    // The bulk endpoint in two launches: f*_m on the contact rows, which the substep loop
+    // needs, then T_m (and its increment) off the contact as a side branch beside the loop,
+    // which writes the contact rows. The returned branch node is joined after the loop.
+    auto bulk = [&](BulkArgs& b, const double* Fx0) -> cudaGraphNode_t {
+        b.dof = c->C.dof;
+        b.n_iface = NI;
         if (mixed) {
             b.dX = c->Dsum;
             b.Fx0 = Fx0;
             b.dT = c->dTv;
-            ch.kernel(k_bulk_endpoint_mx, row_grid(c, k_bulk_endpoint_mx), (unsigned)RED_BLOCK, b);
-        } else {
-            ch.kernel(k_bulk_endpoint, row_grid(c, k_bulk_endpoint), (unsigned)RED_BLOCK, b);
         }
+        auto kern = mixed ? k_bulk_endpoint_mx : k_bulk_endpoint;
+        b.rows = BULK_CONTACT;
+        ch.kernel(kern, blocks_for(std::max(NI, 1), 256), 256u, b);
+        b.rows = BULK_OFF_CONTACT;
+        return ch.branch_kernel({ch.last}, kern, dim3(row_grid(c, kern)), dim3(RED_BLOCK), b);
     };
 
     auto sdt_row = [&](int m, double* out) {
@@ -1081,8 +1088,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         b.n = c->n;
         b.pos = c->C.pos;
         b.fstar_I = c->fst;
-        bulk(b, F_at(m - 1, 0));
+        const cudaGraphNode_t off = bulk(b, F_at(m - 1, 0));
         substeps(ii, m, RHS_PRED, 0, 0, pn);
+        ch.join(off);
         fi(m, 0);
     }
     // ---- Algorithm 2 (sweeps)
@@ -1122,8 +1130,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.n = c->n;
             b.pos = c->C.pos;
             b.fstar_I = c->fst;
-            bulk(b, c->FI[so][m - 1]);
+            const cudaGraphNode_t off = bulk(b, c->FI[so][m - 1]);
             substeps(ii, m, RHS_SWEEP, so, sn, pn);
+            ch.join(off);
             if (k < K || c->residuals) fi(m, sn);
         }
     }

@@ -793,9 +793,17 @@ __global__ void k_mx_refine(MixArgs a) {
 //   m T_{m,P} = m T_{m-1} + dtau f*_m + sum_j dt s_{m,j} F^I_j
 // (sum_p stil_{m,p,j} = s_{m,j}). Contact rows are overwritten by the
 // substep loop that follows.
+// The row a thread of a bulk-endpoint launch handles (BulkArgs::rows), or -1.
+__device__ __forceinline__ int64_t bulk_row(const BulkArgs& a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.rows == BULK_CONTACT) return t < a.n_iface ? (int64_t)a.dof[t] : -1;
+    if (t >= a.n) return -1;
+    return (a.rows == BULK_OFF_CONTACT && a.pos[t] >= 0) ? -1 : t;
+}
+
 __global__ void k_bulk_endpoint(BulkArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) {
+    const int64_t i = bulk_row(a);
+    if (i >= 0) {
         const double KX = ell_row(a.A, i, a.X);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
@@ -807,9 +815,9 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
             for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
             incr = fma(a.dtau, fstar, I);
         }
-        a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
         const int pa = a.pos[i];
-        if (pa >= 0) a.fstar_I[pa] = fstar;
+        if (pa >= 0) a.fstar_I[pa] = fstar;  // contact rows: T_m comes from the substep loop
+        else a.Tout[i] = fma(incr, a.minv[i], a.Tprev[i]);
     }
 }
 
@@ -818,8 +826,8 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
 //   sweep:     f*_m = f^I(T*) - f^I(T^k_m) = -K dX          (x0 = T^k_m)
 // K dX as an FP32 SpMV; the increment of every row goes to dT for k_fi_mx.
 __global__ void k_bulk_endpoint_mx(BulkArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) {
+    const int64_t i = bulk_row(a);
+    if (i >= 0) {
         const double KdX = (double)ell_row32(a.A, i, a.dX);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
@@ -831,11 +839,14 @@ __global__ void k_bulk_endpoint_mx(BulkArgs a) {
             for (int j = 0; j < a.nFI; ++j) I = fma(a.Sdt[j], a.FI[j][i], I);
             incr = fma(a.dtau, fstar, I);
         }
-        const double dT = incr * a.minv[i];
-        a.Tout[i] = a.Tprev[i] + dT;
-        a.dT[i] = (float)dT;
         const int pa = a.pos[i];
-        if (pa >= 0) a.fstar_I[pa] = fstar;
+        if (pa >= 0) {
+            a.fstar_I[pa] = fstar;  // contact rows: T_m and its increment come from the substep loop
+        } else {
+            const double dT = incr * a.minv[i];
+            a.Tout[i] = a.Tprev[i] + dT;
+            a.dT[i] = (float)dT;
+        }
     }
 }
 

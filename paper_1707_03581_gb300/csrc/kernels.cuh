@@ -95,6 +95,8 @@ struct RhsArgs {
 };
 
 // Bulk endpoint update after the solve (see k_bulk_endpoint).
+enum { BULK_ALL = 0, BULK_CONTACT = 1, BULK_OFF_CONTACT = 2 };
+
 struct BulkArgs {
     EllDev A;
     const double* minv;
@@ -111,6 +113,11 @@ struct BulkArgs {
     int64_t n;
     const int32_t* pos;             // DOF -> contact index or -1
     double* fstar_I;                // [NI] f*_m on the contact DOFs (output)
+    // rows of this launch: BULK_ALL, BULK_CONTACT (one thread per contact DOF, through dof),
+    // or BULK_OFF_CONTACT (every row not on the contact)
+    int rows;
+    const int32_t* dof;             // [NI] contact index -> DOF
+    int n_iface;
     // mixed precision (k_bulk_endpoint_mx): T* = x0 + dX with dX the solve's accumulated FP32
     // correction, so K T* = K x0 + K dX with K x0 known through F^I(x0); the pass over K is
     // an FP32 SpMV of dX. The output increment T_m - T_{m-1} goes to dT (FP32).
