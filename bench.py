@@ -499,6 +499,79 @@ def run_batch(args, rank, world):
         s.close()
 
 
+def run_orders(args, rank, world):
+    """The reduced problem of Sec. 4 (synth.slab_machine: a stand rectangle under a moving
+    source of constant temperature) on the GPU, FP64: the measured order of MRSDC with
+    k = 0..4 sweeps for (M, P) = (5, 8) and (5, 2) with the literal embedded weights,
+    against a reference from 256 steps of (5, 8) with 8 sweeps, and the SDC residual of
+    the first macro step after k sweeps for three step sizes. Theory: order
+    min(M, P, k + 1); every sweep divides the residual by a factor proportional to dt."""
+    import numpy as np
+    import torch
+
+    from paper_1707_03581_gb300 import Solver
+    from synth.machines import Scheme, slab_machine
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    t_end = 2.0
+
+    def slab(M, P, K, dt, cap=1e12):
+        return slab_machine(4, 16, scheme=Scheme("equi_noleft", M, P, K, P, dt, 1e-14, 4000), rho=10.0, c=1000.0,
+                            capacity_ratio=cap)
+
+    def run(mach, T0, n, residuals=False):
+        s = Solver(local)
+        s.set_machine(mach, precision="fp64", T0=T0, residuals=residuals)
+        reps = [s.step(report=True) for _ in range(n)]
+        T = s.temperature()
+        s.close()
+        return T, reps
+
+    t0 = time.perf_counter()
+    mach, T0 = slab(5, 8, 8, t_end / 256)
+    ref, _ = run(mach, T0, 256)
+    nf = mach.stand.mesh.n_nodes
+
+    def err(T):
+        return float(np.linalg.norm(T[:nf] - ref[:nf]) / np.linalg.norm(ref[:nf] - T0[:nf]))
+
+    steps = (2, 4, 8, 16, 32)
+    orders, errors, ratio = {}, {}, []
+    for M, P in ((5, 8), (5, 2)):
+        key = f"({M},{P})"
+        orders[key], errors[key] = [], []
+        for k in range(5):
+            e = [err(run(slab(M, P, k, t_end / n)[0], T0, n)[0]) for n in steps]
+            ok = [i for i in range(len(steps) - 1) if e[i + 1] >= 1e-9]
+            i = ok[-1] if ok else 0
+            order = float(np.log2(e[i] / e[i + 1]))
+            orders[key].append(order)
+            errors[key].append(e)
+            ratio.append(order / min(M, P, k + 1))
+    residuals = {}
+    for n in (5, 10, 20, 40):
+        m, Tr = slab(5, 8, 4, t_end / n, cap=1e6)
+        residuals[f"dt={t_end / n:g}"] = [float(r) for r in run(m, Tr, 1, residuals=True)[1][0]["residual"]]
+    wall = time.perf_counter() - t0
+    if rank != 0:
+        return
+    line = {
+        "metric": "measured order / min(M, P, k+1), MRSDC on the reduced problem of Sec. 4 (worst case)",
+        "value": min(ratio), "unit": "ratio", "n_gpus": world, "steps": None, "warmup": 0, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"slab 1x4x16 hexes ({mach.n_dof} DOF) under a 100 degC source moving along its "
+                               f"top edge, equidistant nodes without the left end point, literal embedded weights, "
+                               f"t_end = {t_end} s",
+                   "orders_from": "the smallest pair of step sizes whose errors stay above 1e-9"},
+        "orders": orders, "expected": {"(5,8)": [1, 2, 3, 4, 5], "(5,2)": [1, 2, 2, 2, 2]},
+        "errors_at_t_end": {"steps": list(steps), **errors},
+        "residual_after_k_sweeps": residuals,
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, rank, world):
     """Serving workload: Poisson arrivals (rate --lam) of look-ahead requests, each a
     machine of the 64-machine pool with horizon ~ U(30, 600) s from its resident
@@ -562,7 +635,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
     ap.add_argument("--config", type=int, default=1,
                     help="0/1/2: one machine (1 = the headline workload); 3: the batch of 64 machines; "
-                         "4: serving (Poisson arrivals)")
+                         "4: serving (Poisson arrivals); 5: convergence order and residual decay on the "
+                         "reduced problem of Sec. 4")
     ap.add_argument("--machines", type=int, default=None, help="config 3: use only the first machines")
     ap.add_argument("--lam", type=float, default=10.0, help="config 4: arrival rate [requests/s]")
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
@@ -590,6 +664,8 @@ def main():
         run_batch(args, rank, world)
     elif args.config == 4:
         run_serving(args, rank, world)
+    elif args.config == 5:
+        run_orders(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

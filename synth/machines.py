@@ -338,6 +338,56 @@ CONFIGS = {
 }
 
 
+def slab_machine(ny: int = 8, nz: int = 32, *, scheme: Optional[Scheme] = None, T_source: float = 100.0,
+                 T_stand: float = 20.0, alpha: float = 2000.0, speed: float = 0.1, period: float = 80.0,
+                 thickness: float = 0.05, height: float = 1.0, length: float = 4.0, source_len: float = 0.2,
+                 capacity_ratio: float = 1e12, k: float = STEEL_K, rho: float = STEEL_RHO, c: float = STEEL_C):
+    """The reduced problem of Sec. 4 as a two-body machine: a stand rectangle
+    (length x height in z and y) whose top edge meets a small source of constant
+    temperature T_source moving along it; every other edge insulated, no
+    environment (g = 0), no friction.
+
+    The rectangle is a slab one hexahedron thick in x with insulated faces, so
+    the trilinear model reduces exactly to the bilinear one of Sec. 4 (nodal
+    values equal on both faces). The source is a stock whose volumetric heat
+    capacity is capacity_ratio times the stand's, so its temperature stays at
+    T_source to ~1/capacity_ratio. The exchange alpha (T_source - T) on the
+    overlap is the contact term with h_c = alpha. The source moves by the
+    library's motion law, s(t) = z0 + A sin(2 pi t / period), with A set so that
+    its speed at t = 0 is -speed (the paper moves it at a constant -0.1 m/s),
+    starting with its centre at the middle of the top edge.
+
+    Returns (machine, T0) with T0 the initial temperature vector (stand nodes
+    first)."""
+    stand = box_mesh((0.0, 0.0, 0.0), (thickness, height, length), (1, ny, nz))
+    hz = length / nz
+    ns = max(1, int(round(source_len / hz)))
+    stock = box_mesh((0.0, height, 0.0), (thickness, height / ny, ns * hz), (1, 1, ns))
+    top, _, _ = stand.side_quads("ymax")
+    bottom, _, _ = stock.side_quads("ymin")
+    none = np.zeros((0, 4), dtype=np.int64)
+    amp = -speed * period / (2.0 * np.pi)
+    z0 = 0.5 * length - 0.5 * ns * hz
+    m = Machine(
+        name=f"slab-{ny}x{nz}",
+        stand=Body(stand, k, rho, c, none, 0.0, T_stand),
+        stock=Body(stock, k, rho * capacity_ratio, c, none, 0.0, T_source),
+        stand_contact=top,
+        stock_contact=bottom,
+        h_c=alpha,
+        q0=0.0,
+        motion_dir=(0.0, 0.0, 1.0),
+        z0=z0,
+        amp=amp,
+        period=period,
+        scheme=scheme if scheme is not None else Scheme("equi_noleft", 5, 8, 4, 8, 1.0, 1e-14, 4000),
+        T0=T_stand,
+        horizon=20.0,
+    )
+    T0 = np.concatenate([np.full(stand.n_nodes, T_stand), np.full(stock.n_nodes, T_source)])
+    return m, T0
+
+
 def with_scheme(machine: Machine, **kw) -> Machine:
     """A copy of `machine` with some scheme fields replaced."""
     return replace(machine, scheme=replace(machine.scheme, **kw))
