@@ -1,4 +1,5 @@
-"""IMEX multi-rate SDC, Algorithms 1 and 2 taken literally (oracle; test infrastructure only).
+"""IMEX multi-rate SDC, Algorithms 1 and 2 taken literally, and single-rate
+semi-implicit SDC (Sec. 3) for comparison (oracle; test infrastructure only).
 
 Problem interface (any object with):
     mass           (N,) diagonal of M (lumped)
@@ -153,6 +154,61 @@ def mrsdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False, keep_nodes=F
     if keep_nodes:
         res.T_std, res.T_emb = T_std, T_emb
     return T_std[M].copy(), res
+
+
+def sisdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False):
+    """One macro step of single-rate semi-implicit SDC (Sec. 3), the method MRSDC
+    extends; returns (T(t_n + dt), StepResult). f^E is evaluated only at the
+    standard nodes:
+
+    predictor (IMEX Euler from node to node), for m = 1..M:
+        M T_m = M T_{m-1} + dtau_m (f^I(T_m) + g(tau_m)) + dtau_m f^E(T_{m-1}, tau_{m-1})
+    sweep (Eq. sdc_sweep), for m = 1..M:
+        M T^{k+1}_m = M T^{k+1}_{m-1} + dtau_m (f^I(T^{k+1}_m) - f^I(T^k_m))
+                      + dtau_m (f^E(T^{k+1}_{m-1}, tau_{m-1}) - f^E(T^k_{m-1}, tau_{m-1}))
+                      + I_{m-1}^m,
+        I_{m-1}^m = sum_j s_{m,j} F(T^k_j, tau_j),  F = f^I + g + f^E.
+
+    The residual (Eq. residual) uses this I_{m-1}^m."""
+    M = W["M"]
+    c = W["c"]
+    tau = [t_n + dt * c[m] for m in range(M + 1)]          # tau[0] = t_n
+    mass = prob.mass
+    res = StepResult()
+
+    def quadrature(T):
+        F = [prob.fI(T[j + 1]) + prob.g(tau[j + 1]) + prob.fE(T[j + 1], tau[j + 1]) for j in range(M)]
+        I = []
+        for m in range(M):
+            acc = np.zeros_like(T_n)
+            for j in range(M):
+                acc = acc + dt * W["S"][m, j] * F[j]
+            I.append(acc)
+        return I
+
+    T = [T_n.copy()] + [None] * M
+    for m in range(M):
+        dtau = tau[m + 1] - tau[m]
+        rhs = mass * T[m] + dtau * (prob.g(tau[m + 1]) + prob.fE(T[m], tau[m]))
+        T[m + 1], it = prob.solve(dtau, rhs, T[m])
+        res.cg_iters.append(it)
+    for k in range(sweeps):
+        I = quadrature(T)
+        if want_residuals:
+            res.residuals.append(_residual(prob, T_n, T, I))
+        fe_left_old = [prob.fE(T[m], tau[m]) for m in range(M)]   # f^E(T^k_{m-1}, tau_{m-1})
+        new = [T_n.copy()] + [None] * M
+        for m in range(M):
+            dtau = tau[m + 1] - tau[m]
+            fI_old = prob.fI(T[m + 1])                            # f^I(T^k_m)
+            rhs = (mass * new[m] - dtau * fI_old
+                   + dtau * (prob.fE(new[m], tau[m]) - fe_left_old[m]) + I[m])
+            new[m + 1], it = prob.solve(dtau, rhs, T[m + 1])
+            res.cg_iters.append(it)
+        T = new
+    if want_residuals:
+        res.residuals.append(_residual(prob, T_n, T, quadrature(T)))
+    return T[M].copy(), res
 
 
 def run(prob, T0, t0, dt, W, sweeps, n_steps, callback=None):
