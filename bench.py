@@ -253,6 +253,42 @@ def _stationary_start(m, local, torch):
     return out
 
 
+def _single_rate(m, local, torch, args, flush):
+    """Single-rate semi-implicit SDC (Sec. 3) on the same machine, nodes, sweeps and dt
+    (mixed precision): f^E only at the standard nodes, no substeps. Timed like the
+    headline (CUDA events around each step, L2 flushed between steps); and its relative
+    difference from MRSDC after 5 macro steps from the same start, i.e. what resolving
+    the contact term on the embedded nodes changes."""
+    import numpy as np
+
+    from paper_1707_03581_gb300 import Solver
+    from synth.machines import with_scheme
+
+    a = Solver(local)
+    a.set_machine(with_scheme(m, P=1, window=0), precision=args.precision)
+    a.set_single_rate(True)
+    b = Solver(local)
+    b.set_machine(m, precision=args.precision)
+    for _ in range(5):
+        a.step(report=False)
+        b.step(report=False)
+    Ta, Tb = a.temperature(), b.temperature()
+    diff = float(np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb))
+    rise = float(np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb - m.T0))
+    b.close()
+    st = a.stream
+    with torch.cuda.stream(st):
+        for _ in range(args.warmup):
+            a.step(report=False)
+        torch.cuda.synchronize()
+        ms = _timed_steps(a, st, flush, args.steps, torch)
+        rep = a.step(report=True)
+    a.close()
+    ms_step = float(sum(ms) / len(ms))
+    return {"ms_per_step": ms_step, "eta": m.scheme.dt / (ms_step * 1e-3), "cg_iters_per_step": rep["cg_iters_total"],
+            "rel_l2_vs_mrsdc_after_5_steps": diff, "rel_l2_rise_vs_mrsdc_after_5_steps": rise}
+
+
 def run_gpu(args, rank, world):
     import numpy as np
     import torch
@@ -393,6 +429,8 @@ def run_gpu(args, rank, world):
                             "after_steps": args.warmup + args.steps + 1}
     if not args.no_stationary:
         line["stationary_start"] = _stationary_start(m, local, torch)
+    if not args.no_single_rate:
+        line["single_rate"] = _single_rate(m, local, torch, args, flush)
     if not args.no_cpu_baseline and world == 1:
         try:
             import tempfile
@@ -642,6 +680,8 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-single-rate", action="store_true",
+                    help="skip the single-rate SDC comparison (Sec. 3) on the same machine")
     ap.add_argument("--no-stationary", action="store_true",
                     help="skip the stationary-start measurement (Sec. 5 initial state)")
     ap.add_argument("--eager", action="store_true",

@@ -95,6 +95,8 @@ struct sdc_ctx {
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
+    int single_rate = 0;            // sdc_set_single_rate
+    double* fe_std[2][MAX_M + 1] = {};  // single-rate SDC: f^E at the standard nodes, by iterate
     int in_batch = 0;               // batches holding this context (their members run without side branches)
     void* iface_rep = nullptr;      // their buffers
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
@@ -889,6 +891,15 @@ void alloc_scheme_buffers(sdc_ctx* c) {
         c->ihat[s] = dalloc_n<double>(c, c->pool_scheme, (size_t)n_int * NI);
         SDC_CUDA_TRY(cudaMemsetAsync(c->ihat[s], 0, (size_t)n_int * NI * sizeof(double), c->stream));
     }
+    // f^E at the standard nodes for single-rate SDC: the nodes up to the first interval's
+    // left end hold f^E(T_n, t_n) in both iterates (one buffer); later nodes one per iterate
+    {
+        double* fe0 = dalloc_n<double>(c, c->pool_scheme, NI);
+        for (int s = 0; s < 2; ++s)
+            for (int j = 0; j <= M; ++j)
+                c->fe_std[s][j] = j < c->nondeg[0] ? fe0 : (s == 0 ? dalloc_n<double>(c, c->pool_scheme, NI) : nullptr);
+        for (int j = c->nondeg[0]; j <= M; ++j) c->fe_std[1][j] = dalloc_n<double>(c, c->pool_scheme, NI);
+    }
     c->cpre = dalloc_n<double>(c, c->pool_scheme, (size_t)P * NI);
     c->fst = dalloc_n<double>(c, c->pool_scheme, NI);
     pick_iface_cluster(c);
@@ -1063,56 +1074,116 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ch.kernel(k_residual, row_grid(c, k_residual), (unsigned)RED_BLOCK, ra);
     };
 
-    // ---- Algorithm 1 (predictor)
-    for (int ii = 0; ii < n_int; ++ii) {
-        const int m = c->nondeg[ii];
-        const double dtau = dt * (W.c[m] - W.c[m - 1]);
-        const cudaGraphNode_t pn = prep(ii, m, RHS_PRED, 0, {ch.last, ii == 0 ? geom : nullptr});
-        RhsArgs r{};
-        r.mode = RHS_PRED;
-        r.Tprev = c->Tstd[m - 1];
-        r.g = c->d_genv;
-        r.x0 = c->Tstd[m - 1];
-        r.Fx0 = F_at(m - 1, 0);
-        r.pos = c->C.pos;
-        add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
-        BulkArgs b{};
-        b.A = c->A;
-        b.minv = c->d_minv;
-        b.g = c->d_genv;
-        b.X = c->X;
-        b.Tprev = c->Tstd[m - 1];
-        b.Tout = c->Tstd[m];
-        b.dtau = dtau;
-        b.mode = RHS_PRED;
-        b.n = c->n;
-        b.pos = c->C.pos;
-        b.fstar_I = c->fst;
-        const cudaGraphNode_t off = bulk(b, F_at(m - 1, 0));
-        substeps(ii, m, RHS_PRED, 0, 0, pn);
-        ch.join(off);
-        fi(m, 0);
-    }
-    // ---- Algorithm 2 (sweeps)
-    for (int k = 1; k <= K; ++k) {
-        const int so = (k - 1) & 1, sn = k & 1;
-        if (c->residuals) residual(so, k - 1);
+    if (c->single_rate) {
+        // ---- single-rate semi-implicit SDC (Sec. 3): f^E only at the standard nodes, in the
+        // right-hand side of each interval's implicit stage; no substeps
+        auto sis = [&]() {
+            SisdcArgs a{};
+            a.C = c->C;
+            a.E = c->E;
+            a.cs = c->iface_cluster;
+            a.chunk = c->iface_chunk;
+            return a;
+        };
+        const unsigned gi = blocks_for(std::max(NI, 1), 256);
+        // f^E(T, tau) at the slot of a standard node (an end slot of an interval)
+        auto fe_at = [&](const double* T, int slot, double* out) {
+            SisdcArgs a = sis();
+            a.T = T;
+            a.slot = slot;
+            a.fe_out = out;
+            ch.kernel(k_sisdc_fe, gi, 256u, a);
+        };
+        auto endpoint = [&](int m) {
+            ch.kernel(k_sisdc_endpoint, row_grid(c, k_sisdc_endpoint), (unsigned)RED_BLOCK, (const double*)c->X,
+                      (const double*)c->Tstd[m - 1], c->Tstd[m], mixed ? c->dTv : (float*)nullptr, (int64_t)c->n);
+        };
+        // f^E(T_n, t_n), the left node of the first interval in every iterate
+        ch.join(geom);
+        fe_at(c->Tn, 0, c->fe_std[0][c->nondeg[0] - 1]);
         for (int ii = 0; ii < n_int; ++ii) {
             const int m = c->nondeg[ii];
             const double dtau = dt * (W.c[m] - W.c[m - 1]);
-            const cudaGraphNode_t pn = prep(ii, m, RHS_SWEEP, so, {ch.last});
+            SisdcArgs a = sis();
+            a.mode = RHS_PRED;
+            a.dtau = dtau;
+            a.fe_left_new = c->fe_std[0][m - 1];
+            a.ihat = c->ihat[0] + (size_t)ii * NI;
+            ch.kernel(k_sisdc_rhs, gi, 256u, a);
             RhsArgs r{};
-            r.mode = RHS_SWEEP;
+            r.mode = RHS_PRED;
             r.Tprev = c->Tstd[m - 1];
             r.g = c->d_genv;
-            r.FIm = c->FI[so][m - 1];
-            for (int j = 0; j < M; ++j) r.FI[j] = c->FI[so][j];
-            sdt_row(m, r.Sdt);
-            r.nFI = M;
-            r.ihat = c->ihat[so] + (size_t)ii * NI;
+            r.x0 = c->Tstd[m - 1];
+            r.Fx0 = F_at(m - 1, 0);
             r.pos = c->C.pos;
-            r.x0 = c->Tstd[m];
-            r.Fx0 = c->FI[so][m - 1];
+            r.ihat = a.ihat;
+            add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
+            endpoint(m);
+            fe_at(c->Tstd[m], ii * (P + 1) + P, c->fe_std[0][m]);
+            fi(m, 0);
+        }
+        for (int k = 1; k <= K; ++k) {
+            const int so = (k - 1) & 1, sn = k & 1;
+            for (int ii = 0; ii < n_int; ++ii) {
+                const int m = c->nondeg[ii];
+                const double dtau = dt * (W.c[m] - W.c[m - 1]);
+                SisdcArgs a = sis();
+                a.mode = RHS_SWEEP;
+                a.dtau = dtau;
+                a.fe_left_new = c->fe_std[sn][m - 1];
+                a.fe_left_old = c->fe_std[so][m - 1];
+                for (int j = 0; j < M; ++j) a.fe_old[j] = c->fe_std[so][j + 1];
+                sdt_row(m, a.Sdt);
+                a.nFE = M;
+                a.ihat = c->ihat[0] + (size_t)ii * NI;
+                ch.kernel(k_sisdc_rhs, gi, 256u, a);
+                RhsArgs r{};
+                r.mode = RHS_SWEEP;
+                r.Tprev = c->Tstd[m - 1];
+                r.g = c->d_genv;
+                r.FIm = c->FI[so][m - 1];
+                for (int j = 0; j < M; ++j) r.FI[j] = c->FI[so][j];
+                sdt_row(m, r.Sdt);
+                r.nFI = M;
+                r.ihat = a.ihat;
+                r.pos = c->C.pos;
+                r.x0 = c->Tstd[m];
+                r.Fx0 = c->FI[so][m - 1];
+                add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
+                endpoint(m);
+                fe_at(c->Tstd[m], ii * (P + 1) + P, c->fe_std[sn][m]);
+                if (k < K) fi(m, sn);
+            }
+        }
+        // the contact heat of the step for the ledger (k_step_end): the quadrature
+        // sum_j dt s_{m,j} f^E(T_j, tau_j) of the final iterate, per interval
+        const int fin = K & 1;
+        for (int ii = 0; ii < n_int; ++ii) {
+            const int m = c->nondeg[ii];
+            SisdcArgs a = sis();
+            a.mode = RHS_SWEEP;
+            a.dtau = 0.0;
+            a.fe_left_new = a.fe_left_old = c->fe_std[fin][m - 1];
+            for (int j = 0; j < M; ++j) a.fe_old[j] = c->fe_std[fin][j + 1];
+            sdt_row(m, a.Sdt);
+            a.nFE = M;
+            a.ihat = c->ihat[K & 1] + (size_t)ii * NI;
+            ch.kernel(k_sisdc_rhs, gi, 256u, a);
+        }
+    } else {
+        // ---- Algorithm 1 (predictor)
+        for (int ii = 0; ii < n_int; ++ii) {
+            const int m = c->nondeg[ii];
+            const double dtau = dt * (W.c[m] - W.c[m - 1]);
+            const cudaGraphNode_t pn = prep(ii, m, RHS_PRED, 0, {ch.last, ii == 0 ? geom : nullptr});
+            RhsArgs r{};
+            r.mode = RHS_PRED;
+            r.Tprev = c->Tstd[m - 1];
+            r.g = c->d_genv;
+            r.x0 = c->Tstd[m - 1];
+            r.Fx0 = F_at(m - 1, 0);
+            r.pos = c->C.pos;
             add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
             BulkArgs b{};
             b.A = c->A;
@@ -1121,19 +1192,58 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.X = c->X;
             b.Tprev = c->Tstd[m - 1];
             b.Tout = c->Tstd[m];
-            b.FIm = c->FI[so][m - 1];
-            for (int j = 0; j < M; ++j) b.FI[j] = c->FI[so][j];
-            sdt_row(m, b.Sdt);
-            b.nFI = M;
             b.dtau = dtau;
-            b.mode = RHS_SWEEP;
+            b.mode = RHS_PRED;
             b.n = c->n;
             b.pos = c->C.pos;
             b.fstar_I = c->fst;
-            const cudaGraphNode_t off = bulk(b, c->FI[so][m - 1]);
-            substeps(ii, m, RHS_SWEEP, so, sn, pn);
+            const cudaGraphNode_t off = bulk(b, F_at(m - 1, 0));
+            substeps(ii, m, RHS_PRED, 0, 0, pn);
             ch.join(off);
-            if (k < K || c->residuals) fi(m, sn);
+            fi(m, 0);
+        }
+        // ---- Algorithm 2 (sweeps)
+        for (int k = 1; k <= K; ++k) {
+            const int so = (k - 1) & 1, sn = k & 1;
+            if (c->residuals) residual(so, k - 1);
+            for (int ii = 0; ii < n_int; ++ii) {
+                const int m = c->nondeg[ii];
+                const double dtau = dt * (W.c[m] - W.c[m - 1]);
+                const cudaGraphNode_t pn = prep(ii, m, RHS_SWEEP, so, {ch.last});
+                RhsArgs r{};
+                r.mode = RHS_SWEEP;
+                r.Tprev = c->Tstd[m - 1];
+                r.g = c->d_genv;
+                r.FIm = c->FI[so][m - 1];
+                for (int j = 0; j < M; ++j) r.FI[j] = c->FI[so][j];
+                sdt_row(m, r.Sdt);
+                r.nFI = M;
+                r.ihat = c->ihat[so] + (size_t)ii * NI;
+                r.pos = c->C.pos;
+                r.x0 = c->Tstd[m];
+                r.Fx0 = c->FI[so][m - 1];
+                add_implicit_solve(c, ch, dtau, solve++, c->rtol, c->max_iter, r);
+                BulkArgs b{};
+                b.A = c->A;
+                b.minv = c->d_minv;
+                b.g = c->d_genv;
+                b.X = c->X;
+                b.Tprev = c->Tstd[m - 1];
+                b.Tout = c->Tstd[m];
+                b.FIm = c->FI[so][m - 1];
+                for (int j = 0; j < M; ++j) b.FI[j] = c->FI[so][j];
+                sdt_row(m, b.Sdt);
+                b.nFI = M;
+                b.dtau = dtau;
+                b.mode = RHS_SWEEP;
+                b.n = c->n;
+                b.pos = c->C.pos;
+                b.fstar_I = c->fst;
+                const cudaGraphNode_t off = bulk(b, c->FI[so][m - 1]);
+                substeps(ii, m, RHS_SWEEP, so, sn, pn);
+                ch.join(off);
+                if (k < K || c->residuals) fi(m, sn);
+            }
         }
     }
     if (c->residuals) residual(K & 1, K);
@@ -1236,6 +1346,8 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
+        {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
+        {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
         {(const void*)k_mx_init, "k_mx_init"},
@@ -1560,8 +1672,17 @@ sdc_status sdc_get_kernel_times(sdc_ctx* c, int32_t capacity, const char** names
     });
 }
 
+sdc_status sdc_set_single_rate(sdc_ctx* c, int on) {
+    return guarded(c, [&] {
+        require(!(on && c->residuals), SDC_ERR_ARG, "single-rate SDC has no residual diagnostics");
+        c->single_rate = on ? 1 : 0;
+        c->graph_ready = false;
+    });
+}
+
 sdc_status sdc_set_diagnostics(sdc_ctx* c, int residuals) {
     return guarded(c, [&] {
+        require(!(residuals && c->single_rate), SDC_ERR_ARG, "single-rate SDC has no residual diagnostics");
         c->residuals = residuals ? 1 : 0;
         c->graph_ready = false;
     });

@@ -312,6 +312,10 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
                 b = r.b_in[i];
             } else if (r.mode == RHS_PRED) {
                 b = m * r.Tprev[i] + a.dtau * r.g[i];
+                if (r.ihat) {  // single-rate SDC: dtau f^E(T_{m-1}, tau_{m-1}) on the contact rows
+                    const int pa = r.pos[i];
+                    if (pa >= 0) b += r.ihat[pa];
+                }
             } else {
                 double I = 0.0;
                 for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
@@ -458,6 +462,10 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
                 b = r.b_in[i];
             } else if (r.mode == RHS_PRED) {
                 b = m * r.Tprev[i] + a.dtau * r.g[i];
+                if (r.ihat) {  // single-rate SDC: dtau f^E(T_{m-1}, tau_{m-1}) on the contact rows
+                    const int pa = r.pos[i];
+                    if (pa >= 0) b += r.ihat[pa];
+                }
             } else {
                 double I = 0.0;
                 for (int j = 0; j < r.nFI; ++j) I = fma(r.Sdt[j], r.FI[j][i], I);
@@ -1170,6 +1178,59 @@ __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const doub
     } else {
         out[C.dof[a]] = apply_coupling(E, slot, C.n_iface, a, Ti);
     }
+}
+
+// ------------------------------------------------------------------ single-rate SDC
+
+// f^E(T, tau) on the contact DOFs at one slot of the step's coupling operator
+// (single-rate SDC evaluates f^E only at the standard nodes, which are the end
+// slots of the intervals). One thread per contact DOF; coupling indices are
+// the substep loop's replica positions, translated back to contact DOFs.
+__global__ void k_sisdc_fe(SisdcArgs a) {
+    const int NI = a.C.n_iface;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NI) return;
+    const size_t so = (size_t)a.slot * NI + i;
+    const int n = a.E.cnt[so];
+    const double Ta = a.T[a.C.dof[i]];
+    double acc = a.E.cst[so];
+    for (int k = 0; k < n; ++k) {
+        const size_t o = ((size_t)a.slot * MAXE + k) * NI + i;
+        const int pos = a.E.idx[o];
+        const int j = pos / a.chunk + a.cs * (pos % a.chunk);
+        const double Tj = a.T[a.C.dof[j]];
+        // mixed precision: zero-sum FP32 rows applied to differences (see k_iface_prep)
+        acc = a.E.coef32 ? fma((double)a.E.coef32[o], Tj - Ta, acc) : fma(a.E.coef[o], Tj, acc);
+    }
+    a.fe_out[i] = acc;
+}
+
+// The contact-row terms of the implicit stage of single-rate SDC (Sec. 3):
+//   predictor: dtau f^E(T_{m-1}, tau_{m-1})
+//   sweep:     dtau (f^E(T^{k+1}_{m-1}) - f^E(T^k_{m-1})) + sum_j dt s_{m,j} f^E(T^k_j, tau_j)
+// (the f^I + g part of the quadrature is added by the solve's RHS).
+__global__ void k_sisdc_rhs(SisdcArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.C.n_iface) return;
+    double v;
+    if (a.mode == RHS_PRED) {
+        v = a.dtau * a.fe_left_new[i];
+    } else {
+        v = a.dtau * (a.fe_left_new[i] - a.fe_left_old[i]);
+        for (int j = 0; j < a.nFE; ++j) v = fma(a.Sdt[j], a.fe_old[j][i], v);
+    }
+    a.ihat[i] = v;
+}
+
+// T_m = the implicit stage's solution on every row; its increment in FP32 for
+// the mixed-precision F^I update (may be NULL).
+__global__ void k_sisdc_endpoint(const double* __restrict__ X, const double* __restrict__ Tprev,
+                                 double* __restrict__ Tout, float* __restrict__ dT, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = X[i];
+    Tout[i] = x;
+    if (dT) dT[i] = (float)(x - Tprev[i]);
 }
 
 // ------------------------------------------------------------------ substep loop

@@ -186,6 +186,26 @@ struct PrepArgs {
     int cs, chunk;
 };
 
+// Single-rate SDC on the contact DOFs: f^E at one slot, and the implicit stage's contact terms.
+struct SisdcArgs {
+    ContactDev C;
+    CouplingOp E;                   // indices are replica positions (see GeomArgs::cs)
+    int cs, chunk;
+    // k_sisdc_fe
+    const double* T;                // [n] temperature at the node
+    int slot;
+    double* fe_out;                 // [NI]
+    // k_sisdc_rhs
+    int mode;                       // RHS_PRED or RHS_SWEEP
+    double dtau;
+    const double* fe_left_new;      // [NI] f^E(T^{k+1}_{m-1}, tau_{m-1})
+    const double* fe_left_old;      // [NI] f^E(T^k_{m-1}, tau_{m-1}) (sweep)
+    const double* fe_old[MAX_M];    // [NI] f^E(T^k_j, tau_j), j = 1..M (sweep)
+    double Sdt[MAX_M];              // dt s_{m,j}
+    int nFE;
+    double* ihat;                   // [NI] output
+};
+
 // Sequential substeps of one interval on the contact DOFs (one cluster).
 struct IfaceArgs {
     ContactDev C;
@@ -231,6 +251,9 @@ struct ResidualArgs {
 // kernels (defined in kernels.cu)
 __global__ void k_apply_operator(EllDev A, const double* mass, double dtau, const double* x, double* y);
 __global__ void k_fi(EllDev A, const double* g, const double* T, double* F, int* step_counts);
+__global__ void k_sisdc_fe(SisdcArgs a);
+__global__ void k_sisdc_rhs(SisdcArgs a);
+__global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* Tout, float* dT, int64_t n);
 __global__ void k_cg_init(CgArgs a, RhsArgs r);
 __global__ void k_cg_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);
