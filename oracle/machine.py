@@ -101,6 +101,29 @@ class MachineProblem:
         q = self.mass * T
         return float(q[: self.n_fix].sum()), float(q[self.n_fix:].sum())
 
+    def fI_matrix(self):
+        """f^I(T) = L_I T with L_I = -K (sparse)."""
+        return -self.K
+
+    def contact_matrix(self, t):
+        """Sparse E and e with f^E(T, t) = E T + e: f^E is affine in T and depends only on
+        the temperatures of the contact nodes, so E is formed column by column from
+        f^E of unit vectors on those nodes."""
+        e = self.fE(np.zeros(self.n), t)
+        nodes = np.unique(np.concatenate([self.fix_quads.ravel(), self.mov_quads.ravel()]))
+        rows, cols, vals = [], [], []
+        for j in nodes:
+            unit = np.zeros(self.n)
+            unit[j] = 1.0
+            col = self.fE(unit, t) - e
+            nz = np.nonzero(col)[0]
+            rows.append(nz)
+            cols.append(np.full(nz.size, j))
+            vals.append(col[nz])
+        E = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.n, self.n))
+        return E, e
+
     def coupling_operator(self, t):
         """Dense matrix E and vector e with f^E(T, t) = E T + e (small problems only)."""
         e = self.fE(np.zeros(self.n), t)

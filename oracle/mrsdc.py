@@ -1,5 +1,6 @@
-"""IMEX multi-rate SDC, Algorithms 1 and 2 taken literally, and single-rate
-semi-implicit SDC (Sec. 3) for comparison (oracle; test infrastructure only).
+"""IMEX multi-rate SDC, Algorithms 1 and 2 taken literally, and for comparison
+single-rate semi-implicit SDC (Sec. 3) and fully implicit Euler with the
+coupling in the matrix (Sec. 1, Sec. 5) (oracle; test infrastructure only).
 
 Problem interface (any object with):
     mass           (N,) diagonal of M (lumped)
@@ -52,6 +53,8 @@ exponential of a <= 200-DOF machine).
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 
 class StepResult:
@@ -209,6 +212,21 @@ def sisdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False):
     if want_residuals:
         res.residuals.append(_residual(prob, T_n, T, quadrature(T)))
     return T[M].copy(), res
+
+
+def implicit_euler_step(prob, T_n, t_n, dt):
+    """One step of fully implicit Euler with the contact coupling in the matrix, the
+    comparison method of Sec. 1 and Sec. 5 (oracle):
+
+        M T_{n+1} = M T_n + dt (f^I(T_{n+1}) + g(t_{n+1}) + f^E(T_{n+1}, t_{n+1})),
+
+    with f^I = L_I T and f^E(T, t) = E(t) T + e(t) affine in T, i.e. the sparse direct
+    solve of (M - dt L_I - dt E(t_{n+1})) T_{n+1} = M T_n + dt (g(t_{n+1}) + e(t_{n+1}))."""
+    t1 = t_n + dt
+    E, e = prob.contact_matrix(t1)
+    A = sp.diags(prob.mass) - dt * prob.fI_matrix() - dt * E
+    rhs = prob.mass * T_n + dt * (prob.g(t1) + e)
+    return spla.spsolve(sp.csc_matrix(A), rhs)
 
 
 def run(prob, T0, t0, dt, W, sweeps, n_steps, callback=None):
