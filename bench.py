@@ -253,6 +253,77 @@ def _stationary_start(m, local, torch):
     return out
 
 
+def _vs_implicit_euler(m, local, torch, args):
+    """Work against accuracy, the comparison of Sec. 5: MRSDC (k = 0..3 sweeps, the
+    scheme's dt, the run's precision), single-rate SDC and fully implicit Euler with the
+    coupling in the matrix (FP64 solve; dt / 1 .. dt / 32) over the same horizon of 8 macro
+    steps from the same start. Error: ||T - T_ref|| / ||T_ref - T0|| at the horizon, T_ref
+    from FP64 MRSDC with dt / 16 and 5 sweeps. eta = horizon / device time of
+    run_horizon (CUDA events on the solver's stream; second run from the same start, so
+    the step graph is built; no L2 flush: consecutive steps, as a look-ahead runs).
+    Implicit Euler is first order: the step it needs for MRSDC's error is extrapolated
+    from its smallest measured step with error proportional to dt, and its eta from
+    that step's cost per step, and both are marked as extrapolated."""
+    import numpy as np
+
+    from paper_1707_03581_gb300 import Solver
+    from synth.machines import with_scheme
+
+    n_macro = 8
+    horizon = n_macro * m.scheme.dt
+
+    def run(mach, precision, stepper, n):
+        s = Solver(local)
+        s.set_machine(mach, precision=precision)
+        if stepper != "mrsdc":
+            s.set_stepper(stepper)
+        s.run_horizon(n)
+        T = s.temperature()
+        s.set_temperature(m.T0 * np.ones(s.n), t0=mach.t0)
+        st = s.stream
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        rep = s.run_horizon(n)
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        T2 = s.temperature()
+        s.close()
+        assert rep["status"] == 0 and np.array_equal(T, T2)
+        return T, ms
+
+    ref_m = with_scheme(m, dt=m.scheme.dt / 16, sweeps=5)
+    T_ref, _ = run(ref_m, "fp64", "mrsdc", 16 * n_macro)
+    rise = np.linalg.norm(T_ref - m.T0)
+
+    def entry(T, ms, dt):
+        return {"dt": dt, "rel_err": float(np.linalg.norm(T - T_ref) / rise), "ms": ms, "eta": horizon / (ms * 1e-3)}
+
+    out = {"workload": f"{m.n_dof}-DOF machine, {n_macro} macro steps of {m.scheme.dt:g} s from {m.T0:g} degC",
+           "reference": "FP64 MRSDC, dt / 16, 5 sweeps", "mrsdc": {}, "implicit_euler": []}
+    for k in range(4):
+        T, ms = run(with_scheme(m, sweeps=k), args.precision, "mrsdc", n_macro)
+        out["mrsdc"][f"k={k}"] = entry(T, ms, m.scheme.dt)
+    T, ms = run(with_scheme(m, P=1), args.precision, "sisdc", n_macro)
+    out["single_rate_sdc"] = entry(T, ms, m.scheme.dt)
+    for r in (1, 2, 4, 8, 16, 32):
+        T, ms = run(with_scheme(m, dt=m.scheme.dt / r), args.precision, "implicit_euler", r * n_macro)
+        out["implicit_euler"].append(entry(T, ms, m.scheme.dt / r))
+    # implicit Euler at the error of MRSDC with the scheme's sweeps (first order in dt)
+    target = out["mrsdc"][f"k={min(m.scheme.sweeps, 3)}"]
+    ie = [e for e in out["implicit_euler"] if e["rel_err"] <= target["rel_err"]]
+    if ie:
+        best = max(ie, key=lambda e: e["eta"])
+        out["ie_at_mrsdc_error"] = {"dt": best["dt"], "eta": best["eta"], "extrapolated": False}
+    else:
+        last = out["implicit_euler"][-1]
+        dt_need = last["dt"] * target["rel_err"] / last["rel_err"]
+        out["ie_at_mrsdc_error"] = {"dt": dt_need, "eta": last["eta"] * dt_need / last["dt"], "extrapolated": True}
+    out["eta_gain_mrsdc_vs_ie_at_equal_error"] = target["eta"] / out["ie_at_mrsdc_error"]["eta"]
+    return out
+
+
 def _single_rate(m, local, torch, args, flush):
     """Single-rate semi-implicit SDC (Sec. 3) on the same machine, nodes, sweeps and dt
     (mixed precision): f^E only at the standard nodes, no substeps. Timed like the
@@ -266,7 +337,7 @@ def _single_rate(m, local, torch, args, flush):
 
     a = Solver(local)
     a.set_machine(with_scheme(m, P=1, window=0), precision=args.precision)
-    a.set_single_rate(True)
+    a.set_stepper("sisdc")
     b = Solver(local)
     b.set_machine(m, precision=args.precision)
     for _ in range(5):
@@ -431,6 +502,8 @@ def run_gpu(args, rank, world):
         line["stationary_start"] = _stationary_start(m, local, torch)
     if not args.no_single_rate:
         line["single_rate"] = _single_rate(m, local, torch, args, flush)
+    if not args.no_ie and world == 1:
+        line["vs_implicit_euler"] = _vs_implicit_euler(m, local, torch, args)
     if not args.no_cpu_baseline and world == 1:
         try:
             import tempfile
@@ -682,6 +755,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single-rate", action="store_true",
                     help="skip the single-rate SDC comparison (Sec. 3) on the same machine")
+    ap.add_argument("--no-ie", action="store_true",
+                    help="skip the comparison with fully implicit Euler (work against accuracy)")
     ap.add_argument("--no-stationary", action="store_true",
                     help="skip the stationary-start measurement (Sec. 5 initial state)")
     ap.add_argument("--eager", action="store_true",

@@ -177,15 +177,21 @@ sdc_status sdc_set_scheme(sdc_ctx* ctx, sdc_nodes nodes, int M, int P, int sweep
  * the predictor and every sweep (costs extra passes). */
 sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
 
-/* Time stepper. 0 (default): IMEX multi-rate SDC (Algorithms 1 and 2). 1:
- * single-rate semi-implicit SDC (Sec. 3, the method MRSDC extends), with f^E
- * only at the standard nodes and in the right-hand side of each interval's
- * implicit stage: the IMEX Euler predictor and Eq. sdc_sweep with
- * I_{m-1}^m = sum_j s_{m,j} F(T^k_j). The scheme's nodes, M, sweeps, dt and
- * solver settings apply; its P only sets how many embedded geometry slots
- * are formed (the end slots give f^E at the standard nodes), so P = 1 is the
- * cheapest. No residual diagnostics (SDC_ERR_ARG with sdc_set_diagnostics). */
-sdc_status sdc_set_single_rate(sdc_ctx* ctx, int on);
+/* Time stepper of sdc_step.
+ * SDC_STEPPER_MRSDC (default): IMEX multi-rate SDC (Algorithms 1 and 2).
+ * SDC_STEPPER_SISDC: single-rate semi-implicit SDC (Sec. 3, the method MRSDC
+ *   extends), with f^E only at the standard nodes and in the right-hand side of
+ *   each interval's implicit stage: the IMEX Euler predictor and Eq. sdc_sweep
+ *   with I_{m-1}^m = sum_j s_{m,j} F(T^k_j). The scheme's nodes, M, sweeps, dt and
+ *   solver settings apply; its P only sets how many embedded geometry slots are
+ *   formed (the end slots give f^E at the standard nodes), so P = 1 is cheapest.
+ * SDC_STEPPER_IMPLICIT_EULER: fully implicit Euler with the contact coupling in
+ *   the matrix (the comparison method of Sec. 1 and Sec. 5): one step of the
+ *   scheme's dt solves (m + dt (K - L_E(t_{n+1}))) T_{n+1} = m T_n + dt (g +
+ *   f^E(0, t_{n+1})) with FP64 Jacobi-PCG, where f^E(T, t) = f^E(0, t) + L_E(t) T.
+ * Residual diagnostics (sdc_set_diagnostics) exist for MRSDC only; SDC_ERR_ARG. */
+enum { SDC_STEPPER_MRSDC = 0, SDC_STEPPER_SISDC = 1, SDC_STEPPER_IMPLICIT_EULER = 2 };
+sdc_status sdc_set_stepper(sdc_ctx* ctx, int stepper);
 
 /* Execution mode. 0 (default): each macro step is one CUDA graph launch with
  * device-side CG loops. 1: the same kernels as plain launches, each CG loop

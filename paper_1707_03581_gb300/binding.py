@@ -66,7 +66,7 @@ _SIGS = {
                                C.c_double, C.c_double, C.c_double]),
     "sdc_set_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_add_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
-    "sdc_set_single_rate": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_stepper": (C.c_int, [_vp, C.c_int]),
     "sdc_set_stationary_state": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
     "sdc_set_contact": (C.c_int, [_vp, _i64p, C.c_int64, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_set_motion": (C.c_int, [_vp, _f64p, C.c_double, C.c_double, C.c_double]),
@@ -266,9 +266,14 @@ class Solver:
         """Force the contact loop's replicas into global memory (True) or choose automatically."""
         self._call("sdc_set_contact_replicas", 1 if global_memory else 0)
 
-    def set_single_rate(self, on: bool):
-        """Single-rate semi-implicit SDC (Sec. 3) instead of MRSDC (sdc_set_single_rate)."""
-        self._call("sdc_set_single_rate", 1 if on else 0)
+    STEPPERS = {"mrsdc": 0, "sisdc": 1, "implicit_euler": 2}
+
+    def set_stepper(self, stepper: str):
+        """Time stepper of step(): "mrsdc" (default), "sisdc" (single-rate semi-implicit
+        SDC, Sec. 3) or "implicit_euler" (coupling in the matrix) (sdc_set_stepper)."""
+        if stepper not in self.STEPPERS:
+            raise ValueError(f"unknown stepper {stepper!r}")
+        self._call("sdc_set_stepper", self.STEPPERS[stepper])
 
     def set_graph_branches(self, on: bool):
         """Run solve-independent kernels beside the implicit solves (True) or in one chain."""

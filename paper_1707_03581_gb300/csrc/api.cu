@@ -95,7 +95,9 @@ struct sdc_ctx {
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
-    int single_rate = 0;            // sdc_set_single_rate
+    int stepper = SDC_STEPPER_MRSDC;  // sdc_set_stepper
+    double* w_slot_ie = nullptr;      // implicit Euler: the unit position of t_{n+1} (one slot)
+    double* ie_coef = nullptr;        // implicit Euler: FP64 coupling rows of that slot
     double* fe_std[2][MAX_M + 1] = {};  // single-rate SDC: f^E at the standard nodes, by iterate
     int in_batch = 0;               // batches holding this context (their members run without side branches)
     void* iface_rep = nullptr;      // their buffers
@@ -482,16 +484,17 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
 }
 
 // init kernel, then WHILE { spmv, update, p-update }
-void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
+void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r, void (*init)(CgArgs, RhsArgs) = k_cg_init,
+               void (*spmv)(CgArgs) = k_cg_spmv) {
     const int unroll = cg_unroll(c);
     if (ch.is_eager) {
         a.handle = 0;
-        ch.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
+        ch.kernel(init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
         eager_cg_loop(
             c, ch,
             [&] {
                 for (int u = 0; u < unroll; ++u) {
-                    ch.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, a);
+                    ch.kernel(spmv, row_grid(c, k_cg_spmv), RED_BLOCK, a);
                     ch.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, a);
                 }
             },
@@ -501,12 +504,12 @@ void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r) {
     cudaGraphConditionalHandle h;
     SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, ch.g, 1u, cudaGraphCondAssignDefault));
     a.handle = (unsigned long long)h;
-    ch.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
+    ch.kernel(init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
     Chain body(ch.while_node(h));
     for (int u = 0; u < unroll; ++u) {
         CgArgs au = a;
         au.tail_pairs = unroll - 1 - u;
-        body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, au);
+        body.kernel(spmv, row_grid(c, k_cg_spmv), RED_BLOCK, au);
         body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, au);
     }
 }
@@ -910,6 +913,8 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     c->E.coef = mixed ? nullptr : dalloc_n<double>(c, c->pool_scheme, slots * MAXE * NI);
     c->E.cst = dalloc_n<double>(c, c->pool_scheme, slots * NI);
     c->E.coef32 = mixed ? dalloc_n<float>(c, c->pool_scheme, slots * MAXE * NI) : nullptr;
+    // implicit Euler forms one slot in FP64 in both precisions (its coupling is in the matrix)
+    c->ie_coef = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)MAXE * NI) : c->E.coef;
     c->fe_base = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)(P + 1) * NI) : nullptr;
     // dt-scaled weights
     std::vector<double> Stil(W.Stil), Semb(W.Semb), Shat(W.Shat), slot_pos(slots);
@@ -923,6 +928,7 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     c->w_Shat = upload(c, c->pool_scheme, Shat);
     c->w_emb = upload(c, c->pool_scheme, W.emb);
     c->w_slot = upload(c, c->pool_scheme, slot_pos);
+    c->w_slot_ie = upload(c, c->pool_scheme, std::vector<double>{1.0});
     SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
 }
 
@@ -941,13 +947,20 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ga.st = c->st;
     ga.use_fixed = 0;
     ga.n_slots = n_int * (P + 1);
+    const bool ie = c->stepper == SDC_STEPPER_IMPLICIT_EULER;
+    if (ie) {  // implicit Euler: the coupling at t_{n+1} only, in FP64
+        ga.slot_pos = c->w_slot_ie;
+        ga.n_slots = 1;
+        ga.E.coef = c->ie_coef;
+        ga.E.coef32 = nullptr;
+    }
     ga.status = &c->st->status;
     ga.cs = c->iface_cluster;
     ga.chunk = c->iface_chunk;
     // side branch: nothing reads the coupling operator before the first interval's
     // k_iface_prep, so it forms while the first implicit solve runs
     const cudaGraphNode_t geom = ch.branch_kernel(
-        {ch.last}, c->precision == SDC_MIXED_FP32 ? k_iface_geom_mx : k_iface_geom,
+        {ch.last}, c->precision == SDC_MIXED_FP32 && !ie ? k_iface_geom_mx : k_iface_geom,
         dim3(blocks_for(NI, GEOM_THREADS), (unsigned)ga.n_slots), dim3(GEOM_THREADS), ga);
 
     // F^I(T_n) + g in FP64 (the only pass over K in FP64 of a mixed-precision step); a
@@ -1074,7 +1087,50 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ch.kernel(k_residual, row_grid(c, k_residual), (unsigned)RED_BLOCK, ra);
     };
 
-    if (c->single_rate) {
+    int ledger_intervals = n_int;
+    if (ie) {
+        // ---- fully implicit Euler with the contact coupling in the matrix (Sec. 1, Sec. 5):
+        // (m + dt (K - L_E(t_{n+1}))) T_{n+1} = m T_n + dt (g + cst(t_{n+1})), FP64 PCG
+        ch.join(geom);
+        const unsigned gi = blocks_for(std::max(NI, 1), 256);
+        SisdcArgs a = {};
+        a.C = c->C;
+        a.E = ga.E;
+        a.cs = c->iface_cluster;
+        a.chunk = c->iface_chunk;
+        a.mode = RHS_PRED;
+        a.dtau = dt;
+        a.fe_left_new = c->E.cst;  // slot 0: dt cst(t_{n+1}) on the contact rows
+        a.ihat = c->ihat[0];
+        ch.kernel(k_sisdc_rhs, gi, 256u, a);
+        RhsArgs r{};
+        r.mode = RHS_PRED;
+        r.Tprev = c->Tn;
+        r.g = c->d_genv;
+        r.x0 = c->Tn;
+        r.pos = c->C.pos;
+        r.ihat = c->ihat[0];
+        CgArgs ca = cg_args(c, dt, 0, c->rtol, c->max_iter);
+        ca.ie.pos = c->C.pos;
+        ca.ie.dof = c->C.dof;
+        ca.ie.E = ga.E;
+        ca.ie.slot = 0;
+        ca.ie.cs = c->iface_cluster;
+        ca.ie.chunk = c->iface_chunk;
+        ca.ie.NI = NI;
+        add_solve(c, ch, ca, r, k_ie_init, k_ie_spmv);
+        ch.copy(c->Tstd[M], c->X, (size_t)c->n * sizeof(double));
+        // the step's contact heat for the ledger: dt f^E(T_{n+1}, t_{n+1})
+        SisdcArgs f = a;
+        f.T = c->X;
+        f.slot = 0;
+        f.fe_out = c->fe_std[0][M];
+        ch.kernel(k_sisdc_fe, gi, 256u, f);
+        a.fe_left_new = c->fe_std[0][M];
+        a.ihat = c->ihat[K & 1];
+        ch.kernel(k_sisdc_rhs, gi, 256u, a);
+        ledger_intervals = 1;
+    } else if (c->stepper == SDC_STEPPER_SISDC) {
         // ---- single-rate semi-implicit SDC (Sec. 3): f^E only at the standard nodes, in the
         // right-hand side of each interval's implicit stage; no substeps
         auto sis = [&]() {
@@ -1250,7 +1306,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     ch.copy(c->Tn, c->Tstd[M], (size_t)c->n * sizeof(double));
     ch.kernel(k_heat, row_grid(c, k_heat), (unsigned)RED_BLOCK, (const double*)c->d_mass, (const double*)c->Tn, (int64_t)c->n,
               (int64_t)c->n_fix, c->partials, c->counter, &c->st->heat[0]);
-    ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], n_int, NI);
+    ch.kernel(k_step_end, 1u, 256u, c->st, (const double*)c->ihat[K & 1], ledger_intervals, NI);
 }
 
 void build_step_graph(sdc_ctx* c) {
@@ -1291,8 +1347,9 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
     const StepState& s = *c->st_host;
     std::memset(rep, 0, sizeof(*rep));
     rep->t = s.t0 + (double)s.n_done * s.dt;
-    rep->sweeps = c->K_sweeps;
-    const int n_solves = (int)c->nondeg.size() * (c->K_sweeps + 1);
+    const bool ie = c->stepper == SDC_STEPPER_IMPLICIT_EULER;
+    rep->sweeps = ie ? 0 : c->K_sweeps;
+    const int n_solves = ie ? 1 : (int)c->nondeg.size() * (c->K_sweeps + 1);
     rep->n_solves = n_solves;
     for (int i = 0; i < n_solves; ++i) {
         rep->cg_iters_total += s.cg_iters[i];
@@ -1347,7 +1404,8 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
         {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
-        {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"},
+        {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"}, {(const void*)k_ie_init, "k_ie_init"},
+        {(const void*)k_ie_spmv, "k_ie_spmv"},
         {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
         {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
         {(const void*)k_mx_init, "k_mx_init"},
@@ -1672,17 +1730,22 @@ sdc_status sdc_get_kernel_times(sdc_ctx* c, int32_t capacity, const char** names
     });
 }
 
-sdc_status sdc_set_single_rate(sdc_ctx* c, int on) {
+sdc_status sdc_set_stepper(sdc_ctx* c, int stepper) {
     return guarded(c, [&] {
-        require(!(on && c->residuals), SDC_ERR_ARG, "single-rate SDC has no residual diagnostics");
-        c->single_rate = on ? 1 : 0;
+        require(stepper == SDC_STEPPER_MRSDC || stepper == SDC_STEPPER_SISDC ||
+                    stepper == SDC_STEPPER_IMPLICIT_EULER,
+                SDC_ERR_ARG, "unknown stepper");
+        require(stepper == SDC_STEPPER_MRSDC || !c->residuals, SDC_ERR_ARG,
+                "residual diagnostics are available with MRSDC only");
+        c->stepper = stepper;
         c->graph_ready = false;
     });
 }
 
 sdc_status sdc_set_diagnostics(sdc_ctx* c, int residuals) {
     return guarded(c, [&] {
-        require(!(residuals && c->single_rate), SDC_ERR_ARG, "single-rate SDC has no residual diagnostics");
+        require(!residuals || c->stepper == SDC_STEPPER_MRSDC, SDC_ERR_ARG,
+                "residual diagnostics are available with MRSDC only");
         c->residuals = residuals ? 1 : 0;
         c->graph_ready = false;
     });

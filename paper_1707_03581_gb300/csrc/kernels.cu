@@ -299,10 +299,31 @@ __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __res
 
 // ------------------------------------------------------------------ Jacobi-PCG
 
+// L_E u on row i for fully implicit Euler: the linear part of the contact term,
+// f^E(u, t) = cst + L_E u, from the step's FP64 coupling rows at one slot
+// (replica positions translated back to contact DOFs); 0 off the contact. The
+// FP64 rows are used in both precisions: L_E is symmetric, so the operator stays SPD.
+__device__ __forceinline__ double ie_contact(const IeOp& o, int64_t i, const double* u) {
+    const int pa = o.pos[i];
+    if (pa < 0) return 0.0;
+    const size_t so = (size_t)o.slot * o.NI + pa;
+    const int n = o.E.cnt[so];
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const size_t off = ((size_t)o.slot * MAXE + k) * o.NI + pa;
+        const int p = o.E.idx[off];
+        const int j = p / o.chunk + o.cs * (p % o.chunk);
+        acc = fma(o.E.coef[off], u[o.dof[j]], acc);
+    }
+    return acc;
+}
+
 // Right-hand side of the implicit stage (Algorithm 1: m T_{m-1} + dtau g;
 // Algorithm 2: m T^{k+1}_{m-1} - dtau f^I(T^k_m) + I_{m-1}^m), the initial
 // residual r = b - (m x0 + dtau K x0), u = D r, and the stop test.
-__global__ void k_cg_init(CgArgs a, RhsArgs r) {
+// IE: the operator is m + dtau (K - L_E(t_{n+1})) (contact coupling in the matrix).
+template <bool IE>
+__device__ __forceinline__ void cg_init_impl(const CgArgs& a, const RhsArgs& r) {
     double v[2] = {0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
@@ -324,7 +345,8 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
                 b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
             }
             const double x0 = r.x0[i];
-            const double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            if constexpr (IE) Kx0 -= ie_contact(a.ie, i, r.x0);
             const double Ax = fma(a.dtau, Kx0, m * x0);
             const double res = b - Ax;
             const double d = 1.0 / (m + a.dtau * a.diagK[i]);
@@ -350,16 +372,23 @@ __global__ void k_cg_init(CgArgs a, RhsArgs r) {
     }
 }
 
-// w = m u + dtau K u; gamma = (r, u), delta = (w, u), rr = (r, r). The last
-// block tests ||r|| <= rtol ||b|| (stop) or sets the step lengths:
+__global__ void k_cg_init(CgArgs a, RhsArgs r) { cg_init_impl<false>(a, r); }
+__global__ void k_ie_init(CgArgs a, RhsArgs r) { cg_init_impl<true>(a, r); }
+
+// w = m u + dtau K u (IE: m u + dtau (K - L_E) u); gamma = (r, u), delta = (w, u),
+// rr = (r, r). The last block tests ||r|| <= rtol ||b|| (stop) or sets the step
+// lengths:
 //   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev).
-__global__ void k_cg_spmv(CgArgs a) {
+template <bool IE>
+__device__ __forceinline__ void cg_spmv_impl(const CgArgs& a) {
     if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     double v[3] = {0.0, 0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
             const double u = a.U[i];
-            const double w = fma(a.dtau, ell_row(a.A, i, a.U), a.mass[i] * u);
+            double Ku = ell_row(a.A, i, a.U);
+            if constexpr (IE) Ku -= ie_contact(a.ie, i, a.U);
+            const double w = fma(a.dtau, Ku, a.mass[i] * u);
             const double res = a.R[i];
             a.W[i] = w;
             v[0] += res * u;
@@ -395,6 +424,9 @@ __global__ void k_cg_spmv(CgArgs a) {
         *a.iters_out = s->iter;
     }
 }
+
+__global__ void k_cg_spmv(CgArgs a) { cg_spmv_impl<false>(a); }
+__global__ void k_ie_spmv(CgArgs a) { cg_spmv_impl<true>(a); }
 
 // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D r
 __global__ void k_cg_update(CgArgs a) {

@@ -21,6 +21,23 @@ enum RhsMode { RHS_GIVEN = 0, RHS_PRED = 1, RHS_SWEEP = 2 };
 // One Jacobi-PCG solve of (diag(m) + dtau K) x = b in the Chronopoulos-Gear
 // arrangement: per iteration one kernel forms w = A u and the three dot
 // products (one global reduction), a second updates the vectors.
+// Precomputed coupling operator f^E(T, tau_s)_a = cst[s][a] + sum_k coef[s][k][a] T_I[idx[s][k][a]].
+struct CouplingOp {
+    int32_t* cnt;     // [slots][NI]
+    int32_t* idx;     // [slots][MAXE][NI]
+    double* coef;     // [slots][MAXE][NI]
+    double* cst;      // [slots][NI]
+    float* coef32;    // [slots][MAXE][NI] FP32 copy (mixed precision), or NULL
+};
+
+// The contact coupling in the matrix of fully implicit Euler (see ie_contact).
+struct IeOp {
+    const int32_t* pos;             // DOF -> contact index or -1
+    const int32_t* dof;             // contact index -> DOF
+    CouplingOp E;                   // the step's coupling rows; indices are replica positions
+    int slot, cs, chunk, NI;
+};
+
 struct CgArgs {
     EllDev A;
     const double* mass;
@@ -39,6 +56,7 @@ struct CgArgs {
     int tail_pairs;                 // (spmv, update) pairs after this one in the graph's loop body
     double rtol2;
     unsigned long long handle;      // cudaGraphConditionalHandle of the enclosing while node
+    IeOp ie;                        // k_ie_init / k_ie_spmv only
 };
 
 // One mixed-precision solve of (diag(m) + dtau K) x = b: FP64 residuals
@@ -135,14 +153,6 @@ struct FiDevArgs {
     int64_t n;
 };
 
-// Precomputed coupling operator f^E(T, tau_s)_a = cst[s][a] + sum_k coef[s][k][a] T_I[idx[s][k][a]].
-struct CouplingOp {
-    int32_t* cnt;     // [slots][NI]
-    int32_t* idx;     // [slots][MAXE][NI]
-    double* coef;     // [slots][MAXE][NI]
-    double* cst;      // [slots][NI]
-    float* coef32;    // [slots][MAXE][NI] FP32 copy (mixed precision), or NULL
-};
 
 struct GeomArgs {
     ContactDev C;
@@ -256,6 +266,8 @@ __global__ void k_sisdc_rhs(SisdcArgs a);
 __global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* Tout, float* dT, int64_t n);
 __global__ void k_cg_init(CgArgs a, RhsArgs r);
 __global__ void k_cg_spmv(CgArgs a);
+__global__ void k_ie_init(CgArgs a, RhsArgs r);
+__global__ void k_ie_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);
 __global__ void k_mx_init(MixArgs a, RhsArgs r);
 __global__ void k_mx_spmv(MixArgs a);

@@ -1,4 +1,4 @@
-"""Single-rate semi-implicit SDC (Sec. 3, sdc_set_single_rate) on the GPU
+"""Single-rate semi-implicit SDC (Sec. 3, sdc_set_stepper) on the GPU
 against oracle.mrsdc.sisdc_step."""
 
 import numpy as np
@@ -26,7 +26,7 @@ def _solver(mach, precision, T0=None):
 
     s = Solver(0)
     s.set_machine(mach, precision=precision, T0=T0)
-    s.set_single_rate(True)
+    s.set_stepper("sisdc")
     return s
 
 
