@@ -254,73 +254,84 @@ def _stationary_start(m, local, torch):
 
 
 def _vs_implicit_euler(m, local, torch, args):
-    """Work against accuracy, the comparison of Sec. 5: MRSDC (k = 0..3 sweeps, the
-    scheme's dt, the run's precision), single-rate SDC and fully implicit Euler with the
-    coupling in the matrix (FP64 solve; dt / 1 .. dt / 32) over the same horizon of 8 macro
-    steps from the same start. Error: ||T - T_ref|| / ||T_ref - T0|| at the horizon, T_ref
-    from FP64 MRSDC with dt / 16 and 5 sweeps. eta = horizon / device time of
-    run_horizon (CUDA events on the solver's stream; second run from the same start, so
-    the step graph is built; no L2 flush: consecutive steps, as a look-ahead runs).
-    Implicit Euler is first order: the step it needs for MRSDC's error is extrapolated
-    from its smallest measured step with error proportional to dt, and its eta from
-    that step's cost per step, and both are marked as extrapolated."""
+    """Work against accuracy, the comparison of Sec. 5: MRSDC (k = 0..3 sweeps at the
+    scheme's dt, and the scheme's sweeps at dt / 2 and dt / 4; the run's precision),
+    single-rate SDC and fully implicit Euler with the coupling in the matrix (FP64 solve;
+    dt / 1 .. dt / 32) over the same horizon of 8 macro steps from the same start. Error:
+    ||T - T_ref|| / ||T_ref - T0|| at the horizon, T_ref from FP64 MRSDC with dt / 64 and
+    the scheme's sweeps (its own error is estimated against dt / 32). eta = horizon /
+    device time of run_horizon (CUDA events on the solver's stream; a second run from the
+    same start, so the step graph exists; no L2 flush: consecutive steps, as a look-ahead
+    runs them). Implicit Euler's eta at MRSDC's error is interpolated log-log between the
+    two implicit Euler runs that bracket it (extrapolated from the last two, and marked,
+    when none reaches it)."""
     import numpy as np
 
     from paper_1707_03581_gb300 import Solver
     from synth.machines import with_scheme
 
     n_macro = 8
-    horizon = n_macro * m.scheme.dt
+    dt0 = m.scheme.dt
+    horizon = n_macro * dt0
 
-    def run(mach, precision, stepper, n):
+    def run(mach, precision, stepper, n, timed=True):
         s = Solver(local)
         s.set_machine(mach, precision=precision)
         if stepper != "mrsdc":
             s.set_stepper(stepper)
-        s.run_horizon(n)
-        T = s.temperature()
-        s.set_temperature(m.T0 * np.ones(s.n), t0=mach.t0)
-        st = s.stream
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        torch.cuda.synchronize()
-        ev[0].record(st)
         rep = s.run_horizon(n)
-        ev[1].record(st)
-        torch.cuda.synchronize()
-        ms = ev[0].elapsed_time(ev[1])
-        T2 = s.temperature()
+        T = s.temperature()
+        ms = None
+        if timed:
+            s.set_temperature(m.T0 * np.ones(s.n), t0=mach.t0)
+            st = s.stream
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record(st)
+            rep = s.run_horizon(n)
+            ev[1].record(st)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            assert np.array_equal(T, s.temperature())
         s.close()
-        assert rep["status"] == 0 and np.array_equal(T, T2)
+        assert rep["status"] == 0
         return T, ms
 
-    ref_m = with_scheme(m, dt=m.scheme.dt / 16, sweeps=5)
-    T_ref, _ = run(ref_m, "fp64", "mrsdc", 16 * n_macro)
+    T_ref, _ = run(with_scheme(m, dt=dt0 / 64), "fp64", "mrsdc", 64 * n_macro, timed=False)
+    T_r32, _ = run(with_scheme(m, dt=dt0 / 32), "fp64", "mrsdc", 32 * n_macro, timed=False)
     rise = np.linalg.norm(T_ref - m.T0)
 
     def entry(T, ms, dt):
         return {"dt": dt, "rel_err": float(np.linalg.norm(T - T_ref) / rise), "ms": ms, "eta": horizon / (ms * 1e-3)}
 
-    out = {"workload": f"{m.n_dof}-DOF machine, {n_macro} macro steps of {m.scheme.dt:g} s from {m.T0:g} degC",
-           "reference": "FP64 MRSDC, dt / 16, 5 sweeps", "mrsdc": {}, "implicit_euler": []}
+    out = {"workload": f"{m.n_dof}-DOF machine, {n_macro} macro steps of {dt0:g} s from {m.T0:g} degC",
+           "reference": f"FP64 MRSDC, dt / 64, {m.scheme.sweeps} sweeps",
+           "reference_rel_err_estimate": float(np.linalg.norm(T_r32 - T_ref) / rise),
+           "mrsdc": {}, "implicit_euler": []}
     for k in range(4):
         T, ms = run(with_scheme(m, sweeps=k), args.precision, "mrsdc", n_macro)
-        out["mrsdc"][f"k={k}"] = entry(T, ms, m.scheme.dt)
+        out["mrsdc"][f"k={k}"] = entry(T, ms, dt0)
+    K = m.scheme.sweeps
+    for r in (2, 4):
+        T, ms = run(with_scheme(m, dt=dt0 / r), args.precision, "mrsdc", r * n_macro)
+        out["mrsdc"][f"k={K},dt/{r}"] = entry(T, ms, dt0 / r)
     T, ms = run(with_scheme(m, P=1), args.precision, "sisdc", n_macro)
-    out["single_rate_sdc"] = entry(T, ms, m.scheme.dt)
+    out["single_rate_sdc"] = entry(T, ms, dt0)
     for r in (1, 2, 4, 8, 16, 32):
-        T, ms = run(with_scheme(m, dt=m.scheme.dt / r), args.precision, "implicit_euler", r * n_macro)
-        out["implicit_euler"].append(entry(T, ms, m.scheme.dt / r))
-    # implicit Euler at the error of MRSDC with the scheme's sweeps (first order in dt)
-    target = out["mrsdc"][f"k={min(m.scheme.sweeps, 3)}"]
-    ie = [e for e in out["implicit_euler"] if e["rel_err"] <= target["rel_err"]]
-    if ie:
-        best = max(ie, key=lambda e: e["eta"])
-        out["ie_at_mrsdc_error"] = {"dt": best["dt"], "eta": best["eta"], "extrapolated": False}
-    else:
-        last = out["implicit_euler"][-1]
-        dt_need = last["dt"] * target["rel_err"] / last["rel_err"]
-        out["ie_at_mrsdc_error"] = {"dt": dt_need, "eta": last["eta"] * dt_need / last["dt"], "extrapolated": True}
-    out["eta_gain_mrsdc_vs_ie_at_equal_error"] = target["eta"] / out["ie_at_mrsdc_error"]["eta"]
+        T, ms = run(with_scheme(m, dt=dt0 / r), args.precision, "implicit_euler", r * n_macro)
+        out["implicit_euler"].append(entry(T, ms, dt0 / r))
+    # implicit Euler at the error of MRSDC with the scheme's sweeps and dt
+    target = out["mrsdc"][f"k={min(K, 3)}"]
+    ie = out["implicit_euler"]
+    e, eta = np.log([x["rel_err"] for x in ie]), np.log([x["eta"] for x in ie])
+    lt = np.log(target["rel_err"])
+    hit = [i for i in range(len(ie) - 1) if e[i] >= lt >= e[i + 1]]
+    i = hit[0] if hit else len(ie) - 2
+    w = (lt - e[i]) / (e[i + 1] - e[i])
+    eta_ie = float(np.exp(eta[i] + w * (eta[i + 1] - eta[i])))
+    out["ie_at_mrsdc_error"] = {"rel_err": target["rel_err"], "eta": eta_ie, "between_dt": [ie[i]["dt"], ie[i + 1]["dt"]],
+                                "extrapolated": not hit}
+    out["eta_gain_mrsdc_vs_ie_at_equal_error"] = target["eta"] / eta_ie
     return out
 
 
@@ -503,7 +514,11 @@ def run_gpu(args, rank, world):
     if not args.no_single_rate:
         line["single_rate"] = _single_rate(m, local, torch, args, flush)
     if not args.no_ie and world == 1:
-        line["vs_implicit_euler"] = _vs_implicit_euler(m, local, torch, args)
+        from synth import machine_config
+
+        small = machine_config(0)
+        line["vs_implicit_euler"] = [_vs_implicit_euler(x, local, torch, args)
+                                     for x in ([m, small] if m.n_dof != small.n_dof else [m])]
     if not args.no_cpu_baseline and world == 1:
         try:
             import tempfile
