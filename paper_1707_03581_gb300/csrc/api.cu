@@ -796,6 +796,13 @@ IfaceKernel iface_loop_kernel(bool mixed, int chunk, bool global) {
     return one ? k_iface_loop1 : k_iface_loop;
 }
 
+// Threads per CTA of that kernel: one warp-rounded thread per DOF of the chunk when
+// it fits the block (no idle warps in the loop's barriers), else the full block.
+int iface_loop_threads(int chunk, bool global) {
+    if (global || chunk > IFACE_THREADS) return IFACE_THREADS;
+    return std::max(32, (chunk + 31) & ~31);
+}
+
 // Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule for the
 // substep loop with room for every contact DOF. A CTA owns `chunk` replica
 // slots (a multiple of 4, so that every chunk is a whole number of 16-byte
@@ -835,19 +842,22 @@ void pick_iface_cluster(sdc_ctx* c) {
     for (int cs = pref; cs <= cs_max; cs *= 2) order.push_back(cs);
     for (int cs = pref / 2; cs >= 1; cs /= 2) order.push_back(cs);
     for (int cs : order) {
-        const int chunk = ((NI + cs - 1) / cs + 3) & ~3;
-        const size_t rep_bytes = 2 * (size_t)cs * chunk * esz;
+        int chunk = ((NI + cs - 1) / cs + 3) & ~3;
+        size_t rep_bytes = 2 * (size_t)cs * chunk * esz;
         bool global;
-        if (!c->force_global && chunk <= IFACE_THREADS * IFACE_PER_THREAD &&
-            rep_bytes <= smem_cap)
+        if (!c->force_global && chunk <= IFACE_THREADS * IFACE_PER_THREAD && rep_bytes <= smem_cap) {
             global = false;
-        else if (chunk <= IFACE_THREADS * IFACE_PER_THREAD_GL) global = true;
-        else continue;
+        } else {
+            chunk = (chunk + 31) & ~31;  // global replicas are owned in 32-DOF tiles
+            rep_bytes = 2 * (size_t)cs * chunk * esz;
+            if (chunk > IFACE_THREADS * IFACE_PER_THREAD_GL) continue;
+            global = true;
+        }
         const size_t smem = global ? 0 : rep_bytes;
         const void* kern = (const void*)iface_loop_kernel(mixed, chunk, global);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cs);
-        cfg.blockDim = dim3(IFACE_THREADS);
+        cfg.blockDim = dim3(iface_loop_threads(chunk, global));
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -955,8 +965,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ga.E.coef32 = nullptr;
     }
     ga.status = &c->st->status;
-    ga.cs = c->iface_cluster;
-    ga.chunk = c->iface_chunk;
     // side branch: nothing reads the coupling operator before the first interval's
     // k_iface_prep, so it forms while the first implicit solve runs
     const cudaGraphNode_t geom = ch.branch_kernel(
@@ -1031,8 +1039,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         pa.E = c->E;
         pa.slot0 = ii * (P + 1);
         pa.Tprev = c->Tstd[m - 1];
-        pa.cs = c->iface_cluster;
-        pa.chunk = c->iface_chunk;
         return ch.branch_kernel(on, k_iface_prep, dim3(blocks_for((int64_t)(P + 1) * NI, 256)), dim3(256u), pa);
     };
     // the cluster loop of interval ii, after the bulk endpoint and the interval's prep
@@ -1063,7 +1069,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.dT = c->precision == SDC_MIXED_FP32 ? c->dTv : nullptr;
         ia.rep_global = c->iface_rep;
         ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global),
-                          (unsigned)c->iface_cluster, (unsigned)IFACE_THREADS, c->iface_smem,
+                          (unsigned)c->iface_cluster, (unsigned)iface_loop_threads(c->iface_chunk, c->iface_global),
+                          c->iface_smem,
                           (unsigned)c->iface_cluster, ia);
     };
     auto residual = [&](int set, int k) {
@@ -1096,8 +1103,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         SisdcArgs a = {};
         a.C = c->C;
         a.E = ga.E;
-        a.cs = c->iface_cluster;
-        a.chunk = c->iface_chunk;
         a.mode = RHS_PRED;
         a.dtau = dt;
         a.fe_left_new = c->E.cst;  // slot 0: dt cst(t_{n+1}) on the contact rows
@@ -1115,8 +1120,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ca.ie.dof = c->C.dof;
         ca.ie.E = ga.E;
         ca.ie.slot = 0;
-        ca.ie.cs = c->iface_cluster;
-        ca.ie.chunk = c->iface_chunk;
         ca.ie.NI = NI;
         add_solve(c, ch, ca, r, k_ie_init, k_ie_spmv);
         ch.copy(c->Tstd[M], c->X, (size_t)c->n * sizeof(double));
@@ -1137,8 +1140,6 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             SisdcArgs a{};
             a.C = c->C;
             a.E = c->E;
-            a.cs = c->iface_cluster;
-            a.chunk = c->iface_chunk;
             return a;
         };
         const unsigned gi = blocks_for(std::max(NI, 1), 256);

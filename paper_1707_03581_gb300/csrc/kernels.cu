@@ -301,8 +301,8 @@ __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __res
 
 // L_E u on row i for fully implicit Euler: the linear part of the contact term,
 // f^E(u, t) = cst + L_E u, from the step's FP64 coupling rows at one slot
-// (replica positions translated back to contact DOFs); 0 off the contact. The
-// FP64 rows are used in both precisions: L_E is symmetric, so the operator stays SPD.
+// (indices are contact DOFs); 0 off the contact. The FP64 rows are used in both
+// precisions: L_E is symmetric, so the operator stays SPD.
 __device__ __forceinline__ double ie_contact(const IeOp& o, int64_t i, const double* u) {
     const int pa = o.pos[i];
     if (pa < 0) return 0.0;
@@ -311,9 +311,7 @@ __device__ __forceinline__ double ie_contact(const IeOp& o, int64_t i, const dou
     double acc = 0.0;
     for (int k = 0; k < n; ++k) {
         const size_t off = ((size_t)o.slot * MAXE + k) * o.NI + pa;
-        const int p = o.E.idx[off];
-        const int j = p / o.chunk + o.cs * (p % o.chunk);
-        acc = fma(o.E.coef[off], u[o.dof[j]], acc);
+        acc = fma(o.E.coef[off], u[o.dof[o.E.idx[off]]], acc);
     }
     return acc;
 }
@@ -1069,7 +1067,7 @@ __device__ __forceinline__ void iface_geom_impl(const GeomArgs& g) {
     for (int k = 0; k < n; ++k) {
         const size_t o = ((size_t)s * MAXE + k) * NI + a;
         const int j = idx[k * GEOM_THREADS];
-        g.E.idx[o] = g.cs ? (j % g.cs) * g.chunk + j / g.cs : j;
+        g.E.idx[o] = j;
         const R cf = coef[k * GEOM_THREADS];
         if (g.E.coef) g.E.coef[o] = (double)cf;
         if (g.E.coef32) g.E.coef32[o] = (float)cf;
@@ -1217,7 +1215,7 @@ __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const doub
 // f^E(T, tau) on the contact DOFs at one slot of the step's coupling operator
 // (single-rate SDC evaluates f^E only at the standard nodes, which are the end
 // slots of the intervals). One thread per contact DOF; coupling indices are
-// the substep loop's replica positions, translated back to contact DOFs.
+// contact DOFs.
 __global__ void k_sisdc_fe(SisdcArgs a) {
     const int NI = a.C.n_iface;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1228,9 +1226,7 @@ __global__ void k_sisdc_fe(SisdcArgs a) {
     double acc = a.E.cst[so];
     for (int k = 0; k < n; ++k) {
         const size_t o = ((size_t)a.slot * MAXE + k) * NI + i;
-        const int pos = a.E.idx[o];
-        const int j = pos / a.chunk + a.cs * (pos % a.chunk);
-        const double Tj = a.T[a.C.dof[j]];
+        const double Tj = a.T[a.C.dof[a.E.idx[o]]];
         // mixed precision: zero-sum FP32 rows applied to differences (see k_iface_prep)
         acc = a.E.coef32 ? fma((double)a.E.coef32[o], Tj - Ta, acc) : fma(a.E.coef[o], Tj, acc);
     }
@@ -1290,8 +1286,7 @@ __global__ void k_iface_prep(PrepArgs a) {
         double acc = a.E.cst[so];
         for (int k = 0; k < n; ++k) {
             const size_t o = ((size_t)slot * MAXE + k) * NI + i;
-            const int pos = a.E.idx[o];
-            const int j = pos / a.chunk + a.cs * (pos % a.chunk);  // replica position -> contact DOF
+            const int j = a.E.idx[o];
             acc = fma((double)a.E.coef32[o], a.Tprev[a.C.dof[j]] - Ta, acc);
         }
         a.base[(size_t)p * NI + i] = acc;
@@ -1332,10 +1327,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 //   m T_{m,p} = m T_{m,p-1} + c_p + dt_p f^E(T_{m,p-1}, tau_{m,p-1})
 // with c_p from k_iface_prep, on one cluster of CTAs. Every CTA keeps both
 // buffers of a full replica of the contact temperatures in shared memory,
-// chunk-major: CTA r owns the DOFs r, r + cs, r + 2 cs, ... (interleaved, so
-// that the DOFs under the moving stock spread over all CTAs) and stores them
-// contiguously as chunk r. After a substep's update, one thread pushes the
-// own chunk into every other CTA's replica with a bulk shared-memory copy
+// indexed by contact DOF: CTA r owns the contiguous chunk of DOFs
+// [r chunk, (r + 1) chunk), so that the loop's per-DOF loads (coupling rows,
+// c_p, f*) are coalesced. After a substep's update, lane q of the first warp
+// pushes the own chunk into CTA q's replica with a bulk shared-memory copy
 // across the cluster that completes a byte count on the receiver's mbarrier;
 // waiting for all incoming bytes publishes the substep, so no cluster barrier
 // is needed inside the loop. A CTA overwrites a buffer only after it has
@@ -1365,27 +1360,41 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     // [2][cs * chunk]: shared memory, or (GL) global memory for interfaces whose replicas do not
     // fit in shared memory; then owners store their chunk and a cluster barrier publishes it
     V* rep = GL ? (V*)a.rep_global : reinterpret_cast<V*>(dyn);
-    const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+    const int nthr = (int)blockDim.x;
+    // the substep lengths and quadrature weights, formed once (FP64 runs at a small
+    // fraction of the FP32 rate, so no thread repeats this work inside the loop)
+    __shared__ double s_dtp[MAX_P + 1], s_shat[MAX_P + 1];
+    for (int q = threadIdx.x; q < P; q += nthr) {
+        const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+        s_dtp[q + 1] = substep_dt(a, tn, q + 1);
+        s_shat[q + 1] = a.Shat[q];
+    }
 
-    int own[PER], slot[PER];
+    // Replica position = contact DOF. Shared replicas: CTA r owns the contiguous chunk
+    // [r chunk, (r + 1) chunk), which one bulk copy a peer sends. Global replicas (no copies):
+    // CTA r owns the 32-DOF tiles r, r + cs, r + 2 cs, ..., so that the DOFs under the
+    // moving stock, whose coupling rows are long, spread over all CTAs (chunk is a
+    // multiple of 32 there).
+    auto owned = [&](int sl) { return GL ? (((sl >> 5) * cs + rank) << 5) + (sl & 31) : rank * chunk + sl; };
+    int own[PER];
     double T[PER], T0[PER], fe[PER], mi[PER],
-        ih[PER], cn[PER], bn[PER];
+        ih[PER], cn[PER], bn[PER], fs[PER];
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        slot[r] = (int)threadIdx.x + IFACE_THREADS * r;
-        const int i = rank + cs * slot[r];
-        own[r] = (slot[r] < chunk && i < NI) ? i : -1;
+        const int sl = (int)threadIdx.x + nthr * r;
+        const int i = owned(sl);
+        own[r] = (sl < chunk && i < NI) ? i : -1;
         ih[r] = 0.0;
     }
     // buffer 0 = the replica at tau_{m,0}: T_{m-1} (FP64) or zero deviations (mixed)
     if constexpr (GL) {
-        for (int sl = threadIdx.x; sl < chunk; sl += IFACE_THREADS) {
-            const int j = rank + cs * sl;
-            rep[rank * chunk + sl] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
+        for (int sl = threadIdx.x; sl < chunk; sl += nthr) {
+            const int j = owned(sl);
+            rep[j] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
         }
     } else {
-        for (int pos = threadIdx.x; pos < cs * chunk; pos += IFACE_THREADS) {
-            const int j = pos / chunk + cs * (pos % chunk);
+        for (int pos = threadIdx.x; pos < cs * chunk; pos += nthr) {
+            const int j = pos;
             rep[pos] = MIX ? V(0) : (j < NI ? (V)a.Tprev[C.dof[j]] : V(0));
         }
     }
@@ -1418,6 +1427,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         fe[r] = f0;
         a.fe_new[i] = f0;
         cn[r] = a.mode == RHS_PRED ? 0.0 : a.cpre[i];
+        fs[r] = a.fstar[i];  // f*_m is fixed over the interval
         if constexpr (MIX) bn[r] = a.base[(size_t)NI + i];
     }
     unsigned phase[2] = {0u, 0u};
@@ -1426,7 +1436,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     for (int p = 1; p <= P; ++p) {
         const int b = p & 1;
         V* buf = rep + (size_t)b * cs * chunk;
-        const double dtp = substep_dt(a, tn, p);
+        const double dtp = s_dtp[p];
         typename std::conditional<MIX, CouplingRow32T<B>, CouplingRowT<B>>::type row[PER];
         double bp[PER];
 #pragma unroll
@@ -1435,14 +1445,14 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             if (i < 0) continue;
             if constexpr (MIX) coupling_prefetch32(a.E, a.slot0 + p, NI, i, row[r]);
             else coupling_prefetch(a.E, a.slot0 + p, NI, i, row[r]);
-            const double cp = fma(dtp, __ldg(a.fstar + i), cn[r]);  // c_p (Algorithms 1 and 2)
+            const double cp = fma(dtp, fs[r], cn[r]);  // c_p (Algorithms 1 and 2)
             bp[r] = bn[r];
             if (p < P) {  // inputs of the next substep, loaded one substep ahead
                 cn[r] = a.mode == RHS_PRED ? 0.0 : a.cpre[(size_t)p * NI + i];
                 if constexpr (MIX) bn[r] = a.base[(size_t)(p + 1) * NI + i];
             }
             T[r] = fma(fma(dtp, fe[r], cp), mi[r], T[r]);
-            buf[rank * chunk + slot[r]] = MIX ? (V)(T[r] - T0[r]) : (V)T[r];
+            buf[i] = MIX ? (V)(T[r] - T0[r]) : (V)T[r];
         }
         if constexpr (GL) {
             cluster.sync();  // the chunks of this substep are in global memory
@@ -1450,11 +1460,11 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         // generic-proxy writes of the own chunk become visible to the bulk copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < (unsigned)cs) {  // lane q sends the own chunk to CTA q, all at once
+            const int q = (int)threadIdx.x;
             const unsigned src = smem_addr(buf + rank * chunk);
             const unsigned bar = smem_addr(&mbar[b]);
-            for (int q = 0; q < cs; ++q) {
-                if (q == rank) continue;
+            if (q != rank) {
                 unsigned dst, rbar;
                 asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(src), "r"(q));
                 asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(bar), "r"(q));
@@ -1463,8 +1473,9 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
                     "r"(src), "r"(bytes), "r"(rbar)
                     : "memory");
             }
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes * (cs - 1))
-                         : "memory");
+            if (q == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes * (cs - 1))
+                             : "memory");
         }
         if (!timed_out && !mbar_wait(smem_addr(&mbar[b]), phase[b])) timed_out = true;
         phase[b] ^= 1u;
@@ -1476,7 +1487,7 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
             else fe[r] = coupling_apply_shared<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
             a.fe_new[(size_t)p * NI + i] = fe[r];
-            ih[r] = fma(a.Shat[p - 1], fe[r], ih[r]);
+            ih[r] = fma(s_shat[p], fe[r], ih[r]);
         }
     }
     if (timed_out) atomicExch(a.status, (int)SDC_ERR_TIMEOUT);

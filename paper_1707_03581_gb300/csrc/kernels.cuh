@@ -34,8 +34,8 @@ struct CouplingOp {
 struct IeOp {
     const int32_t* pos;             // DOF -> contact index or -1
     const int32_t* dof;             // contact index -> DOF
-    CouplingOp E;                   // the step's coupling rows; indices are replica positions
-    int slot, cs, chunk, NI;
+    CouplingOp E;                   // the step's coupling rows; indices are contact-DOF ids
+    int slot, NI;
 };
 
 struct CgArgs {
@@ -163,9 +163,6 @@ struct GeomArgs {
     int use_fixed;
     int n_slots;
     int* status;
-    // 0: coupling indices are contact-DOF ids; else replica positions of the substep loop
-    // for a cluster of `cs` CTAs with `chunk` slots each (DOF j -> (j % cs) * chunk + j / cs)
-    int cs, chunk;
 };
 
 // T-independent part of every substep increment of one interval
@@ -190,17 +187,15 @@ struct PrepArgs {
     // mixed precision: base_q = f^E(T_{m-1}, tau_{m,q}) for q = 0..P (output), from
     // the interval's slots of the coupling operator and T_{m-1} = Tprev
     double* base;                   // [(P+1)][NI] or NULL
-    CouplingOp E;                   // indices are replica positions (see GeomArgs::cs)
+    CouplingOp E;                   // indices are contact-DOF ids
     int slot0;
     const double* Tprev;
-    int cs, chunk;
 };
 
 // Single-rate SDC on the contact DOFs: f^E at one slot, and the implicit stage's contact terms.
 struct SisdcArgs {
     ContactDev C;
-    CouplingOp E;                   // indices are replica positions (see GeomArgs::cs)
-    int cs, chunk;
+    CouplingOp E;                   // indices are contact-DOF ids
     // k_sisdc_fe
     const double* T;                // [n] temperature at the node
     int slot;
