@@ -214,6 +214,14 @@ sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
  * identical. */
 sdc_status sdc_set_graph_branches(sdc_ctx* ctx, int on);
 
+/* (SpMV, update) pairs in each body of the CG loops (the WHILE nodes of the step
+ * graph, and the host-driven loop of eager execution), 1..8; 0 (default) = 3 on
+ * grids of at most 2048 blocks of 256 rows, else 1. A body runs to its end after
+ * the solve stops (its remaining launches return at once), so more pairs trade
+ * loop iterations for such launches. Results are identical; SDC_ERR_ARG out of
+ * range. */
+sdc_status sdc_set_cg_unroll(sdc_ctx* ctx, int pairs);
+
 /* Upper bound on the CTAs of the contact substep loop's thread-block cluster
  * (1..16; 0 = automatic). The loop takes the largest power of two within the
  * bound whose cluster fits on the device. For tuning and tests: results are

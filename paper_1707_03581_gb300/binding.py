@@ -67,6 +67,7 @@ _SIGS = {
     "sdc_set_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_add_robin": (C.c_int, [_vp, C.c_int, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_set_stepper": (C.c_int, [_vp, C.c_int]),
+    "sdc_set_cg_unroll": (C.c_int, [_vp, C.c_int]),
     "sdc_set_stationary_state": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
     "sdc_set_contact": (C.c_int, [_vp, _i64p, C.c_int64, _i64p, C.c_int64, C.c_double, C.c_double]),
     "sdc_set_motion": (C.c_int, [_vp, _f64p, C.c_double, C.c_double, C.c_double]),
@@ -274,6 +275,10 @@ class Solver:
         if stepper not in self.STEPPERS:
             raise ValueError(f"unknown stepper {stepper!r}")
         self._call("sdc_set_stepper", self.STEPPERS[stepper])
+
+    def set_cg_unroll(self, pairs: int):
+        """(SpMV, update) pairs per CG loop body, 1..8; 0 = by grid size (sdc_set_cg_unroll)."""
+        self._call("sdc_set_cg_unroll", int(pairs))
 
     def set_graph_branches(self, on: bool):
         """Run solve-independent kernels beside the implicit solves (True) or in one chain."""

@@ -96,6 +96,7 @@ struct sdc_ctx {
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
     int stepper = SDC_STEPPER_MRSDC;  // sdc_set_stepper
+    int cg_unroll = 0;                // sdc_set_cg_unroll (0: by grid size)
     double* w_slot_ie = nullptr;      // implicit Euler: the unit position of t_{n+1} (one slot)
     double* ie_coef = nullptr;        // implicit Euler: FP64 coupling rows of that slot
     double* fe_std[2][MAX_M + 1] = {};  // single-rate SDC: f^E at the standard nodes, by iterate
@@ -433,7 +434,11 @@ void eager_cg_loop(sdc_ctx* c, Chain& ch, Iter iteration, int pairs) {
 // body of one. A solve that stops early in a body leaves the body's later
 // pairs to return at once, which costs more than it saves on grids of many
 // blocks (5.75M DOF: 22k blocks a launch), so large grids keep one pair.
+// (SpMV, update) pairs per body of a CG WHILE loop: more pairs cost fewer loop
+// iterations (conditional-node evaluations) and more launches that find the solve
+// stopped; sdc_set_cg_unroll overrides the default
 int cg_unroll(sdc_ctx* c) {
+    if (c->cg_unroll > 0) return c->cg_unroll;
     return blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS ? 3 : 1;
 }
 
@@ -1687,6 +1692,14 @@ sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
     return guarded(c, [&] {
         c->force_global = global ? 1 : 0;
         c->buffers_ready = false;
+        c->graph_ready = false;
+    });
+}
+
+sdc_status sdc_set_cg_unroll(sdc_ctx* c, int pairs) {
+    return guarded(c, [&] {
+        require(pairs >= 0 && pairs <= 8, SDC_ERR_ARG, "CG loop pairs out of range [0, 8]");
+        c->cg_unroll = pairs;
         c->graph_ready = false;
     });
 }

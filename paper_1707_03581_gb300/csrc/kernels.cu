@@ -661,21 +661,28 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
         prev[1] = s->alpha;
         prev[2] = s->bb;
     }
-    // the first row's operands are loaded before the dot sums and the step
-    // lengths, so that their latency overlaps that chain; not by a thread that
-    // already sees the stop flag (set by an earlier kernel, or by this one's block
-    // 0 when it stops the solve, in which case no block updates rows)
+    // the operands of the thread's first MX_UPDATE_ROWS rows are loaded before the dot
+    // sums and the step lengths, so that their latency overlaps that chain; not by a
+    // thread that already sees the stop flag (set by an earlier kernel, or by this
+    // one's block 0 when it stops the solve, in which case no block updates rows)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float u0 = 0.0f, w0 = 0.0f, p0 = 0.0f, s0 = 0.0f, d0 = 0.0f, r0 = 0.0f, q0 = 0.0f;
-    if (i0 < a.n && !s->done) {
-        u0 = a.Ul[i0];
-        w0 = a.Wl[i0];
-        p0 = a.Pl[i0];
-        s0 = a.Sl[i0];
-        d0 = a.Dl[i0];
-        r0 = a.Rl[i0];
-        q0 = a.Dinv[i0];
+    float u0[MX_UPDATE_ROWS], w0[MX_UPDATE_ROWS], p0[MX_UPDATE_ROWS], s0[MX_UPDATE_ROWS], d0[MX_UPDATE_ROWS],
+        r0[MX_UPDATE_ROWS], q0[MX_UPDATE_ROWS];
+    const bool live = !s->done;
+#pragma unroll
+    for (int k = 0; k < MX_UPDATE_ROWS; ++k) {
+        const int64_t i = i0 + k * stride;
+        u0[k] = w0[k] = p0[k] = s0[k] = d0[k] = r0[k] = q0[k] = 0.0f;
+        if (i < a.n && live) {
+            u0[k] = a.Ul[i];
+            w0[k] = a.Wl[i];
+            p0[k] = a.Pl[i];
+            s0[k] = a.Sl[i];
+            d0[k] = a.Dl[i];
+            r0[k] = a.Rl[i];
+            q0[k] = a.Dinv[i];
+        }
     }
     __syncthreads();
     if (skip) {
@@ -727,17 +734,21 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     }
     const float alpha = step[0], beta = step[1];
     const bool first = iter == 0;
-    if (i0 < a.n) {
-        const float p = first ? u0 : fmaf(beta, p0, u0);
-        const float sp = first ? w0 : fmaf(beta, s0, w0);
-        a.Pl[i0] = p;
-        a.Sl[i0] = sp;
-        a.Dl[i0] = first ? alpha * p : fmaf(alpha, p, d0);
-        const float res = fmaf(-alpha, sp, r0);
-        a.Rl[i0] = res;
-        a.Ul[i0] = res * q0;
+#pragma unroll
+    for (int k = 0; k < MX_UPDATE_ROWS; ++k) {
+        const int64_t i = i0 + k * stride;
+        if (i < a.n) {
+            const float p = first ? u0[k] : fmaf(beta, p0[k], u0[k]);
+            const float sp = first ? w0[k] : fmaf(beta, s0[k], w0[k]);
+            a.Pl[i] = p;
+            a.Sl[i] = sp;
+            a.Dl[i] = first ? alpha * p : fmaf(alpha, p, d0[k]);
+            const float res = fmaf(-alpha, sp, r0[k]);
+            a.Rl[i] = res;
+            a.Ul[i] = res * q0[k];
+        }
     }
-    for (int64_t i = i0 + stride; i < a.n; i += stride) mx_update_row(a, i, alpha, beta, first);
+    for (int64_t i = i0 + MX_UPDATE_ROWS * stride; i < a.n; i += stride) mx_update_row(a, i, alpha, beta, first);
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 6) k_mx_spmv_red(MixArgs a) {

@@ -64,6 +64,7 @@ struct CgArgs {
 // Largest grid of the FP32 SpMV whose dot partials every block of the update
 // sums itself (above it: last-block reduction in the SpMV).
 constexpr int MIX_DEFER_MAX_BLOCKS = 2048;
+constexpr int MX_UPDATE_ROWS = 2;       // rows a thread of k_mx_update loads before the dot sums
 
 struct MixArgs {
     EllDev A;                       // val (FP64) for residuals, val32 for the inner solves

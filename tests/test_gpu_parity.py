@@ -367,6 +367,31 @@ def test_graph_side_branches_equal_one_chain(torch, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cg_loop_pairs_are_bitwise_equal(torch, precision):
+    # 1, 2, 5 and the default 3 (SpMV, update) pairs per CG loop body, graph and eager
+    mach = machine_config(0)
+    ref = None
+    for pairs, eager in ((0, False), (1, False), (2, True), (5, False), (5, True)):
+        s = _solver(mach, precision=precision)
+        s.set_cg_unroll(pairs)
+        s.set_execution(eager)
+        for _ in range(3):
+            rep = s.step(report=True)
+        T = s.temperature()
+        if ref is None:
+            ref, iters = T, rep["cg_iters_total"]
+        assert np.array_equal(T, ref), (pairs, eager)
+        assert rep["cg_iters_total"] == iters
+        s.close()
+    from paper_1707_03581_gb300 import SdcError
+
+    s = _solver(mach, precision=precision)
+    with pytest.raises(SdcError):
+        s.set_cg_unroll(9)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_contact_cluster_sizes_are_bitwise_equal(torch, precision):
     # the automatic size and forced 16-, 2- and 1-CTA clusters of the substep loop
     mach = machine_config(0)
