@@ -808,11 +808,12 @@ int iface_loop_threads(int chunk, bool global) {
     return std::max(32, (chunk + 31) & ~31);
 }
 
-// Largest cluster (16, 8, 4, 2 or 1 CTAs) the device can co-schedule for the
-// substep loop with room for every contact DOF. A CTA owns `chunk` replica
-// slots (a multiple of 4, so that every chunk is a whole number of 16-byte
-// units for the bulk copies); the replicas live in shared memory when both
-// buffers fit, else in global memory.
+// Cluster (16, 8, 4, 2 or 1 CTAs) of the substep loop: the preferred size below,
+// else the first other size the device can co-schedule with room for every
+// contact DOF. A CTA owns `chunk` replica slots: a multiple of 4 when the replicas
+// live in shared memory (every chunk a whole number of 16-byte units for the bulk
+// copies), of 32 in global memory (32-DOF tiles); shared memory when both buffers
+// fit, else global memory.
 void pick_iface_cluster(sdc_ctx* c) {
     const int NI = std::max(c->C.n_iface, 1);
     const bool mixed = c->precision == SDC_MIXED_FP32;
