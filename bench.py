@@ -340,17 +340,25 @@ def _vs_implicit_euler(m, local, torch, args):
         out["implicit_euler"].append(entry(T, ms, dt0 / r))
     # implicit Euler at the error of MRSDC with the scheme's sweeps and dt
     target = out["mrsdc"][f"k={min(K, 3)}"]
-    ie = out["implicit_euler"]
-    e, eta = np.log([x["rel_err"] for x in ie]), np.log([x["eta"] for x in ie])
-    lt = np.log(target["rel_err"])
-    hit = [i for i in range(len(ie) - 1) if e[i] >= lt >= e[i + 1]]
-    i = hit[0] if hit else len(ie) - 2
-    w = (lt - e[i]) / (e[i + 1] - e[i])
-    eta_ie = float(np.exp(eta[i] + w * (eta[i + 1] - eta[i])))
-    out["ie_at_mrsdc_error"] = {"rel_err": target["rel_err"], "eta": eta_ie, "between_dt": [ie[i]["dt"], ie[i + 1]["dt"]],
-                                "extrapolated": not hit}
-    out["eta_gain_mrsdc_vs_ie_at_equal_error"] = target["eta"] / eta_ie
+    out["ie_at_mrsdc_error"] = _eta_at_error(out["implicit_euler"], target["rel_err"])
+    out["eta_gain_mrsdc_vs_ie_at_equal_error"] = target["eta"] / out["ie_at_mrsdc_error"]["eta"]
     return out
+
+
+def _eta_at_error(runs, err):
+    """eta of a method at error `err`, from its runs ({"dt", "rel_err", "eta"}, step sizes
+    falling): log eta linear in log error between the first two consecutive runs that
+    bracket `err`, else extrapolated from the last two runs (marked)."""
+    import numpy as np
+
+    e = np.log([x["rel_err"] for x in runs])
+    eta = np.log([x["eta"] for x in runs])
+    lt = np.log(err)
+    hit = [i for i in range(len(runs) - 1) if e[i] >= lt >= e[i + 1]]
+    i = hit[0] if hit else len(runs) - 2
+    w = (lt - e[i]) / (e[i + 1] - e[i])
+    return {"rel_err": float(err), "eta": float(np.exp(eta[i] + w * (eta[i + 1] - eta[i]))),
+            "between_dt": [runs[i]["dt"], runs[i + 1]["dt"]], "extrapolated": not hit}
 
 
 def _single_rate(m, local, torch, args, flush):

@@ -65,3 +65,22 @@ def test_contact_matrix_reproduces_fE_and_heat_is_conserved():
     for n in range(3):
         T = implicit_euler_step(prob, T, 0.6 + 0.5 * n, 0.5)
     assert abs(prob.mass @ T - heat0) <= 1e-12 * abs(heat0)
+
+
+def test_coupling_is_symmetric_and_negative_semidefinite():
+    # Reading of the implicit Euler operator: L_E(t) is symmetric (both bodies' exchange uses one
+    # overlap quadrature) and negative semidefinite (it only exchanges heat), so that
+    # m + dt (K - L_E) is SPD and Jacobi-PCG applies. Checked at several stroke positions.
+    mach = tiny_machine(z0=0.37, amp=0.21, period=1.7)
+    prob = MachineProblem(mach)
+    for t in (0.0, 0.3, 0.9, 1.4):
+        E, _ = prob.contact_matrix(t)
+        Ed = E.toarray()
+        assert np.abs(Ed - Ed.T).max() <= 1e-12 * np.abs(Ed).max()
+        assert np.abs(Ed).max() > 0.0
+        lam = np.linalg.eigvalsh(0.5 * (Ed + Ed.T))
+        assert lam.max() <= 1e-10 * np.abs(lam).max()
+        # rows sum to zero: a uniform temperature exchanges no heat
+        np.testing.assert_allclose(Ed.sum(axis=1), 0.0, atol=1e-10 * np.abs(Ed).max())
+        A = np.diag(prob.mass) - 5.0 * prob.fI_matrix().toarray() - 5.0 * Ed
+        assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0.0
