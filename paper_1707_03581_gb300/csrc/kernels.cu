@@ -331,7 +331,8 @@ __device__ __forceinline__ void cg_init_impl(const CgArgs& a, const RhsArgs& r) 
                 b = r.b_in[i];
             } else if (r.mode == RHS_PRED) {
                 b = m * r.Tprev[i] + a.dtau * r.g[i];
-                if (r.ihat) {  // single-rate SDC: dtau f^E(T_{m-1}, tau_{m-1}) on the contact rows
+                if (r.ihat) {  // contact rows: dtau f^E(T_{m-1}, tau_{m-1}) (single-rate SDC) or
+                               // dt f^E(0, t_{n+1}) (implicit Euler)
                     const int pa = r.pos[i];
                     if (pa >= 0) b += r.ihat[pa];
                 }
@@ -492,7 +493,8 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
                 b = r.b_in[i];
             } else if (r.mode == RHS_PRED) {
                 b = m * r.Tprev[i] + a.dtau * r.g[i];
-                if (r.ihat) {  // single-rate SDC: dtau f^E(T_{m-1}, tau_{m-1}) on the contact rows
+                if (r.ihat) {  // contact rows: dtau f^E(T_{m-1}, tau_{m-1}) (single-rate SDC) or
+                               // dt f^E(0, t_{n+1}) (implicit Euler)
                     const int pa = r.pos[i];
                     if (pa >= 0) b += r.ihat[pa];
                 }

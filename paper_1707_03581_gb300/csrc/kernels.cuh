@@ -105,7 +105,9 @@ struct RhsArgs {
     const double* FI[MAX_M];        // F^I(T^k_j), j = 1..M (sweep)
     double Sdt[MAX_M];              // dt s_{m,j}
     int nFI;
-    const double* ihat;             // sum_q dt shat_{m,q} f^E(T^k_{m,q}) on contact DOFs (sweep)
+    // contact-DOF term of the right-hand side, or NULL: sweep: sum_q dt shat_{m,q}
+    // f^E(T^k_{m,q}); predictor: single-rate SDC's or implicit Euler's f^E part
+    const double* ihat;
     const int32_t* pos;             // DOF -> contact index or -1
     const double* x0;               // initial guess
     // F^I(x0) + g if known (NULL: form m x0 + dtau K x0 with an SpMV). Then
