@@ -330,6 +330,28 @@ def test_mixed_large_grid_matches_fp64(torch):
     b.close()
 
 
+def test_config2_full_size_mixed_matches_fp64(torch):
+    # The 5,751,586-DOF machine (128x128x320 + 64x64x96, per-hex conductivity, Radau M=4,
+    # 4 sweeps, P=40), in the launch configuration bench.py times. The oracle cannot take
+    # a step of it; the FP64 path is the oracle-pinned one (smaller machines above), and
+    # the mixed path must stay within the 1e-6 bar of it on the full size, with the large-grid
+    # FP32 CG and the global-replica contact loop that only this size uses.
+    mach = machine_config(2)
+    a = _solver(mach, precision="mixed")
+    b = _solver(mach, precision="fp64")
+    ra = a.step(report=True)
+    rb = b.step(report=True)
+    assert ra["status"] == 0 and rb["status"] == 0
+    Ta, Tb = a.temperature(), b.temperature()
+    assert np.all(np.isfinite(Ta))
+    assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb) <= 1e-9
+    assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb - mach.T0) <= REL_MIXED
+    # the contact heats the bodies: the step is not trivial
+    assert np.linalg.norm(Tb - mach.T0) > 0.0
+    a.close()
+    b.close()
+
+
 def test_mixed_eager_kernel_timing_counts_every_launch(torch):
     mach = machine_config(0)
     s = _solver(mach, precision="mixed")
