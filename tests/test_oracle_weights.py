@@ -8,6 +8,7 @@ exactness on polynomials.
 
 from fractions import Fraction as F
 import math
+import os
 
 import mpmath as mp
 import numpy as np
@@ -148,3 +149,26 @@ def test_float_tables_round_high_precision_values():
     assert W["S"][2, 1] == float(t["S"][2][1])
     assert W["Semb"][3, 7, 6] == float(t["Semb"][3][7][6])
     assert isinstance(t["S"][2][1], mp.mpf)
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return [line.split() for line in f if line.strip() and not line.startswith("#")]
+
+
+def test_node_layout_of_the_sec3_figure():
+    # tests/golden/nodes_equi_noleft_M4_P3.txt: the M = 4, P = 3 layout of the node figure of Sec. 3
+    t = wt.mrsdc_tables("equi_noleft", 4, 3, exact=True)
+    rows = _golden("nodes_equi_noleft_M4_P3.txt")
+    for kind, m, p, pos in rows:
+        want = F(pos)
+        if kind == "standard":
+            assert t["c"][int(m)] == want, (m, t["c"][int(m)], want)
+        else:
+            assert t["emb"][int(m) - 1][int(p)] == want, (m, p)
+    assert len([r for r in rows if r[0] == "embedded"]) == 4 * 3
+    # t_n (0) is no standard node, and each interval's embedded set ends on its standard node
+    assert F(0) not in t["c"][1:]
+    assert all(t["emb"][m][3] == t["c"][m + 1] for m in range(4))
+
