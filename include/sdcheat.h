@@ -305,6 +305,19 @@ sdc_status sdc_batch_synchronize(sdc_batch* batch);
 /* Device bytes the context holds (assembled system, state and scheme buffers). */
 sdc_status sdc_get_footprint(const sdc_ctx* ctx, int64_t* bytes);
 
+/* The MRSDC weight tables of a scheme on the unit step (Sec. 3: the standard-node weights
+ * s_{m,j}, the embedded ones of Table 1 and the node positions), as sdc_set_scheme forms
+ * them. Host only: no context and no device. Each output may be NULL; otherwise it is a
+ * host array of float64, row-major, the caller's:
+ *   c    [M+1]       node positions, c[0] = 0 (t_n), c[m] = tau_m;
+ *   emb  [M][P+1]    embedded positions tau_{m,p} of interval m (p = 0 is tau_{m-1});
+ *   S    [M][M]      s_{m,j};     Shat [M][P]     shat_{m,q};
+ *   Stil [M][P][M]   stil_{m,p,j}; Semb [M][P][P] s_{m,p,q}
+ * (interval, embedded and node indices from 0). window 0 = min(M, P). SDC_ERR_ARG for
+ * arguments sdc_set_scheme refuses. */
+sdc_status sdc_scheme_weights(sdc_nodes nodes, int M, int P, int window, double* c, double* emb, double* S,
+                              double* Shat, double* Stil, double* Semb);
+
 /* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
 sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,
                          int64_t* n_contact);

@@ -60,6 +60,7 @@ _SIGS = {
     "sdc_create_own_stream": (C.c_int, [C.POINTER(_vp), C.c_int]),
     "sdc_get_stream": (C.c_int, [_vp, C.POINTER(_vp)]),
     "sdc_destroy": (None, [_vp]),
+    "sdc_scheme_weights": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_double)] * 6),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_set_allocator": (C.c_int, [_vp, ALLOC_FN, FREE_FN, _vp]),
     "sdc_set_body": (C.c_int, [_vp, C.c_int, _f64p, C.c_int64, _i64p, C.c_int64, _f64p,
@@ -109,6 +110,24 @@ _SIGS = {
 }
 
 _LIB = None
+
+
+NODES = {"equi_noleft": 0, "radau_right": 1, "lobatto": 2}
+
+
+def scheme_weights(nodes: str, M: int, P: int, window: int = 0) -> dict:
+    """The weight tables sdc_set_scheme forms (sdc_scheme_weights; host only, no GPU)."""
+    import numpy as np
+
+    lib = load_library()
+    shapes = {"c": (M + 1,), "emb": (M, P + 1), "S": (M, M), "Shat": (M, P), "Stil": (M, P, M),
+              "Semb": (M, P, P)}
+    out = {k: np.zeros(v) for k, v in shapes.items()}
+    ptr = [out[k].ctypes.data_as(C.POINTER(C.c_double)) for k in shapes]
+    st = lib.sdc_scheme_weights(NODES[nodes], int(M), int(P), int(window), *ptr)
+    if st != 0:
+        raise SdcError(st, "sdc_scheme_weights refused the scheme")
+    return out
 
 
 def load_library(path: str = LIB_PATH):

@@ -1540,6 +1540,29 @@ void sdc_destroy(sdc_ctx* c) {
 
 const char* sdc_last_error(const sdc_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+sdc_status sdc_scheme_weights(sdc_nodes nodes, int M, int P, int window, double* c, double* emb, double* S,
+                              double* Shat, double* Stil, double* Semb) {
+    try {
+        if (!(nodes == SDC_NODES_EQUI_NOLEFT || nodes == SDC_NODES_RADAU_RIGHT || nodes == SDC_NODES_LOBATTO) ||
+            M < 1 || M > MAX_M || P < 1 || P > MAX_P || window < 0 || window > P ||
+            (nodes == SDC_NODES_LOBATTO && M < 2))
+            return SDC_ERR_ARG;
+        const Weights W = make_weights(nodes, M, P, window);
+        auto out = [](const std::vector<double>& v, double* dst) {
+            if (dst) std::copy(v.begin(), v.end(), dst);
+        };
+        out(W.c, c);
+        out(W.emb, emb);
+        out(W.S, S);
+        out(W.Shat, Shat);
+        out(W.Stil, Stil);
+        out(W.Semb, Semb);
+        return SDC_OK;
+    } catch (...) {
+        return SDC_ERR_ARG;
+    }
+}
+
 sdc_status sdc_set_allocator(sdc_ctx* c, sdc_alloc_fn alloc, sdc_free_fn free_fn, void* user) {
     return guarded(c, [&] {
         require(!c->assembled, SDC_ERR_STATE, "allocator must be set before sdc_assemble");
