@@ -11,7 +11,9 @@ library's CUDA graphs):
   * requests are admitted in arrival order as soon as a slot is free: a
     context assembled for the request's machine, created on demand while
     the device bytes of all slots stay within the HBM budget, and reused
-    once its request has finished;
+    once its request has finished. To make room, idle slots of other
+    machines are closed, least recently used first; a request that cannot
+    fit even with every other slot idle and closed is an error;
   * every admitted request runs on its own stream; whenever that stream is
     idle the loop enqueues the next few macro steps, so requests that
     arrive while others run join the device work at once and their kernels
@@ -75,6 +77,7 @@ class LookAheadServer:
         self.footprint = 0
         self.slots_made = 0
         self.free_slots = {i: [] for i in range(len(self.machines))}
+        self.idle = deque()  # (machine index, slot) in the order the slots became idle
         self.slot_bytes = {}
         # resident warm-start states (device, FP64), initially each machine's uniform T0
         self.state = [None] * len(self.machines)
@@ -85,10 +88,29 @@ class LookAheadServer:
         t = self.torch.as_tensor(np.asarray(T) if not self.torch.is_tensor(T) else T, dtype=self.torch.float64)
         self.state[i] = t.to(f"cuda:{self.device}").contiguous()
 
+    def _release(self, i: int, slot):
+        self.free_slots[i].append(slot)
+        self.idle.append((i, slot))
+
+    def _evict_one(self, keep: int) -> bool:
+        """Close the least recently used idle slot of a machine other than `keep`."""
+        for n, (j, slot) in enumerate(self.idle):
+            if j != keep:
+                del self.idle[n]
+                self.free_slots[j].remove(slot)
+                slot.close()
+                self.footprint -= self.slot_bytes[j]
+                return True
+        return False
+
     def _slot(self, i: int):
         if self.free_slots[i]:
-            return self.free_slots[i].pop()
+            slot = self.free_slots[i].pop()
+            self.idle.remove((i, slot))
+            return slot
         est = self.slot_bytes.get(i, 0)
+        while self.footprint + est > self.budget and self._evict_one(i):
+            pass
         if self.footprint + est > self.budget:
             return None
         from .binding import Solver
@@ -101,6 +123,9 @@ class LookAheadServer:
         self.slot_bytes[i] = b
         self.footprint += b
         self.slots_made += 1
+        # a machine's first slot is sized only once made: back under the budget if idle slots allow
+        while self.footprint > self.budget and self._evict_one(i):
+            pass
         if self.state[i] is None:
             self.set_state(i, np.full(s.n, self.machines[i].T0))
         return s
@@ -110,6 +135,7 @@ class LookAheadServer:
             for s in lst:
                 s.close()
             lst.clear()
+        self.idle.clear()
 
     # ------------------------------------------------------------------ serving
     def run(self, requests: List[Request], clock=time.perf_counter) -> List[Request]:
@@ -130,6 +156,9 @@ class LookAheadServer:
                 r = waiting[i]
                 slot = self._slot(r.machine_index)
                 if slot is None:
+                    if not active:  # nothing running will free device memory
+                        raise RuntimeError(f"machine {r.machine_index} does not fit the HBM budget "
+                                           f"({self.budget} bytes) even with every other slot closed")
                     i += 1
                     continue
                 del waiting[i]
@@ -153,7 +182,7 @@ class LookAheadServer:
                     if self.keep_results:
                         r.result = T
                     active.remove(a)
-                    self.free_slots[r.machine_index].append(slot)
+                    self._release(r.machine_index, slot)
                 progressed = True
             if not progressed:
                 if not active and not waiting and pending:

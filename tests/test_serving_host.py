@@ -1,0 +1,104 @@
+"""Host logic of the serving loop (paper_1707_03581_gb300/serving.py) on the CPU,
+with a stand-in for the library's Solver: admission, slot reuse and, under a tight
+HBM budget, the closing of idle slots of other machines (least recently used
+first). The device work itself is covered by tests/test_gpu_serving.py."""
+
+import types
+
+import numpy as np
+import pytest
+
+
+class FakeSolver:
+    made, closed, live = 0, 0, set()
+    sizes = {}
+
+    def __init__(self, device, own_stream=False):
+        FakeSolver.made += 1
+        self.steps_left = 0
+
+    def set_machine(self, m, precision="mixed"):
+        self.m = m
+        self.n = m.n_dof
+        FakeSolver.live.add(id(self))
+
+    def set_graph_branches(self, on):
+        pass
+
+    def footprint(self):
+        return FakeSolver.sizes[self.m.name]
+
+    def set_temperature(self, T, t0=0.0):
+        self.T = np.full(self.n, 20.0)
+
+    def poll(self):
+        return True
+
+    def step_async(self, k):
+        self.T = self.T + k
+
+    def synchronize(self):
+        pass
+
+    def temperature(self):
+        return self.T.copy()
+
+    def close(self):
+        FakeSolver.closed += 1
+        FakeSolver.live.discard(id(self))
+
+
+def _machine(name, n):
+    sc = types.SimpleNamespace(dt=1.0, M=3, P=20, nodes="lobatto")
+    return types.SimpleNamespace(name=name, n_dof=n, scheme=sc, t0=0.0, T0=20.0)
+
+
+@pytest.fixture
+def server(monkeypatch):
+    pytest.importorskip("torch")
+    from paper_1707_03581_gb300 import binding, serving
+
+    monkeypatch.setattr(binding, "Solver", FakeSolver)
+    FakeSolver.made, FakeSolver.closed, FakeSolver.live = 0, 0, set()
+    machines = [_machine(f"m{i}", 10 + i) for i in range(4)]
+    FakeSolver.sizes = {m.name: 100 for m in machines}
+
+    def make(budget):
+        srv = serving.LookAheadServer(machines, device=0, hbm_budget_bytes=budget, chunk=4, keep_results=True)
+        srv.state = [object()] * len(machines)  # resident states exist (no device here)
+        return srv, serving
+
+    return make
+
+
+def test_slots_are_reused_and_every_request_finishes(server):
+    srv, serving = server(10_000)
+    reqs = [serving.Request(0.0, 10.0, i % 2) for i in range(6)]
+    srv.run(reqs)
+    assert all(r.t_done is not None for r in reqs)
+    assert all(np.all(r.result == 20.0 + 10) for r in reqs)
+    assert srv.slots_made <= 6 and FakeSolver.closed == 0
+    srv.close()
+
+
+def test_tight_budget_closes_idle_slots_of_other_machines(server):
+    srv, serving = server(250)  # room for two slots of 100 bytes
+    reqs = [serving.Request(0.001 * k, 4.0, k % 4) for k in range(8)]
+    srv.run(reqs)
+    assert all(r.t_done is not None for r in reqs)
+    assert srv.footprint <= 250
+    assert FakeSolver.closed >= 2  # four machines through two slots' worth of memory
+    assert len(FakeSolver.live) <= 2
+    srv.close()
+    assert not FakeSolver.live
+
+
+def test_least_recently_idle_slot_goes_first(server):
+    srv, serving = server(250)
+    srv.run([serving.Request(0.0, 1.0, 0)])
+    srv.run([serving.Request(0.0, 1.0, 1)])
+    srv.run([serving.Request(0.0, 1.0, 0)])  # machine 0's slot is reused and idle again, last
+    assert [j for j, _ in srv.idle] == [1, 0]
+    srv.run([serving.Request(0.0, 1.0, 2)])  # makes room by closing machine 1's slot
+    assert srv.free_slots[1] == [] and len(srv.free_slots[0]) == 1 and len(srv.free_slots[2]) == 1
+    srv.close()
