@@ -18,7 +18,12 @@ library's CUDA graphs):
     idle the loop enqueues the next few macro steps, so requests that
     arrive while others run join the device work at once and their kernels
     overlap;
-  * a request ends when its result is on the host.
+  * a request ends when its result is on the host ("done"). A request can be
+    cancelled (Request.cancel_at_s, or LookAheadServer.cancel): it leaves the
+    queue, or, once admitted, leaves between two enqueued batches of steps,
+    with none of its steps in flight, and its slot is reused ("cancelled"). A
+    request whose slot cannot be made (device memory, assembly) fails alone
+    ("failed", with the error), and the others go on.
 
 Each slot holds its own state and every reduction has a fixed order, so a
 request's result equals the same forecast run alone.
@@ -39,11 +44,19 @@ class Request:
     arrival_s: float
     horizon_s: float
     machine_index: int
+    # the client's cancellation time (relative to the start of the run), if any
+    cancel_at_s: Optional[float] = None
     # filled by the server
     n_steps: int = 0
+    status: str = "pending"  # then "done", "cancelled" or "failed"
+    error: Optional[str] = None
     t_admit: Optional[float] = None
     t_done: Optional[float] = None
     result: Optional[np.ndarray] = field(default=None, repr=False)
+    cancel_requested: bool = False
+
+    def cancelled_by(self, now: float) -> bool:
+        return self.cancel_requested or (self.cancel_at_s is not None and now >= self.cancel_at_s)
 
     @property
     def latency_s(self) -> float:
@@ -116,10 +129,14 @@ class LookAheadServer:
         from .binding import Solver
 
         s = Solver(self.device, own_stream=True)
-        s.set_machine(self.machines[i], precision=self.precision)
-        # slots overlap one another; a slot's own graph runs as one chain
-        s.set_graph_branches(False)
-        b = s.footprint()
+        try:
+            s.set_machine(self.machines[i], precision=self.precision)
+            # slots overlap one another; a slot's own graph runs as one chain
+            s.set_graph_branches(False)
+            b = s.footprint()
+        except Exception:
+            s.close()
+            raise
         self.slot_bytes[i] = b
         self.footprint += b
         self.slots_made += 1
@@ -129,6 +146,10 @@ class LookAheadServer:
         if self.state[i] is None:
             self.set_state(i, np.full(s.n, self.machines[i].T0))
         return s
+
+    def cancel(self, request: Request):
+        """Ask the running loop to drop `request` (queued, or between its batches of steps)."""
+        request.cancel_requested = True
 
     def close(self):
         for lst in self.free_slots.values():
@@ -151,14 +172,22 @@ class LookAheadServer:
             now = clock() - t0
             while pending and pending[0].arrival_s <= now:
                 waiting.append(pending.popleft())
+            for r in [r for r in waiting if r.cancelled_by(now)]:
+                waiting.remove(r)
+                r.status, r.t_done = "cancelled", now
             i = 0
             while i < len(waiting) and len(active) < self.max_active:
                 r = waiting[i]
-                slot = self._slot(r.machine_index)
-                if slot is None:
-                    if not active:  # nothing running will free device memory
+                try:
+                    slot = self._slot(r.machine_index)
+                    if slot is None and not active:  # nothing running will free device memory
                         raise RuntimeError(f"machine {r.machine_index} does not fit the HBM budget "
                                            f"({self.budget} bytes) even with every other slot closed")
+                except Exception as e:  # this request fails alone; the others go on
+                    del waiting[i]
+                    r.status, r.error, r.t_done = "failed", str(e), clock() - t0
+                    continue
+                if slot is None:
                     i += 1
                     continue
                 del waiting[i]
@@ -171,6 +200,12 @@ class LookAheadServer:
                 r, slot, left = a
                 if not slot.poll():
                     continue
+                if r.cancelled_by(clock() - t0):  # between batches: none of its steps in flight
+                    active.remove(a)
+                    self._release(r.machine_index, slot)
+                    r.status, r.t_done = "cancelled", clock() - t0
+                    progressed = True
+                    continue
                 if left > 0:
                     k = min(self.chunk, left)
                     slot.step_async(k)
@@ -179,6 +214,7 @@ class LookAheadServer:
                     slot.synchronize()  # surfaces device errors of the request's steps
                     T = slot.temperature()
                     r.t_done = clock() - t0
+                    r.status = "done"
                     if self.keep_results:
                         r.result = T
                     active.remove(a)
@@ -193,7 +229,13 @@ class LookAheadServer:
 
 
 def summarize(requests: List[Request], machines, n_dof) -> dict:
-    """Latency percentiles, per-request look-ahead factors and aggregate throughput."""
+    """Latency percentiles, per-request look-ahead factors and aggregate throughput of the
+    requests served to the end; cancelled and failed ones are counted apart."""
+    counts = {"cancelled": sum(r.status == "cancelled" for r in requests),
+              "failed": sum(r.status == "failed" for r in requests)}
+    requests = [r for r in requests if r.status == "done"]
+    if not requests:
+        return {"requests": 0, **counts}
     lat = np.array([r.latency_s for r in requests])
     eta = np.array([r.eta for r in requests])
     span = max(r.t_done for r in requests) - min(r.arrival_s for r in requests)
@@ -204,6 +246,7 @@ def summarize(requests: List[Request], machines, n_dof) -> dict:
         units += n_dof[r.machine_index] * r.n_steps * n_int * sc.P
     return {
         "requests": len(requests),
+        **counts,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "eta_per_request": {"p50": float(np.percentile(eta, 50)), "p1": float(np.percentile(eta, 1)),

@@ -17,10 +17,14 @@ class FakeSolver:
         FakeSolver.made += 1
         self.steps_left = 0
 
+    fail_names = set()
+
     def set_machine(self, m, precision="mixed"):
         self.m = m
         self.n = m.n_dof
         FakeSolver.live.add(id(self))
+        if m.name in FakeSolver.fail_names:  # a forced allocation failure
+            raise RuntimeError("SDC_ERR_CUDA: out of memory (forced)")
 
     def set_graph_branches(self, on):
         pass
@@ -60,6 +64,7 @@ def server(monkeypatch):
 
     monkeypatch.setattr(binding, "Solver", FakeSolver)
     FakeSolver.made, FakeSolver.closed, FakeSolver.live = 0, 0, set()
+    FakeSolver.fail_names = set()
     machines = [_machine(f"m{i}", 10 + i) for i in range(4)]
     FakeSolver.sizes = {m.name: 100 for m in machines}
 
@@ -102,3 +107,39 @@ def test_least_recently_idle_slot_goes_first(server):
     srv.run([serving.Request(0.0, 1.0, 2)])  # makes room by closing machine 1's slot
     assert srv.free_slots[1] == [] and len(srv.free_slots[0]) == 1 and len(srv.free_slots[2]) == 1
     srv.close()
+
+
+def test_cancelled_requests_leave_and_the_others_are_unchanged(server):
+    srv, serving = server(10_000)
+    reqs = [serving.Request(0.0, 6.0, k % 2) for k in range(4)]
+    queued = serving.Request(0.01, 6.0, 0, cancel_at_s=0.0)     # cancelled on arrival
+    running = serving.Request(0.0, 1e6, 1, cancel_at_s=0.05)    # cancelled while its steps run
+    srv.run(reqs + [queued, running])
+    assert queued.status == "cancelled" and queued.t_admit is None
+    assert running.status == "cancelled" and running.t_admit is not None
+    assert all(r.status == "done" and np.all(r.result == 26.0) for r in reqs)
+    stats = serving.summarize(reqs + [queued, running], srv.machines, [m.n_dof for m in srv.machines])
+    assert (stats["requests"], stats["cancelled"], stats["failed"]) == (4, 2, 0)
+    # the cancelled request's slot went back to the pool and serves the next request
+    more = serving.Request(0.0, 3.0, 1)
+    srv.run([more])
+    assert more.status == "done" and np.all(more.result == 23.0)
+    srv.close()
+
+
+def test_a_failed_admission_fails_alone(server):
+    srv, serving = server(10_000)
+    FakeSolver.fail_names = {"m3"}
+    reqs = [serving.Request(0.001 * k, 5.0, k % 4) for k in range(8)]
+    srv.run(reqs)
+    for r in reqs:
+        if r.machine_index == 3:
+            assert r.status == "failed" and "out of memory" in r.error
+        else:
+            assert r.status == "done" and np.all(r.result == 25.0)
+    assert FakeSolver.closed == 2  # each failed slot was closed at once
+    stats = serving.summarize(reqs, srv.machines, [m.n_dof for m in srv.machines])
+    assert (stats["requests"], stats["failed"]) == (6, 2)
+    srv.close()
+    assert not FakeSolver.live
+
