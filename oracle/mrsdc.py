@@ -102,6 +102,25 @@ def _residual(prob, T_n, T_std, I_std):
     return r
 
 
+def predictor_interval(prob, T_left, tau_left, tau_right, tau_emb_m, n_substeps=None):
+    """Algorithm 1 on one interval [tau_{m-1}, tau_m]: the implicit solve for T*_m, f*_m, then
+    the explicit substeps T_{m,p}, p = 1..P, on the embedded nodes tau_emb_m[0..P]. Returns
+    ([T_{m,0}, ..., T_{m,P}], CG iterations). n_substeps < P stops after that many substeps
+    (a bounded sample of the interval's work; the list then ends at T_{m,n_substeps})."""
+    mass = prob.mass
+    P = len(tau_emb_m) - 1
+    dtau = tau_right - tau_left
+    rhs = mass * T_left + dtau * prob.g(tau_right)
+    Tstar, it = prob.solve(dtau, rhs, T_left)
+    fstar = prob.fI(Tstar) + prob.g(tau_right)
+    T_emb = [T_left.copy()]
+    for p in range(1, (P if n_substeps is None else min(P, n_substeps)) + 1):
+        dtp = tau_emb_m[p] - tau_emb_m[p - 1]
+        incr = dtp * (fstar + prob.fE(T_emb[p - 1], tau_emb_m[p - 1]))
+        T_emb.append(T_emb[p - 1] + incr / mass)
+    return T_emb, it
+
+
 def mrsdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False, keep_nodes=False):
     """One macro step; returns (T(t_n + dt), StepResult)."""
     M, P = W["M"], W["P"]
@@ -113,18 +132,10 @@ def mrsdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False, keep_nodes=F
 
     # ---------------- Algorithm 1: predictor ----------------
     T_std = [T_n.copy()] + [None] * M
-    T_emb = [[None] * (P + 1) for _ in range(M)]
+    T_emb = [None] * M
     for m in range(M):
-        dtau = tau[m + 1] - tau[m]
-        rhs = mass * T_std[m] + dtau * prob.g(tau[m + 1])
-        Tstar, it = prob.solve(dtau, rhs, T_std[m])
+        T_emb[m], it = predictor_interval(prob, T_std[m], tau[m], tau[m + 1], tau_emb[m])
         res.cg_iters.append(it)
-        fstar = prob.fI(Tstar) + prob.g(tau[m + 1])
-        T_emb[m][0] = T_std[m].copy()
-        for p in range(1, P + 1):
-            dtp = tau_emb[m][p] - tau_emb[m][p - 1]
-            incr = dtp * (fstar + prob.fE(T_emb[m][p - 1], tau_emb[m][p - 1]))
-            T_emb[m][p] = T_emb[m][p - 1] + incr / mass
         T_std[m + 1] = T_emb[m][P]
 
     # ---------------- Algorithm 2: sweeps ----------------
