@@ -11,9 +11,13 @@ library's CUDA graphs):
   * requests are admitted in arrival order as soon as a slot is free: a
     context assembled for the request's machine, created on demand while
     the device bytes of all slots stay within the HBM budget, and reused
-    once its request has finished. To make room, idle slots of other
-    machines are closed, least recently used first; a request that cannot
-    fit even with every other slot idle and closed is an error;
+    once its request has finished. A slot's bytes are estimated before it
+    is made (measured for a machine that had one, else scaled by DOF count
+    from the slots made so far) and measured after; a new slot that leaves
+    the total over the budget is closed again and its request waits for
+    active slots to finish. To make room, idle slots of other machines are
+    closed, least recently used first; a request that cannot fit even with
+    every other slot idle and closed is an error;
   * every admitted request runs on its own stream; whenever that stream is
     idle the loop enqueues the next few macro steps, so requests that
     arrive while others run join the device work at once and their kernels
@@ -88,6 +92,7 @@ class LookAheadServer:
             hbm_budget_bytes = int(0.8 * free)
         self.budget = hbm_budget_bytes
         self.footprint = 0
+        self.peak_footprint = 0
         self.slots_made = 0
         self.free_slots = {i: [] for i in range(len(self.machines))}
         self.idle = deque()  # (machine index, slot) in the order the slots became idle
@@ -116,12 +121,23 @@ class LookAheadServer:
                 return True
         return False
 
+    def _estimate(self, i: int) -> int:
+        """Device bytes of a slot of machine i: measured once one was made, else scaled
+        from the slots made so far by DOF count (0 before the first slot of any machine)."""
+        if i in self.slot_bytes:
+            return self.slot_bytes[i]
+        known = [(self.slot_bytes[j], self.machines[j].n_dof) for j in self.slot_bytes]
+        if not known:
+            return 0
+        per_dof = max(b / max(n, 1) for b, n in known)
+        return int(per_dof * self.machines[i].n_dof)
+
     def _slot(self, i: int):
         if self.free_slots[i]:
             slot = self.free_slots[i].pop()
             self.idle.remove((i, slot))
             return slot
-        est = self.slot_bytes.get(i, 0)
+        est = self._estimate(i)
         while self.footprint + est > self.budget and self._evict_one(i):
             pass
         if self.footprint + est > self.budget:
@@ -139,10 +155,16 @@ class LookAheadServer:
             raise
         self.slot_bytes[i] = b
         self.footprint += b
-        self.slots_made += 1
-        # a machine's first slot is sized only once made: back under the budget if idle slots allow
+        # the estimate can be short: back under the budget if idle slots allow, else the new
+        # slot is closed again and the request waits for active slots to finish
         while self.footprint > self.budget and self._evict_one(i):
             pass
+        if self.footprint > self.budget:
+            s.close()
+            self.footprint -= b
+            return None
+        self.slots_made += 1
+        self.peak_footprint = max(self.peak_footprint, self.footprint)
         if self.state[i] is None:
             self.set_state(i, np.full(s.n, self.machines[i].T0))
         return s

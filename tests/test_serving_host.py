@@ -143,3 +143,60 @@ def test_a_failed_admission_fails_alone(server):
     srv.close()
     assert not FakeSolver.live
 
+
+
+class SlowSolver(FakeSolver):
+    """A stand-in whose enqueued steps stay in flight for a number of polls, so that
+    slots of several machines are active at once."""
+
+    polls_busy = 30
+
+    def step_async(self, k):
+        super().step_async(k)
+        self.busy = SlowSolver.polls_busy
+
+    def poll(self):
+        if getattr(self, "busy", 0) > 0:
+            self.busy -= 1
+            return False
+        return True
+
+
+def test_admission_never_exceeds_the_budget_while_slots_are_active(server, monkeypatch):
+    from paper_1707_03581_gb300 import binding
+
+    monkeypatch.setattr(binding, "Solver", SlowSolver)
+    srv, serving = server(250)  # room for two slots of 100 bytes
+    seen = []
+    orig = srv._slot
+
+    def watched(i):
+        s = orig(i)
+        seen.append(srv.footprint)
+        assert srv.footprint <= srv.budget, (i, srv.footprint)
+        return s
+
+    srv._slot = watched
+    reqs = [serving.Request(0.0, 8.0, k % 4) for k in range(8)]  # four machines at once
+    srv.run(reqs)
+    assert all(r.status == "done" and np.all(r.result == 28.0) for r in reqs)
+    assert max(seen) <= 250 and srv.peak_footprint <= 250
+    srv.close()
+    assert not FakeSolver.live
+
+
+def test_an_underestimated_first_slot_is_closed_and_its_request_waits(server, monkeypatch):
+    # machine 3's slot has twice the bytes per DOF of the others: its estimate (scaled
+    # from them) is short, so the slot made while two others run is closed again at once
+    from paper_1707_03581_gb300 import binding
+
+    monkeypatch.setattr(binding, "Solver", SlowSolver)
+    srv, serving = server(350)
+    FakeSolver.sizes["m3"] = 200  # estimate 13 DOF x 10 bytes = 130
+    reqs = [serving.Request(0.0, 8.0, 0), serving.Request(0.0, 8.0, 1), serving.Request(0.0, 8.0, 3)]
+    srv.run(reqs)
+    assert all(r.status == "done" for r in reqs)
+    assert srv.peak_footprint <= 350
+    assert FakeSolver.made > srv.slots_made  # the oversized attempt was made, then closed
+    srv.close()
+    assert not FakeSolver.live
