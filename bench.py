@@ -1,8 +1,11 @@
 """Benchmark: IMEX multi-rate SDC macro steps of the coupled stand/stock heat problem.
 
-Workload (default): the 48x48x120 stand + 24x24x36 stock machine (313,646
-DOF, seeded stroke), Lobatto M=3, 3 sweeps, P=20 embedded substeps, dt = 1 s,
-CG to rel 1e-12. One "step" = one macro step (Algorithm 1 + 3 x Algorithm 2).
+Workload (default): the largest single-GPU machine, 128x128x320 stand + 64x64x96
+stock hexes (5,751,586 DOF, one conductivity per hexahedron), Radau IIA M=4,
+4 sweeps, P=40 embedded substeps, dt = 1 s, CG to rel 1e-12. One "step" = one
+macro step (Algorithm 1 + 4 x Algorithm 2). The 313,646-DOF machine (Lobatto
+M=3, 3 sweeps, P=20) is measured beside it (`workload_313k`; --config 1 makes
+it the headline).
 
   value  = DOF x substeps per second (N_dof x M' x P per macro step) of the
            mixed-precision path (FP32 SpMV/CG on the correction inside FP64
@@ -11,7 +14,10 @@ CG to rel 1e-12. One "step" = one macro step (Algorithm 1 + 3 x Algorithm 2).
   fp64   = the plain FP64 path on the same inputs, timed the same way, with
            the gain of the mixed path over it and the rel-L2 between the two;
            `accuracy` also holds the rel-L2 of each path against the CPU
-           oracle's first macro step (computed with the cpu_baseline leg)
+           oracle's first macro step where the oracle takes one (313k)
+  roofline / cg_iteration = the CG SpMV and the whole CG iteration (SpMV +
+           update) against the measured HBM bandwidth, from CUDA events in live
+           eager steps and in graph execution
 
 Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
 on the solver's stream, with L2 flushed (256 MiB write) between steps
@@ -114,53 +120,164 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_baseline(config_idx, steps, save_to=None):
-    """Time the CPU oracle (single-threaded numpy/scipy) in a fresh process;
-    optionally save its final temperature field (.npy) for an accuracy check."""
-    code = (
-        "import os, sys, time, json, numpy as np\n"
-        f"sys.path.insert(0, {ROOT!r})\n"
-        "from synth import machine_config\n"
-        "from oracle.machine import MachineProblem\n"
-        "from oracle.mrsdc import mrsdc_step\n"
-        "from oracle.weights import mrsdc_weights\n"
-        f"m = machine_config({config_idx}); s = m.scheme\n"
-        "prob = MachineProblem(m)\n"
-        "W = mrsdc_weights(s.nodes, s.M, s.P, s.window)\n"
-        "T = np.full(prob.n, m.T0)\n"
-        "t = time.perf_counter()\n"
-        f"for n in range({steps}):\n"
-        "    T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)\n"
-        "el = time.perf_counter() - t\n"
-        f"save_to = {save_to!r}\n"
-        "if save_to: np.save(save_to, T)\n"
-        "print(json.dumps({'seconds': el, 'n': prob.n}))\n"
-    )
+def _host_cpu():
+    """Model name of the host CPU and its logical core count (os.cpu_count())."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+
+    return {"model": model or platform.processor() or platform.machine(), "logical_cores": os.cpu_count(),
+            "arch": platform.machine()}
+
+
+def _oracle_env():
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    return env
+
+
+# The oracle runs in a child process with one thread for BLAS (single-threaded numpy/scipy).
+_ORACLE_STEPS = """
+import os, sys, time, json, numpy as np
+sys.path.insert(0, {root!r})
+from synth import machine_config
+from oracle.machine import MachineProblem
+from oracle.mrsdc import mrsdc_step
+from oracle.weights import mrsdc_weights
+m = machine_config({idx}); s = m.scheme
+t = time.perf_counter()
+prob = MachineProblem(m)
+W = mrsdc_weights(s.nodes, s.M, s.P, s.window)
+asm = time.perf_counter() - t
+T = np.full(prob.n, m.T0)
+times = []
+for n in range({warmup} + {steps}):
+    t = time.perf_counter()
+    T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)
+    if n >= {warmup}:
+        times.append(time.perf_counter() - t)
+if {save_to!r}:
+    np.save({save_to!r}, T)
+print(json.dumps({{"seconds": times, "n": prob.n, "assembly_s": asm}}))
+"""
+
+# A bounded sample of one macro step: Algorithm 1 on the first interval of positive length
+# (its implicit solve, f*_m, then the first `substeps` of its P explicit substeps on the full
+# vectors), with the oracle's own predictor code, repeated from the same start.
+_ORACLE_SAMPLE = """
+import os, sys, time, json, numpy as np
+sys.path.insert(0, {root!r})
+from synth import machine_config
+from oracle.machine import MachineProblem
+from oracle.mrsdc import predictor_interval
+from oracle.weights import mrsdc_weights
+m = machine_config({idx}); s = m.scheme
+t = time.perf_counter()
+prob = MachineProblem(m)
+W = mrsdc_weights(s.nodes, s.M, s.P, s.window)
+asm = time.perf_counter() - t
+c = W["c"]
+k = next(j for j in range(s.M) if c[j + 1] > c[j])
+tau_l, tau_r = m.t0 + s.dt * c[k], m.t0 + s.dt * c[k + 1]
+emb = [m.t0 + s.dt * e for e in W["emb"][k]]
+T = np.full(prob.n, m.T0)
+times, it = [], 0
+for n in range({warmup} + {reps}):
+    t = time.perf_counter()
+    Temb, it = predictor_interval(prob, T, tau_l, tau_r, emb, n_substeps={substeps})
+    if n >= {warmup}:
+        times.append(time.perf_counter() - t)
+print(json.dumps({{"seconds": times, "n": prob.n, "assembly_s": asm, "interval": k + 1, "cg_iters": it,
+                   "substeps": len(Temb) - 1}}))
+"""
+
+
+def _oracle_start(code):
+    """Start an oracle child process (returns the Popen; read it with _oracle_finish)."""
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                            env=_oracle_env())
+
+
+def _oracle_finish(proc, timeout=3600):
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError("oracle run failed: " + err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def _oracle_steps(config_idx, steps, warmup=0, save_to=None):
+    return _oracle_start(_ORACLE_STEPS.format(root=ROOT, idx=config_idx, steps=steps, warmup=warmup,
+                                              save_to=save_to))
+
+
+def _oracle_sample(config_idx, substeps, reps, warmup=0):
+    return _oracle_start(_ORACLE_SAMPLE.format(root=ROOT, idx=config_idx, substeps=substeps, reps=reps,
+                                               warmup=warmup))
+
+
+# Workloads whose oracle macro step does not fit a bounded CPU sample: the sample is part of
+# Algorithm 1 (first interval: its solve and the first SAMPLE_SUBSTEPS substeps).
+SAMPLE_SUBSTEPS = {2: 8}
+REFERENCE_SUBSTEPS = {2: 2}
+
+
+def _sample_desc(m, n_int, substeps, res):
+    return (f"Algorithm 1 on interval {res['interval']} of the first macro step of the {m.n_dof}-DOF workload: "
+            f"its implicit solve ({res['cg_iters']} CG iterations from the uniform start), f*_m and the first "
+            f"{substeps} of its P = {m.scheme.P} explicit substeps on the full vectors; credited "
+            f"{substeps} x {m.n_dof} DOF-substeps per sample. A macro step runs {n_int} intervals of P substeps "
+            f"and {m.scheme.sweeps} sweeps, whose quadratures and f^E differences the sample leaves out, so this "
+            f"rate bounds the oracle's macro-step rate from above; single-threaded numpy/scipy "
+            f"(oracle assembly, {res['assembly_s']:.0f} s, not timed)")
+
+
+def _cpu_baseline_line(value, cores_note, sample, host):
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "threads": cores_note, "host_cpu": host}
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores (the only reference: the paper ships no code), on the
+    workload and metric of the GPU arm: K timed steps after W untimed ones, each a bounded
+    sample of the workload (a full macro step where the oracle takes one in seconds, else
+    part of Algorithm 1, see SAMPLE_SUBSTEPS)."""
     m, n_int, desc = _workload(args.config)
     if rank != 0:
         return
-    steps = max(1, min(args.steps, 3))
-    res = _oracle_baseline(args.config, steps)
-    units = res["n"] * n_int * m.scheme.P * steps
-    value = units / res["seconds"]
-    ms = res["seconds"] / steps * 1e3
+    host = _host_cpu()
+    if args.config in REFERENCE_SUBSTEPS:
+        S = REFERENCE_SUBSTEPS[args.config]
+        res = _oracle_finish(_oracle_sample(args.config, S, args.steps, args.warmup))
+        units = res["n"] * S * len(res["seconds"])
+        sample = _sample_desc(m, n_int, S, res)
+    else:
+        res = _oracle_finish(_oracle_steps(args.config, args.steps, args.warmup))
+        units = res["n"] * n_int * m.scheme.P * len(res["seconds"])
+        sample = (f"{args.steps} macro steps of the workload after {args.warmup} untimed ones, "
+                  f"single-threaded numpy/scipy")
+    secs = float(sum(res["seconds"]))
+    value = units / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": steps, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "precision": "fp64", "l2": "n/a (CPU)"},
-            "eta": steps * m.scheme.dt / res["seconds"],
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {steps} macro steps of the workload, single-threaded"},
+            "cpu_baseline": _cpu_baseline_line(value, "1 (BLAS threads = 1)", sample, host),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -207,10 +324,37 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
-# capture of the current kernel on the named workload (summary under profiles/);
-# reported only for that workload, and to be cleared whenever the kernel changes.
-TRAFFIC = {("k_mx_spmv", 1): 70.511872e6 + 0.678144e6}
+def _kernels_sha():
+    import hashlib
+
+    with open(os.path.join(ROOT, "paper_1707_03581_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _profile_traffic(kernel, n_dof):
+    """DRAM bytes (read + written) per launch of `kernel` on the n_dof-DOF workload, from a
+    kept ncu summary under profiles/: a line
+        bench-traffic: kernel=<name> n_dof=<N> dram_bytes=<B> kernels_cu_sha256=<first 16 hex>
+    Returns (bytes or None, note); None when no summary has the kernel and workload, or when
+    kernels.cu changed since the capture (the counters then describe another kernel)."""
+    import glob
+
+    sha = _kernels_sha()
+    stale = None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for ln in open(path):
+            if not ln.startswith("bench-traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in ln.split(":", 1)[1].split())
+            if kv.get("kernel") != kernel or int(kv.get("n_dof", -1)) != n_dof:
+                continue
+            if kv.get("kernels_cu_sha256") != sha:
+                stale = os.path.basename(path)
+                continue
+            return float(kv["dram_bytes"]), f"ncu summary {os.path.basename(path)} (kernels.cu {sha})"
+    if stale:
+        return None, f"kernels.cu changed since the capture in {stale}"
+    return None, "no ncu summary of this kernel on this workload"
 
 
 def _dominant_kernel(s, precision, kt, reps):
@@ -225,12 +369,27 @@ def _dominant_kernel(s, precision, kt, reps):
     iters = sum(r["cg_iters_total"] for r in reps)
     if precision == "mixed":
         name = "k_mx_spmv" if "k_mx_spmv" in kt else "k_mx_spmv_red"
+        upd = "k_mx_update" if name == "k_mx_spmv" else "k_mx_update_red"
         work = iters + sum(r["refinements_total"] for r in reps)
-        return (name, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)", 8 * nnz + 16 * n,
-                work, kt.get(name, (0, 0.0)))
+        return (name, upd, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)", 8 * nnz + 16 * n,
+                48 * n, work, kt.get(name, (0, 0.0)), kt.get(upd, (0, 0.0)))
     work = iters + sum(r["n_solves"] for r in reps)
-    return ("k_cg_spmv", "FP64 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)", 12 * nnz + 32 * n,
-            work, kt.get("k_cg_spmv", (0, 0.0)))
+    return ("k_cg_spmv", "k_cg_update", "FP64 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)",
+            12 * nnz + 32 * n, 96 * n, work, kt.get("k_cg_spmv", (0, 0.0)), kt.get("k_cg_update", (0, 0.0)))
+
+
+def _graph_cg(s, m, flush, n_iters=30, reps=3):
+    """Device time of the CG iterations of the implicit stage in graph execution
+    (sdc_time_cg_iterations): n_iters back-to-back iterations, L2 flushed before each of
+    `reps` graphs; the median per iteration, of (SpMV, update) pairs and of SpMVs alone."""
+    dtau = 0.5 * m.scheme.dt
+    pair, spmv = [], []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        pair.append(s.time_cg_iterations(dtau, n_iters) / n_iters)
+        flush.fill_(2.0)
+        spmv.append(s.time_cg_iterations(dtau, n_iters, spmv_only=True) / n_iters)
+    return statistics.median(pair), statistics.median(spmv)
 
 
 def _stationary_start(m, local, torch):
@@ -397,31 +556,28 @@ def _single_rate(m, local, torch, args, flush):
             "rel_l2_vs_mrsdc_after_5_steps": diff, "rel_l2_rise_vs_mrsdc_after_5_steps": rise}
 
 
-def run_gpu(args, rank, world):
+def _measure(m, n_int, args, local, torch, flush, world, precision, compare, e2e=True, clocks=True):
+    """Macro steps of machine m timed in graph execution (the path in `precision`, and the
+    plain FP64 path on the same inputs when `compare`), per-kernel event times of eager
+    steps, the graph-mode CG iterations, and the end-to-end run through the public API."""
     import numpy as np
-    import torch
 
     from paper_1707_03581_gb300 import Solver
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    m, n_int, desc = _workload(args.config)
-    P = m.scheme.P
-
-    def make(precision):
-        s = Solver(local)
-        s.set_machine(m, precision=precision)
+    def make(prec):
+        sv = Solver(local)
+        sv.set_machine(m, precision=prec)
         if args.eager:
-            s.set_execution(True)
-        return s
+            sv.set_execution(True)
+        return sv
 
-    s = make(args.precision)
-    compare = args.precision == "mixed" and not args.no_compare
+    t_setup = time.perf_counter()
+    s = make(precision)
     s64 = make("fp64") if compare else None
-    units_per_step = s.n * n_int * P
+    t_setup = time.perf_counter() - t_setup
     stream = s.stream
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
-
+    out = {"n": s.n, "nnz": s.nnz, "n_contact": s.n_contact, "setup_s": t_setup,
+           "units_per_step": s.n * n_int * m.scheme.P}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.step(report=True)
@@ -431,61 +587,173 @@ def run_gpu(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
         with ClockSampler(local) as clk:
-            ms_steps = _timed_steps(s, stream, flush, args.steps, torch)
-        total_ms = float(sum(ms_steps))
-        # launches and CG work of one step, from a reported step after the timed region
-        rep = s.step(report=True)
-        launches = rep["kernel_launches"] * args.steps
-        ms64 = None
+            out["ms_steps"] = _timed_steps(s, stream, flush, args.steps, torch)
+        out["clocks"] = clk.summary() if clocks else None
+        out["rep"] = s.step(report=True)
         if s64 is not None:
-            ms64 = _timed_steps(s64, stream, flush, args.steps, torch)
-            rep64 = s64.step(report=True)
-            rel_vs_fp64 = _rel_l2(s.temperature(), s64.temperature())
-
+            out["ms64"] = _timed_steps(s64, stream, flush, args.steps, torch)
+            out["rep64"] = s64.step(report=True)
+            Ta, Tb = s.temperature(), s64.temperature()
+            out["rel_vs_fp64"] = _rel_l2(Ta, Tb)
+            out["rel_rise_vs_fp64"] = _rel_l2(Ta - m.T0, Tb - m.T0)
+            s64.close()
         # per-kernel device times of the same steps, each launch between CUDA events on the
         # solver's stream (plain launches; the CG loop is driven from the host one iteration ahead)
         s.set_execution(True)
         s.set_kernel_timing(True)
-        eager_reps = []
-        eager_ms = _timed_steps(s, stream, flush, args.steps, torch, eager_reps)
-        kt = s.kernel_times()
+        out["eager_reps"] = []
+        out["eager_ms"] = _timed_steps(s, stream, flush, args.steps, torch, out["eager_reps"])
+        out["kt"] = s.kernel_times()
         s.set_kernel_timing(False)
         s.set_execution(bool(args.eager))
+        out["graph_cg_ms"], out["graph_spmv_ms"] = _graph_cg(s, m, flush)
+    out["total_ms"] = float(sum(out["ms_steps"]))
+    if e2e:
+        # end to end through the public API: host state in, host state out, every step
+        pin_in = torch.empty(s.n, dtype=torch.float64).pin_memory()
+        pin_out = torch.empty(s.n, dtype=torch.float64).pin_memory()
+        pin_in.copy_(torch.from_numpy(s.temperature()))
+        t_sim = m.t0
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_temperature(pin_in.numpy(), t0=t_sim)
+            s.step(report=False)
+            s.temperature(out=pin_out)
+            t_sim += m.scheme.dt
+        torch.cuda.synchronize()
+        out["e2e_s"] = _max_over_ranks(time.perf_counter() - t0, world, f"cuda:{local}")
+    out["solver"] = s
+    return out
 
-    t_max = _max_over_ranks(total_ms, world, f"cuda:{local}")
 
-    # end-to-end through the public API: host state in, host state out, every step
-    pin_in = torch.empty(s.n, dtype=torch.float64).pin_memory()
-    pin_out = torch.empty(s.n, dtype=torch.float64).pin_memory()
-    pin_in.copy_(torch.from_numpy(s.temperature()))
-    t_sim = m.t0
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        s.set_temperature(pin_in.numpy(), t0=t_sim)
-        s.step(report=False)
-        s.temperature(out=pin_out)
-        t_sim += m.scheme.dt
-    torch.cuda.synchronize()
-    e2e_s = _max_over_ranks(time.perf_counter() - t0, world, f"cuda:{local}")
-
-    # dominant HBM kernel: the CG SpMV
-    peak, peak_kind = _peaks()
-    spmv_name, spmv_desc, spmv_bytes, n_spmv, (n_launched, ms_spmv) = _dominant_kernel(s, args.precision, kt,
-                                                                                      eager_reps)
-    ms_per_spmv = ms_spmv / max(n_spmv, 1)
-    achieved = spmv_bytes / (ms_per_spmv * 1e-3) / 1e9 if n_spmv else 0.0
+def _kernel_report(mres, precision, args, peak, peak_kind):
+    """Roofline of the dominant kernel (the CG SpMV), the FP32/FP64 CG iteration in graph
+    execution, and every kernel's share of the eager steps' kernel time."""
+    s, kt, reps = mres["solver"], mres["kt"], mres["eager_reps"]
+    name, upd, desc, sp_bytes, up_bytes, n_work, (n_launched, ms_spmv), (_, ms_upd) = _dominant_kernel(
+        s, precision, kt, reps)
+    ms_per_spmv = ms_spmv / max(n_work, 1)
+    achieved = sp_bytes / (ms_per_spmv * 1e-3) / 1e9 if n_work else 0.0
+    traffic, traffic_note = _profile_traffic(name, s.n)
+    g_spmv = mres["graph_spmv_ms"]
+    g_iter = mres["graph_cg_ms"]
+    it_bytes = sp_bytes + up_bytes
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic, "traffic_source": traffic_note,
+            "kernel": f"{name} ({desc})", "algorithmic_bytes": sp_bytes, "ms_per_launch": ms_per_spmv,
+            "launches_timed": n_launched, "launches_working": n_work, "peak_kind": peak_kind,
+            "timing": "CUDA events around each launch of the eager timed steps (live macro steps, L2 flushed "
+                      "between steps); total time of all launches / launches that did work",
+            "graph_mode": {"ms_per_launch": g_spmv, "achieved": sp_bytes / (g_spmv * 1e-3) / 1e9,
+                           "frac": sp_bytes / (g_spmv * 1e-3) / 1e9 / peak,
+                           "timing": "30 back-to-back SpMV launches in one CUDA graph "
+                                     "(sdc_time_cg_iterations), L2 flushed before; median of 3"}}
+    cg_it = {"kernels": f"{name} + {upd}", "algorithmic_bytes": it_bytes,
+             "bytes_note": (f"SpMV {sp_bytes} (8 B/nnz + 16 B/row) + update {up_bytes} (48 B/row)" if precision == "mixed"
+                            else f"SpMV {sp_bytes} (12 B/nnz + 32 B/row) + update {up_bytes} (96 B/row)"),
+             "ms_graph": g_iter, "achieved": it_bytes / (g_iter * 1e-3) / 1e9,
+             "frac": it_bytes / (g_iter * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+             "ms_eager": (ms_spmv + ms_upd) / max(n_work, 1),
+             "timing": "30 back-to-back (SpMV, update) iterations in one CUDA graph of the step's kernels, "
+                       "grids and launch order (sdc_time_cg_iterations), L2 flushed before; median of 3"}
     kern_total = sum(v[1] for v in kt.values())
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
                    "ms_per_launch": v[1] / max(v[0], 1), "share": v[1] / kern_total if kern_total else 0.0}
                for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+    return roof, cg_it, kernels
 
+
+def _workload_summary(m, n_int, mres, args, precision):
+    """Per-workload figures: the timed path, the FP64 comparison, the accuracy between them."""
+    ms = mres["total_ms"] / args.steps
+    units = mres["units_per_step"]
+    srt = sorted(mres["ms_steps"])
+    out = {"ms_per_step": ms, "value": units / (ms * 1e-3), "eta": m.scheme.dt / (ms * 1e-3),
+           "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+           "cg_iters_per_step": mres["rep"]["cg_iters_total"],
+           "refinements_per_step": mres["rep"]["refinements_total"],
+           "contact_cluster": mres["rep"]["contact_cluster"],
+           "eager_ms_per_step": sum(mres["eager_ms"]) / len(mres["eager_ms"]),
+           "setup_s": mres["setup_s"]}
+    if "ms64" in mres:
+        ms64 = sum(mres["ms64"]) / args.steps
+        out["fp64"] = {"value": units / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                       "eta": m.scheme.dt / (ms64 * 1e-3), "cg_iters_per_step": mres["rep64"]["cg_iters_total"]}
+        out["gain_vs_fp64"] = ms64 / ms
+        out["accuracy"] = {"rel_l2_mixed_vs_fp64": mres["rel_vs_fp64"],
+                           "rel_l2_rise_mixed_vs_fp64": mres["rel_rise_vs_fp64"],
+                           "after_steps": args.warmup + args.steps + 1}
+    return out
+
+
+def _oracle_accuracy(m, precision, compare, local, T_or):
+    """rel-L2 of the GPU paths against the oracle's first macro step."""
+    from paper_1707_03581_gb300 import Solver
+
+    acc = {}
+    for prec in ([precision, "fp64"] if compare else [precision]):
+        g = Solver(local)
+        g.set_machine(m, precision=prec)
+        g.step(report=True)
+        acc[f"rel_l2_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature(), T_or)
+        acc[f"rel_l2_rise_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature() - m.T0, T_or - m.T0)
+        g.close()
+    return acc
+
+
+def run_gpu(args, rank, world):
+    import tempfile
+
+    import numpy as np
+    import torch
+
+    from synth import machine_config
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    m, n_int, desc = _workload(args.config)
+    compare = args.precision == "mixed" and not args.no_compare
+    peak, peak_kind = _peaks()
+    host = _host_cpu()
+    cpu_on = not args.no_cpu_baseline and world == 1 and rank == 0
+    # The 313,646-DOF workload rides along with the 5.75M-DOF headline (labelled extra key); the
+    # comparison rows (stationary start, single-rate SDC, implicit Euler) run on it there.
+    side_idx = 1 if args.config == 2 and not args.no_extra else None
+    tmp = tempfile.mkdtemp()
+    oracle = {}
+    if cpu_on:
+        # the oracle runs in child processes on the host cores while the GPU work proceeds
+        if args.config in SAMPLE_SUBSTEPS:
+            oracle["main"] = _oracle_sample(args.config, SAMPLE_SUBSTEPS[args.config], reps=1)
+        else:
+            oracle["main"] = _oracle_steps(args.config, 1, save_to=os.path.join(tmp, "main.npy"))
+        if side_idx is not None:
+            oracle["side"] = _oracle_steps(side_idx, 1, save_to=os.path.join(tmp, "side.npy"))
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    mres = _measure(m, n_int, args, local, torch, flush, world, args.precision, compare)
+    t_max = _max_over_ranks(mres["total_ms"], world, f"cuda:{local}")
+    roof, cg_it, kernels = _kernel_report(mres, args.precision, args, peak, peak_kind)
+    summ = _workload_summary(m, n_int, mres, args, args.precision)
+    units_per_step = mres["units_per_step"]
+    s = mres["solver"]
+
+    side = None
+    if side_idx is not None:
+        ms_, ni_, desc_ = _workload(side_idx)
+        sres = _measure(ms_, ni_, args, local, torch, flush, world, args.precision, compare, e2e=False,
+                        clocks=False)
+        sroof, scg, skern = _kernel_report(sres, args.precision, args, peak, peak_kind)
+        side = {"workload": desc_, **_workload_summary(ms_, ni_, sres, args, args.precision),
+                "roofline": sroof, "cg_iteration": scg,
+                "kernels_top": dict(list(skern.items())[:6])}
+        sres["solver"].close()
     if rank != 0:
         return
     value = units_per_step * args.steps * world / (t_max * 1e-3)
-    srt = sorted(ms_steps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -496,68 +764,59 @@ def run_gpu(args, rank, world):
                                  "FP64 residuals, quadratures and state" if args.precision == "mixed"
                                  else "fp64 throughout"),
                    "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MiB write)",
+                   "l2": "flushed between timed steps (256 MiB write); the step's working set exceeds L2",
                    "execution": "eager launches" if args.eager else "one CUDA graph per macro step"},
         "eta": args.steps * m.scheme.dt / (t_max * 1e-3),
-        "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
-        "cg_iters_per_step": rep["cg_iters_total"],
-        "refinements_per_step": rep["refinements_total"],
-        "contact_cluster": rep["contact_cluster"],
-        "e2e": {"value": units_per_step * args.steps * world / e2e_s, "unit": UNIT,
+        **{k: v for k, v in summ.items() if k not in ("ms_per_step", "value", "eta")},
+        "e2e": {"value": units_per_step * args.steps * world / mres["e2e_s"], "unit": UNIT,
                 "h2d_bytes_per_step": 8 * s.n, "d2h_bytes_per_step": 8 * s.n,
-                "eta": args.steps * m.scheme.dt / e2e_s},
-        "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None,
-                     "traffic": TRAFFIC.get((spmv_name, args.config)),
-                     "kernel": f"{spmv_name} ({spmv_desc})",
-                     "algorithmic_bytes": spmv_bytes, "ms_per_launch": ms_per_spmv,
-                     "launches_timed": n_launched, "launches_working": n_spmv, "peak_kind": peak_kind,
-                     "timing": "CUDA events around each launch of the eager timed steps; total time of all "
-                               "launches / launches that did work"},
+                "eta": args.steps * m.scheme.dt / mres["e2e_s"]},
+        "gpu_launches": mres["rep"]["kernel_launches"] * args.steps,
+        "roofline": roof,
+        "cg_iteration": cg_it,
         "kernels": kernels,
-        "eager_ms_per_step": sum(eager_ms) / len(eager_ms),
-        "clocks": clk.summary(),
+        "clocks": mres["clocks"],
+        "host_cpu": host,
     }
-    if ms64 is not None:
-        v64 = units_per_step * args.steps / (sum(ms64) * 1e-3)
-        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": sum(ms64) / args.steps,
-                        "eta": args.steps * m.scheme.dt / (sum(ms64) * 1e-3),
-                        "cg_iters_per_step": rep64["cg_iters_total"]}
-        line["gain_vs_fp64"] = value / v64
-        line["accuracy"] = {"rel_l2_mixed_vs_fp64": rel_vs_fp64,
-                            "after_steps": args.warmup + args.steps + 1}
+    if side is not None:
+        line["workload_313k"] = side
+    s.close()
+    rows_m = machine_config(side_idx) if side_idx is not None else m
     if not args.no_stationary:
-        line["stationary_start"] = _stationary_start(m, local, torch)
+        line["stationary_start"] = _stationary_start(rows_m, local, torch)
     if not args.no_single_rate:
-        line["single_rate"] = _single_rate(m, local, torch, args, flush)
+        line["single_rate"] = _single_rate(rows_m, local, torch, args, flush)
     if not args.no_ie and world == 1:
-        from synth import machine_config
-
         small = machine_config(0)
         line["vs_implicit_euler"] = [_vs_implicit_euler(x, local, torch, args)
-                                     for x in ([m, small] if m.n_dof != small.n_dof else [m])]
-    if not args.no_cpu_baseline and world == 1:
+                                     for x in ([rows_m, small] if rows_m.n_dof != small.n_dof else [rows_m])]
+    if cpu_on:
         try:
-            import tempfile
-
-            with tempfile.TemporaryDirectory() as tmp:
-                path = os.path.join(tmp, "oracle_T.npy")
-                res = _oracle_baseline(args.config, 1, save_to=path)
-                T_or = np.load(path)
-            v = res["n"] * n_int * P / res["seconds"]
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "one macro step of the same workload, single-threaded numpy/scipy"}
-            acc = line.setdefault("accuracy", {})
-            for prec in ([args.precision, "fp64"] if compare else [args.precision]):
-                g = make(prec)
-                g.set_execution(False)
-                g.step(report=True)
-                acc[f"rel_l2_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature(), T_or)
-                acc[f"rel_l2_rise_{prec}_vs_oracle_step1"] = _rel_l2(g.temperature() - m.T0, T_or - m.T0)
-                g.close()
+            res = _oracle_finish(oracle["main"])
+            if args.config in SAMPLE_SUBSTEPS:
+                S = SAMPLE_SUBSTEPS[args.config]
+                v = res["n"] * S / float(np.mean(res["seconds"]))
+                sample = _sample_desc(m, n_int, S, res)
+            else:
+                v = units_per_step / float(np.mean(res["seconds"]))
+                sample = "one macro step of the same workload, single-threaded numpy/scipy"
+                acc = line.setdefault("accuracy", {})
+                acc.update(_oracle_accuracy(m, args.precision, compare, local, np.load(os.path.join(tmp, "main.npy"))))
+            line["cpu_baseline"] = _cpu_baseline_line(v, "1 (BLAS threads = 1)", sample, host)
         except Exception as e:  # reported, not fatal
-            line["cpu_baseline"] = {"error": str(e)[:200]}
+            line["cpu_baseline"] = {"error": str(e)[:300]}
+        if "side" in oracle:
+            try:
+                ms_, ni_, _ = _workload(side_idx)
+                res = _oracle_finish(oracle["side"])
+                side_units = ms_.n_dof * ni_ * ms_.scheme.P
+                line["workload_313k"]["cpu_baseline"] = _cpu_baseline_line(
+                    side_units / float(np.mean(res["seconds"])), "1 (BLAS threads = 1)",
+                    "one full macro step of the 313,646-DOF workload, single-threaded numpy/scipy", host)
+                line["workload_313k"].setdefault("accuracy", {}).update(
+                    _oracle_accuracy(ms_, args.precision, compare, local, np.load(os.path.join(tmp, "side.npy"))))
+            except Exception as e:
+                line["workload_313k"]["cpu_baseline"] = {"error": str(e)[:300]}
     print(json.dumps(line), flush=True)
 
 
@@ -789,8 +1048,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
-    ap.add_argument("--config", type=int, default=1,
-                    help="0/1/2: one machine (1 = the headline workload); 3: the batch of 64 machines; "
+    ap.add_argument("--config", type=int, default=2,
+                    help="0/1/2: one machine (2 = the headline workload, the largest single-GPU one); "
+                         "3: the batch of 64 machines; "
                          "4: serving (Poisson arrivals); 5: convergence order and residual decay on the "
                          "reduced problem of Sec. 4")
     ap.add_argument("--machines", type=int, default=None, help="config 3: use only the first machines")
@@ -798,6 +1058,8 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="config 2: skip the 313,646-DOF workload measured beside the headline")
     ap.add_argument("--no-single-rate", action="store_true",
                     help="skip the single-rate SDC comparison (Sec. 3) on the same machine")
     ap.add_argument("--no-ie", action="store_true",

@@ -228,6 +228,13 @@ sdc_status sdc_set_cg_unroll(sdc_ctx* ctx, int pairs);
  * identical for every cluster size. */
 sdc_status sdc_set_contact_cluster(sdc_ctx* ctx, int max_ctas);
 
+/* Polls of each bounded wait of the contact substep loop's exchange before it gives up
+ * (0 = the default, 2^24). A loop whose wait gives up stops exchanging, drains the copies
+ * still addressed to it and ends the step with SDC_ERR_TIMEOUT; the context stays usable.
+ * For tests of that path (a budget of a few polls gives up on waits that would complete)
+ * and for callers that prefer an early error to a long wait. SDC_ERR_ARG if polls < 0. */
+sdc_status sdc_set_wait_limit(sdc_ctx* ctx, int64_t polls);
+
 /* Measurement aid for eager execution (sdc_set_execution(ctx, 1)): when on,
  * every kernel launch of a step is bracketed by CUDA events on the
  * context's stream and each step waits for its launches, summing the
@@ -359,6 +366,18 @@ sdc_status sdc_set_stationary_state(sdc_ctx* ctx, double t0, double rtol, int32_
  * x_dev holds the initial guess on entry. Waits; *iters receives the
  * iteration count (may be NULL). */
 sdc_status sdc_solve(sdc_ctx* ctx, double dtau, const double* b_dev, double* x_dev, int32_t* iters);
+
+/* Measurement aid for the implicit solves of Algorithms 1 and 2 (the CG of the implicit
+ * stage; its arithmetic is that of sdc_solve): the device time of n_iters consecutive CG
+ * iterations on (diag(m) + dtau K) x = b, b = g and x0 = T(t_n), in the scheme's precision
+ * (FP32 inner iterations for SDC_MIXED_FP32), launched as one CUDA graph of the same kernels,
+ * grids and launch order as a macro step's CG loop. The stop test is disabled so that every
+ * iteration works; spmv_only != 0 launches only the SpMV kernel of each iteration. *ms
+ * receives the milliseconds of the n_iters iterations (CUDA events on the context's stream
+ * around that graph; an initial-residual kernel runs before the first event). Uses the
+ * step's work buffers, not T(t_n); waits. SDC_ERR_ARG unless 1 <= n_iters <= 4096, dtau > 0.
+ * Needs sdc_set_temperature. */
+sdc_status sdc_time_cg_iterations(sdc_ctx* ctx, double dtau, int32_t n_iters, int32_t spmv_only, float* ms);
 
 /* f^E(T, t) on all DOFs (zero away from the contact): Sec. 2, the contact
  * and friction terms of Eq. femContFix / femContMov. */

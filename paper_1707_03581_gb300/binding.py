@@ -94,6 +94,8 @@ _SIGS = {
     "sdc_get_system": (C.c_int, [_vp, _i64p, _i64p, _f64p, _f64p, _f64p]),
     "sdc_apply_operator": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
+    "sdc_set_wait_limit": (C.c_int, [_vp, C.c_int64]),
+    "sdc_time_cg_iterations": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_float)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
     "sdc_poll": (C.c_int, [_vp, C.POINTER(C.c_int)]),
@@ -417,6 +419,17 @@ class Solver:
         self._call("sdc_apply_operator", dtau, _vp(x.data_ptr()), _vp(y.data_ptr()))
         return y
 
+    def set_wait_limit(self, polls: int):
+        """Polls of each bounded exchange wait of the contact loop (0 = default; sdc_set_wait_limit)."""
+        self._call("sdc_set_wait_limit", int(polls))
+
+    def time_cg_iterations(self, dtau: float, n_iters: int, spmv_only: bool = False) -> float:
+        """Device milliseconds of n_iters consecutive CG iterations of the implicit stage in
+        the scheme's precision, launched as one CUDA graph (sdc_time_cg_iterations)."""
+        ms = C.c_float(0.0)
+        self._call("sdc_time_cg_iterations", float(dtau), int(n_iters), 1 if spmv_only else 0, C.byref(ms))
+        return float(ms.value)
+
     def solve(self, dtau, b, x0):
         b = self._dev(b)
         x = self._dev(x0).clone()
@@ -451,6 +464,12 @@ class Solver:
         2-element float64 CUDA tensor `out`, without any device allocation
         (see sdc_heat_totals_noalloc: fixed scratch, at most 8,388,608 DOF;
         concurrent calls on one device race)."""
+        if not (getattr(out, "is_cuda", False) and out.device.index == self.device):
+            raise ValueError(f"out must be a CUDA tensor on cuda:{self.device}")
+        import torch
+
+        if out.dtype != torch.float64 or out.numel() < 2 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of at least 2 elements")
         self._call("sdc_heat_totals_noalloc", _vp(int(T_ptr)), _vp(out.data_ptr()))
         return out
 

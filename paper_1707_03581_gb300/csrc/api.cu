@@ -102,6 +102,8 @@ struct sdc_ctx {
     double* fe_std[2][MAX_M + 1] = {};  // single-rate SDC: f^E at the standard nodes, by iterate
     int in_batch = 0;               // batches holding this context (their members run without side branches)
     void* iface_rep = nullptr;      // their buffers
+    int* iface_sent = nullptr;      // chunks each CTA of the loop's cluster sent (per launch)
+    long long poll_limit = IFACE_POLLS;  // sdc_set_wait_limit
     size_t iface_smem = 0;          // its dynamic shared memory per CTA
     CouplingOp E{};
     double *w_Stil = nullptr, *w_Semb = nullptr, *w_Shat = nullptr, *w_emb = nullptr, *w_slot = nullptr;
@@ -919,6 +921,7 @@ void alloc_scheme_buffers(sdc_ctx* c) {
                 c->fe_std[s][j] = j < c->nondeg[0] ? fe0 : (s == 0 ? dalloc_n<double>(c, c->pool_scheme, NI) : nullptr);
         for (int j = c->nondeg[0]; j <= M; ++j) c->fe_std[1][j] = dalloc_n<double>(c, c->pool_scheme, NI);
     }
+    c->iface_sent = dalloc_n<int>(c, c->pool_scheme, IFACE_MAX_CLUSTER);
     c->cpre = dalloc_n<double>(c, c->pool_scheme, (size_t)P * NI);
     c->fst = dalloc_n<double>(c, c->pool_scheme, NI);
     pick_iface_cluster(c);
@@ -1074,6 +1077,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.status = &c->st->status;
         ia.dT = c->precision == SDC_MIXED_FP32 ? c->dTv : nullptr;
         ia.rep_global = c->iface_rep;
+        ia.sent = c->iface_sent;
+        ia.poll_limit = c->poll_limit;
         ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global),
                           (unsigned)c->iface_cluster, (unsigned)iface_loop_threads(c->iface_chunk, c->iface_global),
                           c->iface_smem,
@@ -1744,6 +1749,14 @@ sdc_status sdc_set_contact_cluster(sdc_ctx* c, int max_ctas) {
     });
 }
 
+sdc_status sdc_set_wait_limit(sdc_ctx* c, int64_t polls) {
+    return guarded(c, [&] {
+        require(polls >= 0, SDC_ERR_ARG, "polls must be >= 0");
+        c->poll_limit = polls == 0 ? IFACE_POLLS : (long long)polls;
+        c->graph_ready = false;
+    });
+}
+
 sdc_status sdc_set_kernel_timing(sdc_ctx* c, int on) {
     return guarded(c, [&] {
         c->timing = on ? 1 : 0;
@@ -1957,6 +1970,75 @@ sdc_status sdc_solve(sdc_ctx* c, double dtau, const double* b, double* x, int32_
     });
 }
 
+sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int32_t spmv_only, float* ms) {
+    return guarded(c, [&] {
+        require(n_iters >= 1 && n_iters <= 4096, SDC_ERR_ARG, "n_iters must be in 1..4096");
+        require(ms != nullptr, SDC_ERR_ARG, "ms is NULL");
+        require(dtau > 0.0, SDC_ERR_ARG, "dtau must be positive");
+        ensure_ready(c);
+        // the implicit-stage system with b = g and x0 = T_n: a nonzero residual; negative
+        // tolerances and no iteration cap keep every iteration working (no stop test passes)
+        const bool mixed = c->precision == SDC_MIXED_FP32;
+        MixArgs ma = mix_args(c, dtau, 0, 1.0, 1);
+        ma.rtol2 = -1.0;
+        ma.inner_rtol2 = -1.0;
+        ma.max_iter = 1 << 30;
+        ma.max_refine = 1 << 30;
+        CgArgs ca = cg_args(c, dtau, 0, 1.0, 1 << 30);
+        ca.rtol2 = -1.0;
+        RhsArgs r{};
+        r.mode = RHS_GIVEN;
+        r.b_in = c->d_genv;
+        r.x0 = c->Tn;
+        r.pos = c->C.pos;
+        cudaGraph_t g[2];
+        SDC_CUDA_TRY(cudaGraphCreate(&g[0], 0));
+        std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> g0(g[0], &cudaGraphDestroy);
+        SDC_CUDA_TRY(cudaGraphCreate(&g[1], 0));
+        std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> g1(g[1], &cudaGraphDestroy);
+        Chain init(g[0]), body(g[1]);
+        if (mixed) init.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, ma, r);
+        else init.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, ca, r);
+        for (int k = 0; k < n_iters; ++k) {
+            if (mixed) {
+                body.kernel(ma.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, ma);
+                if (!spmv_only)
+                    body.kernel(ma.defer ? k_mx_update : k_mx_update_red,
+                                ma.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, ma);
+            } else {
+                body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, ca);
+                if (!spmv_only) body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, ca);
+            }
+        }
+        cudaGraphExec_t ex[2] = {nullptr, nullptr};
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        auto release = [&] {
+            for (auto e : ex)
+                if (e) cudaGraphExecDestroy(e);
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+        };
+        try {
+            for (int k = 0; k < 2; ++k) SDC_CUDA_TRY(cudaGraphInstantiate(&ex[k], g[k], 0));
+            for (int k = 0; k < 2; ++k) SDC_CUDA_TRY(cudaEventCreate(&ev[k]));
+            SDC_CUDA_TRY(cudaGraphLaunch(ex[0], c->stream));
+            SDC_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
+            SDC_CUDA_TRY(cudaGraphLaunch(ex[1], c->stream));
+            SDC_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
+            SDC_CUDA_TRY(cudaEventSynchronize(ev[1]));
+            SDC_CUDA_TRY(cudaEventElapsedTime(ms, ev[0], ev[1]));
+        } catch (...) {
+            release();
+            throw;
+        }
+        release();
+        // the work buffers and scalars are the step's scratch; the status word may hold what
+        // the uncapped loop left: clear it
+        SDC_CUDA_TRY(cudaMemsetAsync(&c->st->status, 0, sizeof(int), c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+}
+
 sdc_status sdc_set_stationary_state(sdc_ctx* c, double t0, double rtol, int32_t max_iter, int32_t* iters) {
     return guarded(c, [&] {
         require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
@@ -2082,6 +2164,18 @@ unsigned char* noalloc_scratch(int device) {
     return static_cast<unsigned char*>(g_noalloc_addr[device]);
 }
 
+// True if p is device memory of GPU `device` (cudaPointerGetAttributes allocates
+// nothing). Host, pinned-host and unregistered pointers, and other GPUs' memory, are
+// refused before a kernel could write through them.
+bool on_device(const void* p, int device) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+
 // Makes `device` current for the scope and restores the caller's device.
 struct CurrentDevice {
     int prev = -1;
@@ -2104,13 +2198,18 @@ extern "C" sdc_status sdc_heat_totals_noalloc(sdc_ctx* c, const double* T_dev, d
         require(c->n <= NOALLOC_MAX_DOF, SDC_ERR_ARG,
                 "sdc_heat_totals_noalloc handles at most 8,388,608 DOF (its fixed scratch holds 32,768 "
                 "block partials); use sdc_get_heat_totals for larger models");
+        require(on_device(T_dev, c->device), SDC_ERR_ARG,
+                "T_dev is not device memory of the context's GPU");
+        require(on_device(heat_dev, c->device), SDC_ERR_ARG,
+                "heat_dev is not device memory of the context's GPU");
         CurrentDevice on(c->device);
         unsigned char* base = noalloc_scratch(c->device);
         double* partials = reinterpret_cast<double*>(base);
         unsigned int* counter = reinterpret_cast<unsigned int*>(base + NOALLOC_PARTIAL_BYTES);
         SDC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), c->stream));
-        k_heat<<<blocks_for(c->n, RED_BLOCK), RED_BLOCK, 0, c->stream>>>(c->d_mass, T_dev, c->n, c->n_fix, partials,
-                                                                          counter, heat_dev);
+        // one block at least, as the step's own ledger launch: a model without DOFs gets zeros
+        k_heat<<<blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK), RED_BLOCK, 0, c->stream>>>(
+            c->d_mass, T_dev, c->n, c->n_fix, partials, counter, heat_dev);
         SDC_CUDA_TRY(cudaGetLastError());
     });
 }

@@ -1321,9 +1321,9 @@ __global__ void k_iface_prep(PrepArgs a) {
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // Wait until the mbarrier at `bar` completes the phase of parity `parity`,
-// for at most ~2^24 polls; returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (long it = 0; it < (1l << 24); ++it) {
+// for at most `polls` polls; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long polls) {
+    for (long long it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile(
             "{ .reg .pred P1; mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
@@ -1333,6 +1333,49 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         if (done) return true;
     }
     return false;
+}
+
+// Copies still addressed to a CTA whose exchange wait gave up, by the thread that armed its
+// barriers. The CTA sent (and armed the barrier phase of) substeps 1..n_sent and stopped;
+// its waits completed up to n_sent - 1. A peer sends the chunk of substep p only after its
+// own wait of substep p - 1 completed, which needs this CTA's chunk p - 1; so peers sent this
+// CTA chunks of substeps n_sent and n_sent + 1 at most, and `sent` (each CTA's count,
+// final once every CTA passed the cluster barrier before this call) says which. The phase of
+// substep n_sent was armed for all cs - 1 peers: the bytes of peers that never sent are
+// completed here, so that the phase completes exactly when the copies that were sent have
+// landed. The phase of substep n_sent + 1 was never armed: it is armed for the copies that
+// were sent. Waiting for both phases leaves no copy into this CTA in flight. Returns false if
+// a drain wait gave up (an issued copy that never landed).
+__device__ bool iface_drain(const int* sent, int rank, int cs, int n_sent, int P, unsigned bytes,
+                            const unsigned long long* mbar) {
+    auto peers_sent = [&](int p) {
+        int k = 0;
+        for (int q = 0; q < cs; ++q)
+            if (q != rank && *(volatile const int*)(sent + q) >= p) ++k;
+        return k;
+    };
+    // completed phases of barrier b: the substeps 1..n_sent - 1 of parity b
+    auto done_phases = [&](int b) { return b == 1 ? n_sent / 2 : (n_sent - 1) / 2; };
+    bool ok = true;
+    {
+        const int b = n_sent & 1;
+        const unsigned bar = smem_addr(&mbar[b]);
+        const unsigned missing = (unsigned)(cs - 1 - peers_sent(n_sent)) * bytes;
+        if (missing)
+            asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(missing) : "memory");
+        ok = mbar_wait(bar, (unsigned)(done_phases(b) & 1), IFACE_DRAIN_POLLS) && ok;
+    }
+    if (n_sent + 1 <= P) {
+        const int b = (n_sent + 1) & 1;
+        const unsigned bar = smem_addr(&mbar[b]);
+        const unsigned arriving = (unsigned)peers_sent(n_sent + 1) * bytes;
+        if (arriving) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(arriving)
+                         : "memory");
+            ok = mbar_wait(bar, (unsigned)(done_phases(b) & 1), IFACE_DRAIN_POLLS) && ok;
+        }
+    }
+    return ok;
 }
 
 // The P explicit substeps of one interval on the contact DOFs (Algorithm 1 /
@@ -1349,6 +1392,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 // is needed inside the loop. A CTA overwrites a buffer only after it has
 // received every peer's next chunk, which each peer sends only after its
 // gather from that buffer (program order), so the two buffers suffice.
+// Waits are bounded (IfaceArgs::poll_limit). A CTA in which a wait gave up
+// stops exchanging (it sends and arms nothing more), reports SDC_ERR_TIMEOUT,
+// and before exit drains the copies still addressed to it (iface_drain); a
+// closing cluster barrier keeps every CTA resident until all copies from and
+// into its shared memory have landed.
 //   FP64 (MIX = false): the replica holds T; f^E = cst + sum_k coef_k T_k.
 //   Mixed (MIX = true): the replica holds the FP32 deviations T - T_{m-1}
 //   (mK over an interval) and f^E = base_p + sum_k coef32_k dT_k, base_p =
@@ -1445,7 +1493,9 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     }
     unsigned phase[2] = {0u, 0u};
     const unsigned bytes = (unsigned)(chunk * sizeof(V));
-    bool timed_out = false;
+    bool my_to = false;   // this thread's exchange wait gave up
+    bool cta_to = false;  // a wait of this CTA gave up: it stopped exchanging after n_sent chunks
+    int n_sent = 0;       // substeps whose chunk this CTA sent and whose barrier phase it armed
     for (int p = 1; p <= P; ++p) {
         const int b = p & 1;
         V* buf = rep + (size_t)b * cs * chunk;
@@ -1472,7 +1522,11 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         } else {
         // generic-proxy writes of the own chunk become visible to the bulk copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        // the CTA stops as a whole once a wait of any of its threads gave up
+        if (__syncthreads_or(my_to)) {
+            cta_to = true;
+            break;
+        }
         if (threadIdx.x < (unsigned)cs) {  // lane q sends the own chunk to CTA q, all at once
             const int q = (int)threadIdx.x;
             const unsigned src = smem_addr(buf + rank * chunk);
@@ -1490,7 +1544,8 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes * (cs - 1))
                              : "memory");
         }
-        if (!timed_out && !mbar_wait(smem_addr(&mbar[b]), phase[b])) timed_out = true;
+        n_sent = p;
+        if (!mbar_wait(smem_addr(&mbar[b]), phase[b], a.poll_limit)) my_to = true;
         phase[b] ^= 1u;
         }
 #pragma unroll
@@ -1503,7 +1558,10 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
             ih[r] = fma(s_shat[p], fe[r], ih[r]);
         }
     }
-    if (timed_out) atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+    if constexpr (!GL) {
+        if (!cta_to) cta_to = __syncthreads_or(my_to);  // a wait of the last substep
+        if (cta_to && threadIdx.x == 0) atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+    }
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const int i = own[r];
@@ -1512,7 +1570,16 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         if (a.dT) a.dT[C.dof[i]] = (float)(T[r] - T0[r]);
         a.ihat_new[i] = ih[r];
     }
-    // no CTA may exit while its shared memory can still be a copy destination
+    if constexpr (!GL) {
+        if (threadIdx.x == 0) a.sent[rank] = n_sent;
+        // every CTA has issued every copy it will issue, and its count in a.sent is visible
+        cluster.sync();
+        // a CTA whose waits all completed has received every copy addressed to it
+        if (cta_to && threadIdx.x == 0 &&
+            !iface_drain(a.sent, rank, cs, n_sent, P, bytes, mbar))
+            atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+    }
+    // no CTA exits while a bulk copy from or into its shared memory can be in flight
     cluster.sync();
 }
 

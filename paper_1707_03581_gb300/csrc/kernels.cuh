@@ -239,7 +239,14 @@ struct IfaceArgs {
     float* dT;                      // mixed: T_m - T_{m-1} on the contact rows (output), or NULL
     void* rep_global;               // [2][cs * chunk] replica buffers of the global-replica loop
     int* status;                    // sticky status word (SDC_ERR_TIMEOUT if an exchange wait gives up)
+    int* sent;                      // [IFACE_MAX_CLUSTER] chunks each CTA of the cluster sent (per launch)
+    long long poll_limit;           // polls of an exchange wait before it gives up
 };
+
+// Polls of an exchange wait of the contact loop (sdc_set_wait_limit overrides it), and of
+// the waits that drain the copies still addressed to a CTA after a wait gave up.
+constexpr long long IFACE_POLLS = 1ll << 24;
+constexpr long long IFACE_DRAIN_POLLS = 1ll << 24;
 
 struct ResidualArgs {
     const double* mass;

@@ -262,7 +262,7 @@ def _res_machine(name, r, **kw):
                          (r // 2, r // 2, int(round(0.75 * r))), **kw)
 
 
-def machine_config(idx: int, seed: int = 0, truncate: Optional[int] = None):
+def machine_config(idx: int, seed: int = 0, truncate: Optional[int] = None, select=None):
     """The five synthetic workloads, as Machine objects (a list for index 3).
 
     0: 8x8x20 stand + 4x4x6 stock (1,876 DOF), Lobatto M=3, 3 sweeps, P=20,
@@ -274,7 +274,8 @@ def machine_config(idx: int, seed: int = 0, truncate: Optional[int] = None):
        Radau IIA M=4, 4 sweeps, P=40, dt = 1 s, 60 s, motion as config 0.
     3: 64 machines; per machine r ~ {16,24,32,48,64}, then A, Per, q0 ~
        U(2.5e4, 7.5e4) W/m^2; scheme as config 0; 120 s each. `truncate`
-       keeps only the first machines.
+       keeps only the first machines; `select` (indices) builds only those
+       machines, in index order (the draws of all 64 are taken either way).
     4: the serving mix: machines are drawn like config 3 (see `serving_requests`).
     """
     if idx == 0:
@@ -305,12 +306,41 @@ def machine_config(idx: int, seed: int = 0, truncate: Optional[int] = None):
             amp = float(rng.uniform(0.1, 0.3))
             per = float(rng.uniform(1.0, 4.0))
             q0 = float(rng.uniform(2.5e4, 7.5e4))
-            if i < n:
+            if i < n and (select is None or i in select):
                 out.append(_res_machine(f"c4-m{i}-r{r}", r, amp=amp, period=per, q0=q0,
                                         scheme=Scheme("lobatto", 3, 20, 3, 0, 1.0),
                                         horizon=120.0))
         return out
     raise ValueError(f"no machine list for config index {idx}")
+
+
+def per_hex_machine(name: str, stand_n, stock_n, seed: int = 0, scheme: Optional[Scheme] = None, **kw) -> Machine:
+    """A machine with one conductivity per hexahedron, exp(U(ln 40, ln 60)) W/(m K), drawn
+    from default_rng(seed) for the stand's hexes then the stock's, in hex order: the
+    material recipe of config 2 at any mesh size (default scheme: config 2's Radau IIA
+    M=4, 4 sweeps, P=40, dt = 1 s)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(40.0), np.log(60.0)
+    n_stand = int(np.prod(stand_n))
+    n_stock = int(np.prod(stock_n))
+    k_stand = np.exp(rng.uniform(lo, hi, n_stand))
+    k_stock = np.exp(rng.uniform(lo, hi, n_stock))
+    return build_machine(name, stand_n, stock_n, k_per_hex_stand=k_stand, k_per_hex_stock=k_stock,
+                         scheme=scheme if scheme is not None else Scheme("radau_right", 4, 40, 4, 0, 1.0), **kw)
+
+
+def batch_resolutions(seed: int = 0):
+    """Index of the first machine of each stand resolution r in the batch of config 3:
+    {r: index}, from the same draws as machine_config(3, seed)."""
+    rng = np.random.default_rng(seed)
+    first = {}
+    for i in range(64):
+        r = int(rng.choice([16, 24, 32, 48, 64]))
+        rng.uniform(0.1, 0.3)
+        rng.uniform(1.0, 4.0)
+        rng.uniform(2.5e4, 7.5e4)
+        first.setdefault(r, i)
+    return first
 
 
 def serving_requests(lam: float, n_requests: int = 500, seed: int = 0, pool: int = 64):

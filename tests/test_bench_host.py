@@ -48,3 +48,29 @@ def test_below_every_run_is_extrapolated_from_the_last_two():
     eta = np.log([runs[-2]["eta"], runs[-1]["eta"]])
     slope = (eta[1] - eta[0]) / (e[1] - e[0])
     assert got["eta"] == pytest.approx(np.exp(eta[1] + slope * (np.log(err) - e[1])), rel=1e-12)
+
+
+def test_oracle_sample_runs_the_predictor_interval():
+    # the bounded CPU sample of the largest workload, here on the 1,876-DOF machine: Algorithm 1
+    # on the first interval of positive length, cut after the given number of substeps
+    res = bench._oracle_finish(bench._oracle_sample(0, substeps=3, reps=2, warmup=1))
+    assert len(res["seconds"]) == 2 and all(t > 0 for t in res["seconds"])
+    assert res["substeps"] == 3 and res["n"] == 1876
+    assert res["interval"] == 2  # Lobatto: the first interval has zero length
+
+
+def test_traffic_comes_from_a_profile_of_the_current_kernel(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1707_03581_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "kernels.cu").write_text("// kernel source\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench._kernels_sha()
+    (tmp_path / "profiles" / "k_a.md").write_text(
+        f"# summary\nbench-traffic: kernel=k_a n_dof=100 dram_bytes=1234.5 kernels_cu_sha256={sha}\n")
+    (tmp_path / "profiles" / "k_b.md").write_text(
+        "bench-traffic: kernel=k_b n_dof=100 dram_bytes=99 kernels_cu_sha256=0000000000000000\n")
+    assert bench._profile_traffic("k_a", 100)[0] == 1234.5
+    assert bench._profile_traffic("k_a", 101)[0] is None
+    t, note = bench._profile_traffic("k_b", 100)
+    assert t is None and "changed" in note
