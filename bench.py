@@ -564,9 +564,15 @@ def _measure(m, n_int, args, local, torch, flush, world, precision, compare, e2e
 
     from paper_1707_03581_gb300 import Solver
 
+    tune = {}
+
     def make(prec):
         sv = Solver(local)
         sv.set_machine(m, precision=prec)
+        if not args.no_tune and not args.eager:
+            t = time.perf_counter()
+            tune[prec] = sv.autotune(trial_steps=3)
+            tune[prec]["seconds"] = time.perf_counter() - t
         if args.eager:
             sv.set_execution(True)
         return sv
@@ -577,7 +583,7 @@ def _measure(m, n_int, args, local, torch, flush, world, precision, compare, e2e
     t_setup = time.perf_counter() - t_setup
     stream = s.stream
     out = {"n": s.n, "nnz": s.nnz, "n_contact": s.n_contact, "setup_s": t_setup,
-           "units_per_step": s.n * n_int * m.scheme.P}
+           "units_per_step": s.n * n_int * m.scheme.P, "autotune": tune}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.step(report=True)
@@ -677,7 +683,8 @@ def _workload_summary(m, n_int, mres, args, precision):
            "refinements_per_step": mres["rep"]["refinements_total"],
            "contact_cluster": mres["rep"]["contact_cluster"],
            "eager_ms_per_step": sum(mres["eager_ms"]) / len(mres["eager_ms"]),
-           "setup_s": mres["setup_s"]}
+           "setup_s": mres["setup_s"],
+           "autotune": mres["autotune"] or "off (--no-tune)"}
     if "ms64" in mres:
         ms64 = sum(mres["ms64"]) / args.steps
         out["fp64"] = {"value": units / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
@@ -838,9 +845,14 @@ def run_batch(args, rank, world):
     n_int = sc.M - 1 if sc.nodes == "lobatto" else sc.M
     t_setup = time.perf_counter()
     solvers = []
+    tuned = {}
     for mach in machines:
         s = Solver(local, own_stream=True)
         s.set_machine(mach, precision=args.precision)
+        if not args.no_tune:
+            rep = s.autotune(trial_steps=3)
+            if not rep["cached"]:
+                tuned[f"{s.n} DOF"] = rep
         solvers.append(s)
     t_setup = time.perf_counter() - t_setup
     dofs = np.array([s.n for s in solvers])
@@ -897,6 +909,7 @@ def run_batch(args, rank, world):
         "gain_vs_sequential": ms_seq / ms,
         "host_wall_ms_per_step": 1e3 * wall / args.steps,
         "setup_s": t_setup,
+        "autotune": tuned or "off (--no-tune)",
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -1058,6 +1071,8 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch options (no sdc_autotune before timing)")
     ap.add_argument("--no-extra", action="store_true",
                     help="config 2: skip the 313,646-DOF workload measured beside the headline")
     ap.add_argument("--no-single-rate", action="store_true",

@@ -78,6 +78,9 @@ typedef struct {
     int32_t contact_cluster;                /* CTAs of the thread-block cluster that runs the
                                                contact substeps                               */
     int32_t pad_;
+    double true_residual_max;               /* largest ||b - (m x + dtau K x)|| / ||b|| of the step's
+                                               mixed-precision solves, with the FP64 operator, if
+                                               enabled (sdc_set_diagnostics bit 1); else -1    */
 } sdc_step_report;
 
 /* Heat ledger (all FP64). */
@@ -173,9 +176,14 @@ sdc_status sdc_assemble(sdc_ctx* ctx);
 sdc_status sdc_set_scheme(sdc_ctx* ctx, sdc_nodes nodes, int M, int P, int sweeps, int window,
                           double dt, double cg_rtol, int cg_max_iter, sdc_precision precision);
 
-/* Enable (1) or disable (0) the FP64 SDC residual r^k of Eq. residual after
- * the predictor and every sweep (costs extra passes). */
-sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int residuals);
+/* Diagnostics of each macro step, a bit set (costs extra passes):
+ *  bit 0 (1): the FP64 SDC residual r^k of Eq. residual after the predictor and every sweep
+ *             (MRSDC only; SDC_ERR_ARG with another stepper);
+ *  bit 1 (2): the true residual of every mixed-precision implicit solve (Algorithms 1 and 2:
+ *             (diag(m) + dtau K) x = b), ||b - (m x + dtau K x)||_2 / ||b||_2 with the FP64
+ *             operator and iterate, after the refinement stopped on its carried residual;
+ *             the step report's true_residual_max holds the largest. No effect on results. */
+sdc_status sdc_set_diagnostics(sdc_ctx* ctx, int flags);
 
 /* Time stepper of sdc_step.
  * SDC_STEPPER_MRSDC (default): IMEX multi-rate SDC (Algorithms 1 and 2).
@@ -227,6 +235,38 @@ sdc_status sdc_set_cg_unroll(sdc_ctx* ctx, int pairs);
  * bound whose cluster fits on the device. For tuning and tests: results are
  * identical for every cluster size. */
 sdc_status sdc_set_contact_cluster(sdc_ctx* ctx, int max_ctas);
+
+/* Blocks a SM of the FP32 CG update's one-wave grid (mixed precision, grids of at most 2048
+ * blocks of 256 rows); 0 (default) = as many as fit. Results are identical; SDC_ERR_ARG
+ * outside 0..32. */
+sdc_status sdc_set_update_blocks(sdc_ctx* ctx, int blocks_per_sm);
+
+/* Launch options picked by sdc_autotune. */
+typedef struct {
+    int32_t cg_unroll;            /* (SpMV, update) pairs per CG loop body (sdc_set_cg_unroll)     */
+    int32_t update_blocks_per_sm; /* FP32 update grid (sdc_set_update_blocks)                       */
+    int32_t contact_cluster_cap;  /* cap on the contact loop's cluster (sdc_set_contact_cluster; 0 =
+                                     automatic)                                                     */
+    int32_t contact_cluster;      /* the cluster size that results                                 */
+    int32_t contact_global;       /* 1: replicas in global memory                                  */
+    int32_t graph_branches;       /* sdc_set_graph_branches                                        */
+    int32_t trials;               /* option sets timed (0 when taken from the cache)               */
+    int32_t cached;               /* 1: picks of an earlier context of the same shape              */
+    double ms_default;            /* ms per macro step with the options the context had (-1 cached)*/
+    double ms_tuned;              /* ms per macro step with the picks (-1 cached)                   */
+} sdc_tune_report;
+
+/* Autotuner: picks the launch options above for this context from timed macro steps in
+ * graph execution, and sets them. Each option set is timed on the same trial_steps macro
+ * steps (0 = 3) from the context's current state, which is saved first and restored after,
+ * so the call leaves T(t_n), the time and the heat ledger as they were. Coordinate descent
+ * from the current options; a candidate must be 1 % faster to be taken. Every option leaves
+ * results bitwise unchanged. Picks are cached in the process by the problem's shape
+ * (device, DOFs, nonzeros, contact DOFs, precision, stepper, nodes, M, P, sweeps): later
+ * contexts of that shape take them without trials. Needs sdc_set_temperature; allocates
+ * n_dof doubles for the duration of the call; SDC_ERR_STATE in eager execution; rep may be
+ * NULL. */
+sdc_status sdc_autotune(sdc_ctx* ctx, int32_t trial_steps, sdc_tune_report* rep);
 
 /* Polls of each bounded wait of the contact substep loop's exchange before it gives up
  * (0 = the default, 2^24). A loop whose wait gives up stops exchanging, drains the copies

@@ -35,7 +35,7 @@ class StepReport(C.Structure):
                 ("refinements_total", C.c_int32), ("status", C.c_int32), ("kernel_launches", C.c_int32),
                 ("residual", C.c_double * (MAX_SWEEPS + 1)),
                 ("heat_stand", C.c_double), ("heat_stock", C.c_double),
-                ("contact_cluster", C.c_int32), ("pad_", C.c_int32)]
+                ("contact_cluster", C.c_int32), ("pad_", C.c_int32), ("true_residual_max", C.c_double)]
 
     def as_dict(self):
         return {"t": self.t, "sweeps": self.sweeps, "n_solves": self.n_solves,
@@ -44,7 +44,16 @@ class StepReport(C.Structure):
                 "kernel_launches": self.kernel_launches,
                 "residual": [r for r in self.residual[: self.sweeps + 1]],
                 "heat_stand": self.heat_stand, "heat_stock": self.heat_stock,
-                "contact_cluster": self.contact_cluster}
+                "contact_cluster": self.contact_cluster, "true_residual_max": self.true_residual_max}
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("cg_unroll", C.c_int32), ("update_blocks_per_sm", C.c_int32), ("contact_cluster_cap", C.c_int32),
+                ("contact_cluster", C.c_int32), ("contact_global", C.c_int32), ("graph_branches", C.c_int32),
+                ("trials", C.c_int32), ("cached", C.c_int32), ("ms_default", C.c_double), ("ms_tuned", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Heat(C.Structure):
@@ -95,6 +104,8 @@ _SIGS = {
     "sdc_apply_operator": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "sdc_solve": (C.c_int, [_vp, C.c_double, _vp, _vp, C.POINTER(C.c_int32)]),
     "sdc_set_wait_limit": (C.c_int, [_vp, C.c_int64]),
+    "sdc_set_update_blocks": (C.c_int, [_vp, C.c_int]),
+    "sdc_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(TuneReport)]),
     "sdc_time_cg_iterations": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_float)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
@@ -323,8 +334,10 @@ class Solver:
         self._call("sdc_get_kernel_times", cap, names, n, ms, C.byref(k))
         return {names[i].decode(): (n[i], ms[i]) for i in range(min(k.value, cap))}
 
-    def set_diagnostics(self, residuals: bool):
-        self._call("sdc_set_diagnostics", 1 if residuals else 0)
+    def set_diagnostics(self, residuals: bool, true_residual: bool = False):
+        """FP64 SDC residual of every sweep (Eq. residual) and/or the FP64 true residual of
+        every mixed-precision solve (sdc_set_diagnostics)."""
+        self._call("sdc_set_diagnostics", (1 if residuals else 0) | (2 if true_residual else 0))
 
     def set_temperature(self, T=None, T_uniform=20.0, t0=0.0):
         if T is None:
@@ -418,6 +431,17 @@ class Solver:
         y = self._torch.empty_like(x)
         self._call("sdc_apply_operator", dtau, _vp(x.data_ptr()), _vp(y.data_ptr()))
         return y
+
+    def set_update_blocks(self, blocks_per_sm: int):
+        """Blocks a SM of the FP32 CG update's grid (0 = as many as fit; sdc_set_update_blocks)."""
+        self._call("sdc_set_update_blocks", int(blocks_per_sm))
+
+    def autotune(self, trial_steps: int = 3) -> dict:
+        """Pick and set the launch options from timed trial steps (sdc_autotune); the state is
+        left as it was. Returns the picks and the timings."""
+        rep = TuneReport()
+        self._call("sdc_autotune", int(trial_steps), C.byref(rep))
+        return rep.as_dict()
 
     def set_wait_limit(self, polls: int):
         """Polls of each bounded exchange wait of the contact loop (0 = default; sdc_set_wait_limit)."""

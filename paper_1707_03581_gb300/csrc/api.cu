@@ -11,7 +11,9 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -56,6 +58,7 @@ struct sdc_ctx {
     unsigned int* counter = nullptr;
     size_t n_counters = 0;
     unsigned update_grid = 1;       // grid of the deferred FP32 update (one wave)
+    int update_bps = 0;             // sdc_set_update_blocks: its blocks per SM (0: as many as fit)
     double *X = nullptr, *R = nullptr, *U = nullptr, *P = nullptr, *Wv = nullptr, *S = nullptr, *D = nullptr;
     // mixed precision: FP64 right-hand side, FP32 inner vectors, FP32 mass, outer scalars
     double* Bv = nullptr;
@@ -78,6 +81,7 @@ struct sdc_ctx {
     int max_iter = 2000;
     int precision = SDC_FP64;
     int residuals = 0;
+    int true_res = 0;               // sdc_set_diagnostics bit 1: FP64 true residual of mixed solves
     std::vector<int> nondeg;        // 1-based standard nodes m whose interval has positive length
     bool temp_set = false;
 
@@ -556,6 +560,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.counter = c->counter;
     a.iters_out = &c->st->cg_iters[solve_idx];
     a.refine_out = &c->st->refinements[solve_idx];
+    a.true_res = &c->st->true_res[solve_idx];
     a.status = &c->st->status;
     a.part_blocks = (int)row_grid(c, k_mx_spmv);
     a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
@@ -568,8 +573,13 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
 
 void add_implicit_solve(sdc_ctx* c, Chain& ch, double dtau, int solve_idx, double rtol, int max_iter,
                         const RhsArgs& r) {
-    if (c->precision == SDC_MIXED_FP32) add_solve_mixed(c, ch, mix_args(c, dtau, solve_idx, rtol, max_iter), r);
-    else add_solve(c, ch, cg_args(c, dtau, solve_idx, rtol, max_iter), r);
+    if (c->precision == SDC_MIXED_FP32) {
+        const MixArgs a = mix_args(c, dtau, solve_idx, rtol, max_iter);
+        add_solve_mixed(c, ch, a, r);
+        if (c->true_res) ch.kernel(k_mx_true_residual, row_grid(c, k_mx_true_residual), RED_BLOCK, a);
+    } else {
+        add_solve(c, ch, cg_args(c, dtau, solve_idx, rtol, max_iter), r);
+    }
 }
 
 
@@ -609,6 +619,20 @@ void build_ell(sdc_ctx* c) {
     c->A.val = upload(c, c->pool_asm, val);
     std::vector<float> v32(val.begin(), val.end());
     c->A.val32 = upload(c, c->pool_asm, v32);
+}
+
+// One wave of the deferred FP32 update (rows strided): update_bps blocks a SM, or as many as
+// fit, and no more blocks than 256-row groups. The update's sums do not depend on its grid.
+void set_update_grid(sdc_ctx* c) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_update, RED_BLOCK, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    per_sm = std::max(per_sm, 1);
+    if (c->update_bps > 0) per_sm = std::min(per_sm, c->update_bps);
+    c->update_grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)per_sm * c->n_sms, blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK)));
 }
 
 void do_assemble(sdc_ctx* c) {
@@ -773,14 +797,7 @@ void do_assemble(sdc_ctx* c) {
     c->n_counters = 1 + n_groups;
     c->counter = dalloc_n<unsigned int>(c, c->pool_asm, c->n_counters);
     SDC_CUDA_TRY(cudaMemsetAsync(c->counter, 0, c->n_counters * sizeof(unsigned int), c->stream));
-    // one wave of the deferred FP32 update (rows strided)
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_update, RED_BLOCK, 0) != cudaSuccess) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    c->update_grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * c->n_sms, blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK)));
+    set_update_grid(c);
     SDC_CUDA_TRY(cudaMemsetAsync(c->st, 0, sizeof(StepState), c->stream));
     const size_t NI = (size_t)C.n_iface;
     c->E1.cnt = dalloc_n<int32_t>(c, c->pool_asm, NI);
@@ -1375,6 +1392,9 @@ void fill_report(sdc_ctx* c, sdc_step_report* rep) {
     rep->heat_stand = s.heat[0];
     rep->heat_stock = s.heat[1];
     rep->contact_cluster = c->iface_cluster;
+    rep->true_residual_max = -1.0;
+    if (c->true_res && c->precision == SDC_MIXED_FP32 && !ie)
+        for (int i = 0; i < n_solves; ++i) rep->true_residual_max = std::max(rep->true_residual_max, s.true_res[i]);
 }
 
 sdc_status read_state(sdc_ctx* c, sdc_step_report* rep) {
@@ -1423,7 +1443,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_mx_init, "k_mx_init"},
         {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_spmv_red, "k_mx_spmv_red"},
         {(const void*)k_mx_update, "k_mx_update"},     {(const void*)k_mx_update_red, "k_mx_update_red"},
-        {(const void*)k_mx_refine, "k_mx_refine"},
+        {(const void*)k_mx_refine, "k_mx_refine"},     {(const void*)k_mx_true_residual, "k_mx_true_residual"},
         {(const void*)k_bulk_endpoint_mx, "k_bulk_endpoint_mx"}, {(const void*)k_fi_mx, "k_fi_mx"},
     };
     for (const auto& n : names)
@@ -1749,6 +1769,15 @@ sdc_status sdc_set_contact_cluster(sdc_ctx* c, int max_ctas) {
     });
 }
 
+sdc_status sdc_set_update_blocks(sdc_ctx* c, int blocks_per_sm) {
+    return guarded(c, [&] {
+        require(blocks_per_sm >= 0 && blocks_per_sm <= 32, SDC_ERR_ARG, "blocks_per_sm out of range [0, 32]");
+        c->update_bps = blocks_per_sm;
+        if (c->assembled) set_update_grid(c);
+        c->graph_ready = false;
+    });
+}
+
 sdc_status sdc_set_wait_limit(sdc_ctx* c, int64_t polls) {
     return guarded(c, [&] {
         require(polls >= 0, SDC_ERR_ARG, "polls must be >= 0");
@@ -1793,11 +1822,13 @@ sdc_status sdc_set_stepper(sdc_ctx* c, int stepper) {
     });
 }
 
-sdc_status sdc_set_diagnostics(sdc_ctx* c, int residuals) {
+sdc_status sdc_set_diagnostics(sdc_ctx* c, int flags) {
     return guarded(c, [&] {
-        require(!residuals || c->stepper == SDC_STEPPER_MRSDC, SDC_ERR_ARG,
+        require(flags >= 0 && flags <= 3, SDC_ERR_ARG, "diagnostics flags are 0..3");
+        require(!(flags & 1) || c->stepper == SDC_STEPPER_MRSDC, SDC_ERR_ARG,
                 "residual diagnostics are available with MRSDC only");
-        c->residuals = residuals ? 1 : 0;
+        c->residuals = flags & 1;
+        c->true_res = (flags >> 1) & 1;
         c->graph_ready = false;
     });
 }
@@ -2344,3 +2375,199 @@ extern "C" sdc_status sdc_batch_synchronize(sdc_batch* b) {
     });
 }
 
+
+// ============================================================================ autotuner
+//
+// sdc_autotune picks the launch options of a context's macro-step graph from timed trial
+// steps: (SpMV, update) pairs per CG loop body, the blocks a SM of the deferred FP32 update,
+// the cap on the contact loop's cluster, the placement of its replicas, and graph side
+// branches. Every option leaves results bitwise unchanged (fixed-order reductions whose
+// order does not depend on them), so only time is compared. Each candidate is timed on the
+// same macro steps from the same saved state (T(t_n) and the step counters), by coordinate
+// descent from the context's current options; a candidate is taken when it is at least 1 %
+// faster. Picks are cached per process by the shape of the problem (device, sizes, contact
+// DOFs, precision, stepper, scheme), so contexts of equal shape (the members of a batch,
+// the slots of the serving loop) are tuned once.
+namespace {
+
+struct TuneOpts {
+    int unroll, update_bps, cluster_cap, global, branches;
+};
+
+struct TuneKey {
+    int device, precision, stepper, nodes, M, P, K;
+    int64_t n, nnz, n_iface;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(device, precision, stepper, nodes, M, P, K, n, nnz, n_iface) <
+               std::tie(o.device, o.precision, o.stepper, o.nodes, o.M, o.P, o.K, o.n, o.nnz, o.n_iface);
+    }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneOpts> g_tune_cache;
+
+TuneKey tune_key(const sdc_ctx* c) {
+    return {c->device, c->precision, c->stepper, c->W.kind, c->W.M, c->W.P, c->K_sweeps,
+            c->n, c->nnz, (int64_t)c->C.n_iface};
+}
+
+TuneOpts current_opts(sdc_ctx* c) {
+    int bps = c->update_bps;
+    if (bps == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_update, RED_BLOCK, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        bps = std::max(per_sm, 1);
+    }
+    return {cg_unroll(c), bps, c->max_cluster, c->force_global, c->branches};
+}
+
+void apply_opts(sdc_ctx* c, const TuneOpts& o) {
+    if (o.cluster_cap != c->max_cluster || o.global != c->force_global) c->buffers_ready = false;
+    c->cg_unroll = o.unroll;
+    c->update_bps = o.update_bps;
+    c->max_cluster = o.cluster_cap;
+    c->force_global = o.global;
+    c->branches = o.branches;
+    set_update_grid(c);
+    c->graph_ready = false;
+}
+
+// Device state a trial step changes, saved once and restored before every timed trial.
+struct TuneSnapshot {
+    sdc_ctx* c;
+    void* T = nullptr;
+    StepState st{};
+    explicit TuneSnapshot(sdc_ctx* cc) : c(cc) {
+        const size_t bytes = (size_t)c->n * sizeof(double);
+        if (c->alloc) T = c->alloc(bytes, c->user);
+        else if (cudaMalloc(&T, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            T = nullptr;
+        }
+        if (!T) throw ApiError(SDC_ERR_OOM, "device allocation of the autotuner's state copy failed");
+        SDC_CUDA_TRY(cudaMemcpyAsync(T, c->Tn, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        SDC_CUDA_TRY(cudaMemcpyAsync(&st, c->st, sizeof(StepState), cudaMemcpyDeviceToHost, c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    void restore() {
+        SDC_CUDA_TRY(cudaMemcpyAsync(c->Tn, T, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        SDC_CUDA_TRY(cudaMemcpyAsync(c->st, &st, sizeof(StepState), cudaMemcpyHostToDevice, c->stream));
+        SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    ~TuneSnapshot() {
+        if (!T) return;
+        cudaStreamSynchronize(c->stream);
+        if (c->alloc) c->free_fn(T, c->user);
+        else cudaFree(T);
+    }
+};
+
+// ms per macro step of the context's current options: one untimed step (graph build and
+// first launch), then the best of two runs of `steps` steps, each from the saved state.
+double time_opts(sdc_ctx* c, TuneSnapshot& snap, int steps) {
+    ensure_ready(c);
+    snap.restore();
+    launch_step(c);
+    read_state(c, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SDC_CUDA_TRY(cudaEventCreate(&e0));
+    SDC_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    try {
+        for (int rep = 0; rep < 2; ++rep) {
+            snap.restore();
+            SDC_CUDA_TRY(cudaEventRecord(e0, c->stream));
+            for (int s = 0; s < steps; ++s) launch_step(c);
+            SDC_CUDA_TRY(cudaEventRecord(e1, c->stream));
+            SDC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SDC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            read_state(c, nullptr);
+            best = std::min(best, (double)ms / steps);
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+}  // namespace
+
+extern "C" sdc_status sdc_autotune(sdc_ctx* c, int32_t trial_steps, sdc_tune_report* rep) {
+    return guarded(c, [&] {
+        require(trial_steps >= 0 && trial_steps <= 64, SDC_ERR_ARG, "trial_steps out of range [0, 64]");
+        require(!c->eager, SDC_ERR_STATE, "autotuning times graph execution: switch eager execution off");
+        ensure_ready(c);
+        const int steps = trial_steps ? trial_steps : 3;
+        const TuneKey key = tune_key(c);
+        sdc_tune_report out{};
+        out.ms_default = out.ms_tuned = -1.0;
+        bool cached = false;
+        TuneOpts picked{};
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                picked = it->second;
+                cached = true;
+            }
+        }
+        if (cached) {
+            apply_opts(c, picked);
+            ensure_ready(c);
+        } else {
+            TuneSnapshot snap(c);
+            TuneOpts best = current_opts(c);
+            apply_opts(c, best);
+            double best_ms = time_opts(c, snap, steps);
+            out.ms_default = best_ms;
+            int trials = 1;
+            auto consider = [&](TuneOpts o) {
+                apply_opts(c, o);
+                const double ms = time_opts(c, snap, steps);
+                ++trials;
+                if (ms < 0.99 * best_ms) {
+                    best = o;
+                    best_ms = ms;
+                }
+            };
+            const bool small_grid = blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS;
+            for (int u : small_grid ? std::vector<int>{1, 2, 3, 4, 6} : std::vector<int>{1, 2})
+                if (u != best.unroll) consider({u, best.update_bps, best.cluster_cap, best.global, best.branches});
+            if (c->precision == SDC_MIXED_FP32 && small_grid) {
+                const int top = best.update_bps;
+                for (int b = 2; b < top; ++b) consider({best.unroll, b, best.cluster_cap, best.global, best.branches});
+            }
+            // smaller clusters than the automatic size (the cap never enlarges it)
+            const int auto_cs = c->iface_cluster;
+            for (int cs = auto_cs / 2; cs >= 1 && cs >= auto_cs / 4; cs /= 2)
+                consider({best.unroll, best.update_bps, cs, best.global, best.branches});
+            if (!best.global && !c->iface_global)
+                consider({best.unroll, best.update_bps, best.cluster_cap, 1, best.branches});
+            if (!c->in_batch) consider({best.unroll, best.update_bps, best.cluster_cap, best.global, 1 - best.branches});
+            apply_opts(c, best);
+            ensure_ready(c);
+            snap.restore();
+            out.ms_tuned = best_ms;
+            out.trials = trials;
+            picked = best;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
+        out.cg_unroll = picked.unroll;
+        out.update_blocks_per_sm = picked.update_bps;
+        out.contact_cluster_cap = picked.cluster_cap;
+        out.contact_cluster = c->iface_cluster;
+        out.contact_global = c->iface_global ? 1 : 0;
+        out.graph_branches = picked.branches;
+        out.cached = cached ? 1 : 0;
+        if (rep) *rep = out;
+    });
+}

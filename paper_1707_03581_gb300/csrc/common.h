@@ -162,6 +162,7 @@ struct StepState {
     double heat[2];
     double friction_in;
     double rmax_partial_dummy;
+    double true_res[MAX_SOLVES];  // ||b - A x|| / ||b|| with FP64 K after each mixed solve (if enabled)
 };
 
 // ----------------------------------------------------------------- helpers

@@ -84,6 +84,7 @@ struct MixArgs {
     unsigned int* counter;          // [0] groups done, [1 + g] blocks of group g done
     int* iters_out;                 // inner iterations of this solve (all passes)
     int* refine_out;                // refinement passes of this solve
+    double* true_res;               // k_mx_true_residual: ||b - A x|| / ||b|| of this solve
     int* status;
     int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_*_red
     int part_blocks;                // grid of k_mx_spmv: number of its block partials
@@ -280,6 +281,7 @@ __global__ void k_mx_spmv_red(MixArgs a);
 __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_update_red(MixArgs a);
 __global__ void k_mx_refine(MixArgs a);
+__global__ void k_mx_true_residual(MixArgs a);
 __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_bulk_endpoint_mx(BulkArgs a);
 __global__ void k_fi_mx(FiDevArgs a);
