@@ -252,6 +252,8 @@ typedef struct {
     int32_t graph_branches;       /* sdc_set_graph_branches                                        */
     int32_t trials;               /* option sets timed (0 when taken from the cache)               */
     int32_t cached;               /* 1: picks of an earlier context of the same shape              */
+    int32_t skipped;              /* option sets the device could not run (skipped)                 */
+    int32_t pad_;
     double ms_default;            /* ms per macro step with the options the context had (-1 cached)*/
     double ms_tuned;              /* ms per macro step with the picks (-1 cached)                   */
 } sdc_tune_report;
@@ -260,7 +262,8 @@ typedef struct {
  * graph execution, and sets them. Each option set is timed on the same trial_steps macro
  * steps (0 = 3) from the context's current state, which is saved first and restored after,
  * so the call leaves T(t_n), the time and the heat ledger as they were. Coordinate descent
- * from the current options; a candidate must be 1 % faster to be taken. Every option leaves
+ * from the current options; a candidate must be 1 % faster to be taken, and one the device
+ * cannot run (a contact cluster too small for the interface) is skipped. Every option leaves
  * results bitwise unchanged. Picks are cached in the process by the problem's shape
  * (device, DOFs, nonzeros, contact DOFs, precision, stepper, nodes, M, P, sweeps): later
  * contexts of that shape take them without trials. Needs sdc_set_temperature; allocates

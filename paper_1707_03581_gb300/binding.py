@@ -50,10 +50,11 @@ class StepReport(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("cg_unroll", C.c_int32), ("update_blocks_per_sm", C.c_int32), ("contact_cluster_cap", C.c_int32),
                 ("contact_cluster", C.c_int32), ("contact_global", C.c_int32), ("graph_branches", C.c_int32),
-                ("trials", C.c_int32), ("cached", C.c_int32), ("ms_default", C.c_double), ("ms_tuned", C.c_double)]
+                ("trials", C.c_int32), ("cached", C.c_int32), ("skipped", C.c_int32), ("pad_", C.c_int32),
+                ("ms_default", C.c_double), ("ms_tuned", C.c_double)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad_"}
 
 
 class Heat(C.Structure):

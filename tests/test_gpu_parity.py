@@ -448,3 +448,27 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
     b.set_kernel_timing(True)
     b.step(report=True)
     assert any(k.endswith("_gl") for k in b.kernel_times())
+
+
+def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):
+    # 3,950 contact DOFs: 16 CTAs give one DOF a thread (k_iface_loop_mx1), 4 CTAs two
+    # (k_iface_loop_mx), 2 CTAs four (k_iface_loop_mx4, the form of the 5.75M-DOF machine)
+    mach = machine_config(1)
+    ref = None
+    seen = []
+    for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx4")):
+        s = _solver(mach, precision="mixed")
+        s.set_contact_cluster(cap)
+        for _ in range(2):
+            s.step(report=True)
+        s.set_execution(True)
+        s.set_kernel_timing(True)
+        s.step(report=True)
+        loops = [k for k in s.kernel_times() if k.startswith("k_iface_loop")]
+        assert loops == [form], (cap, loops)
+        T = s.temperature()
+        if ref is None:
+            ref = T
+        assert np.array_equal(T, ref), cap
+        seen.append(form)
+        s.close()

@@ -47,3 +47,27 @@ def test_results_in_the_mix_equal_results_alone(torch, precision):
         assert np.array_equal(s.temperature(), r.result), r
         s.close()
     server.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_pool_machines_in_the_mix_equal_results_alone(torch, precision):
+    # the machines serving draws from: batch members of stand resolution 16, 24 and 32
+    # (12,902 to 95,434 DOF), with their own strokes and friction fluxes
+    from paper_1707_03581_gb300 import Solver
+    from paper_1707_03581_gb300.serving import LookAheadServer, Request
+    from synth.machines import batch_resolutions
+
+    first = batch_resolutions()
+    machines = machine_config(3, select={first[16], first[24], first[32]})
+    rng = np.random.default_rng(4)
+    server = LookAheadServer(machines, precision=precision, max_active=6, chunk=2, keep_results=True)
+    reqs = [Request(0.001 * k, float(rng.integers(2, 6)), int(k % 3)) for k in range(9)]
+    server.run(reqs)
+    assert all(r.status == "done" for r in reqs)
+    for r in reqs:
+        s = Solver(0, own_stream=True)
+        s.set_machine(machines[r.machine_index], precision=precision)
+        s.run_horizon(r.n_steps)
+        assert np.array_equal(s.temperature(), r.result), (r.machine_index, r.n_steps)
+        s.close()
+    server.close()
