@@ -56,10 +56,10 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _workload(config_idx):
+def _workload(config_idx, member=None):
     from synth import machine_config
 
-    m = machine_config(config_idx)
+    m = machine_config(3, select={member})[0] if member is not None else machine_config(config_idx)
     s = m.scheme
     n_int = s.M - 1 if s.nodes == "lobatto" else s.M
     desc = (f"{m.name}: {m.stand.mesh.n[0]}x{m.stand.mesh.n[1]}x{m.stand.mesh.n[2]} stand + "
@@ -721,14 +721,14 @@ def run_gpu(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    m, n_int, desc = _workload(args.config)
+    m, n_int, desc = _workload(args.config, args.member)
     compare = args.precision == "mixed" and not args.no_compare
     peak, peak_kind = _peaks()
     host = _host_cpu()
-    cpu_on = not args.no_cpu_baseline and world == 1 and rank == 0
+    cpu_on = not args.no_cpu_baseline and world == 1 and rank == 0 and args.member is None
     # The 313,646-DOF workload rides along with the 5.75M-DOF headline (labelled extra key); the
     # comparison rows (stationary start, single-rate SDC, implicit Euler) run on it there.
-    side_idx = 1 if args.config == 2 and not args.no_extra else None
+    side_idx = 1 if args.config == 2 and not args.no_extra and args.member is None else None
     tmp = tempfile.mkdtemp()
     oracle = {}
     if cpu_on:
@@ -1067,6 +1067,8 @@ def main():
                          "4: serving (Poisson arrivals); 5: convergence order and residual decay on the "
                          "reduced problem of Sec. 4")
     ap.add_argument("--machines", type=int, default=None, help="config 3: use only the first machines")
+    ap.add_argument("--member", type=int, default=None,
+                    help="config 3: time batch machine i alone, as a single-machine workload")
     ap.add_argument("--lam", type=float, default=10.0, help="config 4: arrival rate [requests/s]")
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
@@ -1097,7 +1099,7 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.config == 3:
+    elif args.config == 3 and args.member is None:
         run_batch(args, rank, world)
     elif args.config == 4:
         run_serving(args, rank, world)

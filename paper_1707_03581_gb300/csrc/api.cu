@@ -816,7 +816,7 @@ using IfaceKernel = void (*)(IfaceArgs);
 IfaceKernel iface_loop_kernel(bool mixed, int chunk, bool global) {
     if (global) return mixed ? k_iface_loop_mx_gl : k_iface_loop_gl;
     const bool one = chunk <= IFACE_THREADS;
-    if (mixed) return one ? k_iface_loop_mx1 : (chunk <= IFACE_THREADS * IFACE_PER_THREAD ? k_iface_loop_mx : k_iface_loop_mx4);
+    if (mixed) return one ? k_iface_loop_mx1 : k_iface_loop_mx;
     return one ? k_iface_loop1 : k_iface_loop;
 }
 
@@ -844,14 +844,14 @@ void pick_iface_cluster(sdc_ctx* c) {
     size_t smem_cap = (size_t)optin;
     for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
                           (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
-                          (const void*)k_iface_loop_mx_gl, (const void*)k_iface_loop_mx4}) {
+                          (const void*)k_iface_loop_mx_gl}) {
         cudaFuncAttributes fa{};
         SDC_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
         smem_cap = std::min(smem_cap, (size_t)optin - fa.sharedSizeBytes);
     }
     for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
                           (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
-                          (const void*)k_iface_loop_mx_gl, (const void*)k_iface_loop_mx4}) {
+                          (const void*)k_iface_loop_mx_gl}) {
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
@@ -870,8 +870,7 @@ void pick_iface_cluster(sdc_ctx* c) {
         int chunk = ((NI + cs - 1) / cs + 3) & ~3;
         size_t rep_bytes = 2 * (size_t)cs * chunk * esz;
         bool global;
-        const int per_shared = mixed ? IFACE_PER_THREAD_MX : IFACE_PER_THREAD;
-        if (!c->force_global && chunk <= IFACE_THREADS * per_shared && rep_bytes <= smem_cap) {
+        if (!c->force_global && chunk <= IFACE_THREADS * IFACE_PER_THREAD && rep_bytes <= smem_cap) {
             global = false;
         } else {
             chunk = (chunk + 31) & ~31;  // global replicas are owned in 32-DOF tiles
@@ -1436,7 +1435,6 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
-        {(const void*)k_iface_loop_mx4, "k_iface_loop_mx4"},
         {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
         {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"}, {(const void*)k_ie_init, "k_ie_init"},
         {(const void*)k_ie_spmv, "k_ie_spmv"},

@@ -1626,10 +1626,6 @@ __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_gl(IfaceArgs a) { 
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx1(IfaceArgs a) { iface_loop_impl<true, 1, false>(a); }
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx(IfaceArgs a) { iface_loop_impl<true, 2, false>(a); }
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx_gl(IfaceArgs a) { iface_loop_impl<true, 4, true>(a); }
-// mixed precision, shared replicas, up to four contact DOFs a thread: the FP32 replicas of
-// interfaces of up to 16 x 2048 DOFs still fit in shared memory (2 x 16 x 1,700 x 4 B =
-// 212.5 KB for the 27,170 contact DOFs of the 5.75M-DOF machine)
-__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx4(IfaceArgs a) { iface_loop_impl<true, 4, false>(a); }
 
 // ------------------------------------------------------------------ diagnostics
 

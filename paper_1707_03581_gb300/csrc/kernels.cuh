@@ -12,7 +12,6 @@ constexpr int IFACE_TARGET_CHUNK = 128;  // preferred contact DOFs per CTA of th
 constexpr int IFACE_THREADS = 512;      // threads per CTA of that cluster
 constexpr int IFACE_PER_THREAD = 2;     // contact DOFs one thread of a shared-memory-replica loop owns
 constexpr int IFACE_PER_THREAD_GL = 4;  // the same for the global-replica loop
-constexpr int IFACE_PER_THREAD_MX = 4;  // and for the mixed-precision loop with shared replicas
 constexpr int IFACE_BATCH = 8;          // coupling entries fetched per round
 // largest contact interface the loop takes (global replicas, 16 CTAs x 512 threads x 4)
 constexpr int IFACE_MAX_NI = 32768;
@@ -297,7 +296,6 @@ __global__ void k_iface_loop_gl(IfaceArgs a);
 __global__ void k_iface_loop_mx(IfaceArgs a);
 __global__ void k_iface_loop_mx1(IfaceArgs a);
 __global__ void k_iface_loop_mx_gl(IfaceArgs a);
-__global__ void k_iface_loop_mx4(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,
                        unsigned int* counter, double* heat);

@@ -450,13 +450,14 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
     assert any(k.endswith("_gl") for k in b.kernel_times())
 
 
+
 def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):
     # 3,950 contact DOFs: 16 CTAs give one DOF a thread (k_iface_loop_mx1), 4 CTAs two
-    # (k_iface_loop_mx), 2 CTAs four (k_iface_loop_mx4, the form of the 5.75M-DOF machine)
+    # (k_iface_loop_mx), 2 CTAs too many for shared memory forms (global replicas, the form
+    # of the 5.75M-DOF machine: k_iface_loop_mx_gl)
     mach = machine_config(1)
     ref = None
-    seen = []
-    for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx4")):
+    for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx_gl")):
         s = _solver(mach, precision="mixed")
         s.set_contact_cluster(cap)
         for _ in range(2):
@@ -470,5 +471,4 @@ def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):
         if ref is None:
             ref = T
         assert np.array_equal(T, ref), cap
-        seen.append(form)
         s.close()
