@@ -350,6 +350,23 @@ sdc_status sdc_batch_step(sdc_batch* batch, const int64_t* n_steps, int wait);
 /* Wait for every member; returns the first member error. */
 sdc_status sdc_batch_synchronize(sdc_batch* batch);
 
+/* Block-diagonal form of a batch (the batched layout of the stacked per-machine systems of
+ * Eq. coupledFEM): on (1), the members that qualify run as one fused group, one CUDA graph
+ * per batched macro step on a stream of the batch, in which the FP32 inner CG of every
+ * mixed-precision implicit solve (Algorithms 1 and 2) is ONE launch of the SpMV and ONE of
+ * the update per iteration over the concatenated rows of all members, with each member's
+ * own dot products, step lengths and stop test (a member whose CG stopped returns at once),
+ * and one launch of the refinement per pass; the rest of each member's step runs as its
+ * own chain of that graph. Results are bitwise those of the members run alone. Qualify:
+ * mixed precision, the MRSDC stepper, at most 2048 blocks of 256 rows, no diagnostics,
+ * graph execution, and the scheme of the group's first member; the others keep their own
+ * graphs. Fused members take equal step counts in sdc_batch_step (else SDC_ERR_ARG). Off
+ * (0, the default): every member runs its own graph on its own stream. */
+sdc_status sdc_batch_set_fused(sdc_batch* batch, int on);
+
+/* Members in the fused group (0 when the batch is not fused or fewer than two qualify). */
+sdc_status sdc_batch_fused_size(sdc_batch* batch, int32_t* n);
+
 /* ---------------------------------------------------------------- results */
 
 /* Device bytes the context holds (assembled system, state and scheme buffers). */

@@ -121,6 +121,8 @@ _SIGS = {
     "sdc_batch_size": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sdc_batch_step": (C.c_int, [_vp, _i64p, C.c_int]),
     "sdc_batch_synchronize": (C.c_int, [_vp]),
+    "sdc_batch_set_fused": (C.c_int, [_vp, C.c_int]),
+    "sdc_batch_fused_size": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
 }
 
 _LIB = None
@@ -545,6 +547,15 @@ class Batch:
 
     def synchronize(self):
         self._call("sdc_batch_synchronize")
+
+    def set_fused(self, on: bool):
+        """Block-diagonal form: qualifying members' FP32 CG as one launch (sdc_batch_set_fused)."""
+        self._call("sdc_batch_set_fused", 1 if on else 0)
+
+    def fused_size(self) -> int:
+        n = C.c_int32()
+        self._call("sdc_batch_fused_size", C.byref(n))
+        return n.value
 
     def close(self):
         if getattr(self, "h", None):

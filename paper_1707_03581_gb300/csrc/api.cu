@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <map>
 #include <mutex>
@@ -20,6 +21,10 @@
 #include "kernels.cuh"
 
 using namespace sdc;
+
+namespace {
+struct Chain;  // graph-node appender (below)
+}
 
 struct sdc_ctx {
     int device = 0;
@@ -105,6 +110,8 @@ struct sdc_ctx {
     double* ie_coef = nullptr;        // implicit Euler: FP64 coupling rows of that slot
     double* fe_std[2][MAX_M + 1] = {};  // single-rate SDC: f^E at the standard nodes, by iterate
     int in_batch = 0;               // batches holding this context (their members run without side branches)
+    // set while a fused batch group emits this member's step: takes each mixed solve
+    std::function<void(Chain&, MixArgs, const RhsArgs&)>* solve_hook = nullptr;
     void* iface_rep = nullptr;      // their buffers
     int* iface_sent = nullptr;      // chunks each CTA of the loop's cluster sent (per launch)
     long long poll_limit = IFACE_POLLS;  // sdc_set_wait_limit
@@ -575,6 +582,10 @@ void add_implicit_solve(sdc_ctx* c, Chain& ch, double dtau, int solve_idx, doubl
                         const RhsArgs& r) {
     if (c->precision == SDC_MIXED_FP32) {
         const MixArgs a = mix_args(c, dtau, solve_idx, rtol, max_iter);
+        if (c->solve_hook) {
+            (*c->solve_hook)(ch, a, r);
+            return;
+        }
         add_solve_mixed(c, ch, a, r);
         if (c->true_res) ch.kernel(k_mx_true_residual, row_grid(c, k_mx_true_residual), RED_BLOCK, a);
     } else {
@@ -2251,6 +2262,15 @@ struct sdc_batch {
     int device = 0;
     std::vector<sdc_ctx*> members;
     std::string err;
+    // fused group (sdc_batch_set_fused): the members whose inner FP32 CG runs as one launch
+    int fused = 0;
+    bool group_dirty = true;
+    std::vector<sdc_ctx*> group;
+    cudaStream_t gstream = nullptr;
+    cudaGraph_t ggraph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gdone = nullptr;
+    std::vector<void*> gbufs;       // device buffers of the group graph
 };
 
 extern "C" sdc_status sdc_poll(sdc_ctx* c, int* idle) {
@@ -2293,6 +2313,158 @@ void member_check(sdc_ctx* c, sdc_status st, int i) {
     if (st != SDC_OK) throw ApiError(st, "member " + std::to_string(i) + ": " + c->err);
 }
 
+// ---------------------------------------------------------------- fused group
+//
+// The members of a fused group share one CUDA graph per batched macro step. Each member's
+// kernels form a chain of that graph as in its own step graph, except its mixed-precision
+// implicit solves: there the member's k_mx_init is followed by one group solve, a WHILE
+// loop of refinement passes around a WHILE loop of FP32 CG iterations in which each SpMV
+// and each update is ONE launch over the concatenated blocks of every member (the
+// block-diagonal operator of all members), then one refinement launch. A member's blocks
+// use its own arguments, partial sums and scalars, so its arithmetic (block partition and
+// summation order included) is that of its own launches and its results are bitwise those
+// of the member run alone; a member whose CG stopped returns at once from the later
+// launches, and the loops end when the last member stops. Every member's chain waits for
+// the group solve before it goes on. Eligible: mixed precision, MRSDC, grids of at most
+// MIX_DEFER_MAX_BLOCKS blocks (deferred dots), no diagnostics, graph execution, and the
+// same scheme (the same sequence of solves) as the group's first member.
+bool fusable(const sdc_ctx* c, const sdc_ctx* ref) {
+    const bool ok = c->precision == SDC_MIXED_FP32 && c->stepper == SDC_STEPPER_MRSDC && !c->residuals &&
+                    !c->true_res && !c->eager &&
+                    blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS;
+    if (!ok || !ref) return ok;
+    return c->W.kind == ref->W.kind && c->W.M == ref->W.M && c->W.P == ref->W.P && c->W.w == ref->W.w &&
+           c->K_sweeps == ref->K_sweeps && c->dt == ref->dt && c->nondeg == ref->nondeg;
+}
+
+void group_release(sdc_batch* b) {
+    if (b->gstream) cudaStreamSynchronize(b->gstream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->ggraph) cudaGraphDestroy(b->ggraph);
+    b->gexec = nullptr;
+    b->ggraph = nullptr;
+    for (void* p : b->gbufs) cudaFree(p);
+    b->gbufs.clear();
+    b->group.clear();
+    b->group_dirty = true;
+}
+
+template <class T>
+T* group_upload(sdc_batch* b, const std::vector<T>& v) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        throw ApiError(SDC_ERR_OOM, "cudaMalloc of a fused-group table failed");
+    }
+    b->gbufs.push_back(p);
+    if (!v.empty()) SDC_CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return static_cast<T*>(p);
+}
+
+// Member and first-block tables of one fused launch, from each member's block count.
+GroupLaunch group_blocks(sdc_batch* b, const std::vector<int>& counts, unsigned& total) {
+    std::vector<int> member, first(counts.size() + 1, 0);
+    for (size_t m = 0; m < counts.size(); ++m) {
+        first[m + 1] = first[m] + counts[m];
+        member.insert(member.end(), counts[m], (int)m);
+    }
+    total = (unsigned)first.back();
+    GroupLaunch L{};
+    L.member = group_upload(b, member);
+    L.first = group_upload(b, first);
+    return L;
+}
+
+void build_group(sdc_batch* b) {
+    group_release(b);
+    for (sdc_ctx* c : b->members)
+        if (fusable(c, b->group.empty() ? nullptr : b->group[0])) b->group.push_back(c);
+    if (b->group.size() < 2) {  // nothing to fuse: every member runs its own graph
+        b->group.clear();
+        b->group_dirty = false;
+        return;
+    }
+    if (!b->gstream) SDC_CUDA_TRY(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
+    if (!b->gdone) SDC_CUDA_TRY(cudaEventCreateWithFlags(&b->gdone, cudaEventDisableTiming));
+    const size_t nm = b->group.size();
+    GroupState* gs = group_upload(b, std::vector<GroupState>(1, GroupState{0, 0}));
+    SDC_CUDA_TRY(cudaGraphCreate(&b->ggraph, 0));
+    cudaGraph_t G = b->ggraph;
+    std::vector<std::vector<cudaGraphNode_t>> in(nm), out(nm);
+    std::vector<std::vector<MixArgs>> args(nm);
+    for (size_t i = 0; i < nm; ++i) {
+        sdc_ctx* c = b->group[i];
+        ensure_ready(c);
+        Chain ch(G);
+        ch.allow_branches = false;
+        std::function<void(Chain&, MixArgs, const RhsArgs&)> hook = [&](Chain& chh, MixArgs a, const RhsArgs& r) {
+            a.grp = gs;
+            a.h_outer = a.h_inner = 0;
+            a.tail_pairs = 0;
+            chh.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+            in[i].push_back(chh.last);
+            cudaGraphNode_t e;
+            SDC_CUDA_TRY(cudaGraphAddEmptyNode(&e, G, nullptr, 0));
+            chh.last = e;
+            out[i].push_back(e);
+            args[i].push_back(a);
+        };
+        c->solve_hook = &hook;
+        try {
+            emit_step(c, ch);
+        } catch (...) {
+            c->solve_hook = nullptr;
+            throw;
+        }
+        c->solve_hook = nullptr;
+        require(in[i].size() == in[0].size(), SDC_ERR_STATE, "fused members differ in their solves");
+    }
+    std::vector<int> n_spmv(nm), n_upd(nm);
+    for (size_t i = 0; i < nm; ++i) {
+        n_spmv[i] = (int)row_grid(b->group[i], k_mx_spmv);
+        n_upd[i] = (int)b->group[i]->update_grid;
+    }
+    unsigned t_spmv = 0, t_upd = 0, t_ref = 0;
+    GroupArgs g0{};
+    g0.gs = gs;
+    g0.n_members = (int)nm;
+    // beyond what any member's own caps allow (MIX_INNER_MAX iterations, MIX_MAX_REFINE passes)
+    g0.launch_cap = 2 * MIX_INNER_MAX + 16;
+    g0.pass_cap = MIX_MAX_REFINE + 2;
+    g0.spmv = group_blocks(b, n_spmv, t_spmv);
+    g0.update = group_blocks(b, n_upd, t_upd);
+    g0.refine = group_blocks(b, n_spmv, t_ref);  // the refinement runs one row a thread, like the SpMV
+    const int unroll = cg_unroll(b->group[0]);
+    for (size_t k = 0; k < in[0].size(); ++k) {
+        std::vector<MixArgs> ak(nm);
+        for (size_t i = 0; i < nm; ++i) ak[i] = args[i][k];
+        GroupArgs g = g0;
+        g.args = group_upload(b, ak);
+        Chain gc(G);
+        for (size_t i = 0; i < nm; ++i) gc.join(in[i][k]);
+        cudaGraphConditionalHandle ho, hi;
+        SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, G, 1u, cudaGraphCondAssignDefault));
+        g.h_outer = (unsigned long long)ho;
+        gc.kernel(k_group_begin, 1u, 32u, g);
+        Chain outer(gc.while_node(ho));
+        SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, outer.g, 1u, cudaGraphCondAssignDefault));
+        g.h_inner = (unsigned long long)hi;
+        Chain inner(outer.while_node(hi));
+        for (int u = 0; u < unroll; ++u) {
+            GroupArgs gu = g;
+            gu.tail_pairs = unroll - 1 - u;
+            inner.kernel(k_mx_spmv_g, t_spmv, (unsigned)RED_BLOCK, gu);
+            inner.kernel(k_mx_update_g, t_upd, (unsigned)RED_BLOCK, gu);
+        }
+        outer.kernel(k_mx_refine_g, t_ref, (unsigned)RED_BLOCK, g);
+        gc.kernel(k_group_end, 1u, 32u, g);
+        for (size_t i = 0; i < nm; ++i) SDC_CUDA_TRY(cudaGraphAddDependencies(G, &gc.last, &out[i][k], nullptr, 1));
+    }
+    SDC_CUDA_TRY(cudaGraphInstantiate(&b->gexec, G, 0));
+    b->group_dirty = false;
+}
+
 }  // namespace
 
 extern "C" sdc_status sdc_batch_create(sdc_batch** out, int device) {
@@ -2305,7 +2477,29 @@ extern "C" sdc_status sdc_batch_create(sdc_batch** out, int device) {
     return SDC_OK;
 }
 
-extern "C" void sdc_batch_destroy(sdc_batch* b) { delete b; }
+extern "C" void sdc_batch_destroy(sdc_batch* b) {
+    if (!b) return;
+    group_release(b);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->gdone) cudaEventDestroy(b->gdone);
+    delete b;
+}
+
+extern "C" sdc_status sdc_batch_set_fused(sdc_batch* b, int on) {
+    return batch_guarded(b, [&] {
+        if (!on) group_release(b);
+        b->fused = on ? 1 : 0;
+        b->group_dirty = true;
+    });
+}
+
+extern "C" sdc_status sdc_batch_fused_size(sdc_batch* b, int32_t* n) {
+    return batch_guarded(b, [&] {
+        require(n != nullptr, SDC_ERR_ARG, "n is NULL");
+        if (b->fused && b->group_dirty) build_group(b);
+        *n = b->fused ? (int32_t)b->group.size() : 0;
+    });
+}
 
 extern "C" const char* sdc_batch_last_error(const sdc_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
@@ -2319,6 +2513,7 @@ extern "C" sdc_status sdc_batch_add(sdc_batch* b, sdc_ctx* c, int32_t* index) {
             require(m != c, SDC_ERR_ARG, "the context is already a member");
             require(m->stream != c->stream, SDC_ERR_ARG, "every member needs its own stream");
         }
+        b->group_dirty = true;
         b->members.push_back(c);
         c->in_batch += 1;
         c->graph_ready = false;
@@ -2331,6 +2526,7 @@ extern "C" sdc_status sdc_batch_remove(sdc_batch* b, sdc_ctx* c) {
         auto it = std::find(b->members.begin(), b->members.end(), c);
         require(it != b->members.end(), SDC_ERR_ARG, "not a member");
         SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (b->fused) group_release(b);
         b->members.erase(it);
         c->in_batch -= 1;
         c->graph_ready = false;
@@ -2354,15 +2550,44 @@ extern "C" sdc_status sdc_batch_step(sdc_batch* b, const int64_t* n_steps, int w
             require(k >= 0, SDC_ERR_ARG, "negative step count");
             most = std::max(most, k);
         }
+        // fused group: rebuilt when the membership or a member's options changed
+        if (b->fused) {
+            bool dirty = b->group_dirty;
+            for (sdc_ctx* c : b->members) dirty = dirty || !c->graph_ready || !c->buffers_ready;
+            if (dirty) build_group(b);
+        }
+        auto in_group = [&](sdc_ctx* c) {
+            return b->fused && std::find(b->group.begin(), b->group.end(), c) != b->group.end();
+        };
+        int64_t group_steps = -1;
         for (size_t i = 0; i < nm; ++i) {  // graphs and buffers first, outside the launch sweep
             sdc_ctx* c = b->members[i];
-            if ((n_steps ? n_steps[i] : 1) > 0) member_check(c, guarded(c, [&] { ensure_ready(c); }), (int)i);
+            const int64_t k = n_steps ? n_steps[i] : 1;
+            if (in_group(c)) {
+                require(group_steps < 0 || group_steps == k, SDC_ERR_ARG,
+                        "the fused members of a batch step together: give them equal step counts");
+                group_steps = k;
+            }
+            if (k > 0) member_check(c, guarded(c, [&] { ensure_ready(c); }), (int)i);
         }
-        for (int64_t s = 0; s < most; ++s)
+        if (group_steps > 0) {  // the group's graph runs after the work already on the members' streams
+            for (sdc_ctx* c : b->group) {
+                SDC_CUDA_TRY(cudaEventRecord(b->gdone, c->stream));
+                SDC_CUDA_TRY(cudaStreamWaitEvent(b->gstream, b->gdone, 0));
+            }
+        }
+        for (int64_t s = 0; s < most; ++s) {
+            if (s < group_steps) SDC_CUDA_TRY(cudaGraphLaunch(b->gexec, b->gstream));
             for (size_t i = 0; i < nm; ++i) {
                 sdc_ctx* c = b->members[i];
+                if (in_group(c)) continue;
                 if (s < (n_steps ? n_steps[i] : 1)) member_check(c, guarded(c, [&] { launch_step(c); }), (int)i);
             }
+        }
+        if (group_steps > 0) {  // and later work on a member's stream runs after the group's steps
+            SDC_CUDA_TRY(cudaEventRecord(b->gdone, b->gstream));
+            for (sdc_ctx* c : b->group) SDC_CUDA_TRY(cudaStreamWaitEvent(c->stream, b->gdone, 0));
+        }
         if (wait)
             for (size_t i = 0; i < nm; ++i) member_check(b->members[i], sdc_synchronize(b->members[i]), (int)i);
     });

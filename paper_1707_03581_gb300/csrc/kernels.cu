@@ -173,7 +173,20 @@ __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const f
 constexpr int RED_GROUP = 64;
 
 template <int NQ, typename W>
+__device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out,
+                                unsigned int blk, unsigned int nblk);
+
+template <int NQ, typename W>
 __device__ bool reduce_last2(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out) {
+    return reduce_last2_at<NQ, W>(v, partials, gpartials, counters, out, blockIdx.x, gridDim.x);
+}
+
+// The same with the block's index and the grid size given: a fused launch over several
+// machines passes each machine's own block index and grid, so that every machine keeps the
+// partition and summation order of its own launch.
+template <int NQ, typename W>
+__device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out,
+                                unsigned int blk, unsigned int nblk) {
     __shared__ double sh[NQ][32];
     __shared__ int am_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -203,12 +216,12 @@ __device__ bool reduce_last2(W (&v)[NQ], double* partials, double* gpartials, un
                 sh[q][lane] = warp_sum(t);
             }
     }
-    const unsigned int g = blockIdx.x / RED_GROUP;
-    const unsigned int ng = (gridDim.x + RED_GROUP - 1) / RED_GROUP;
-    const unsigned int gsize = min((unsigned int)RED_GROUP, gridDim.x - g * RED_GROUP);
+    const unsigned int g = blk / RED_GROUP;
+    const unsigned int ng = (nblk + RED_GROUP - 1) / RED_GROUP;
+    const unsigned int gsize = min((unsigned int)RED_GROUP, nblk - g * RED_GROUP);
     if (warp == 0 && lane == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) partials[(size_t)q * gridDim.x + blockIdx.x] = sh[q][0];
+        for (int q = 0; q < NQ; ++q) partials[(size_t)q * nblk + blk] = sh[q][0];
         __threadfence();
         am_last = atomicAdd(&counters[1 + g], 1u) == gsize - 1;
     }
@@ -222,7 +235,7 @@ __device__ bool reduce_last2(W (&v)[NQ], double* partials, double* gpartials, un
 #pragma unroll
             for (int c = 0; c < RED_GROUP / 32; ++c) {
                 const unsigned int k = lane + 32 * c;
-                pv[c] = k < gsize ? __ldcg(partials + (size_t)q * gridDim.x + g * RED_GROUP + k) : 0.0;
+                pv[c] = k < gsize ? __ldcg(partials + (size_t)q * nblk + g * RED_GROUP + k) : 0.0;
             }
             double t = 0.0;
 #pragma unroll
@@ -467,6 +480,7 @@ __device__ __forceinline__ void mx_begin_pass(const MixArgs& a, double rr) {
     // the inner loop's condition starts at 1 with each step's graph launch; the
     // refinement (in the same graph as that loop) sets it again for each later pass
     if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 1u);
+    if (a.grp && !s->done) atomicAdd(&a.grp->inner_active, 1);  // the group's refinement sets the condition
 }
 
 // A CG-loop SpMV that finds its solve done on entry. If no kernel of this pass
@@ -529,15 +543,19 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
         *a.refine_out = 0;
         const bool conv = out[1] <= a.rtol2 * out[0];
         s->done = conv ? 1 : 0;
+        if (conv) a.cg->done = 1;  // no inner pass: a fused group's loops skip this member
         if (conv && a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
-        if (!conv) mx_begin_pass(a, out[1]);
+        if (!conv) {
+            if (a.grp) atomicAdd(&a.grp->outer_active, 1);
+            mx_begin_pass(a, out[1]);
+        }
     }
 }
 
 // Sums of FP32 values over a block, fixed order (warp butterflies, then warp 0
 // over the warp totals); thread 0 writes them to partials[q * gridDim.x + block].
 template <int NQ>
-__device__ __forceinline__ void block_partials_f32(float (&v)[NQ], float* partials) {
+__device__ __forceinline__ void block_partials_f32(float (&v)[NQ], float* partials, unsigned int blk, unsigned int nblk) {
     __shared__ float sh[NQ][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -550,7 +568,7 @@ __device__ __forceinline__ void block_partials_f32(float (&v)[NQ], float* partia
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const float t = warp_sum(lane < nw ? sh[q][lane] : 0.0f);
-            if (lane == 0) partials[(size_t)q * gridDim.x + blockIdx.x] = t;
+            if (lane == 0) partials[(size_t)q * nblk + blk] = t;
         }
 }
 
@@ -635,25 +653,35 @@ __device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float
 
 // 8 blocks of 256 threads a SM (32 registers): the gathers of u are latency-bound, and at
 // 5.75M rows a probe of this SpMV took 218 us at 8 blocks a SM against 244 us at 6.
-__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv(MixArgs a) {
+// One block of the deferred-dot FP32 SpMV: block blk of a launch of nblk blocks for the
+// machine of `a` (its own launch, or its range of a fused group launch).
+template <bool GROUP>
+__device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, unsigned nblk) {
     CgState* s = a.cg;
     if (s->done) {  // an iteration after the stop (rest of the loop body, host-driven lookahead)
-        mx_done_on_entry(a);
+        if (!GROUP && blk == 0) mx_done_on_entry(a);
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && s->pending) {
+    if (blk == 0 && threadIdx.x == 0 && s->pending) {
         s->gamma = s->nx_gamma;
         s->alpha = s->nx_alpha;
         s->iter += 1;
         s->pending = 0;
     }
     float v[3] = {0.0f, 0.0f, 0.0f};
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
     if (i < a.n) mx_spmv_row(a, i, v);
-    block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials));
+    block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials), blk, nblk);
 }
 
-__global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
+__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv(MixArgs a) { mx_spmv_block<false>(a, blockIdx.x, gridDim.x); }
+
+// One block of the FP32 CG update (deferred dots), block blk of nblk for the machine of
+// `a`; in a fused group (GROUP) the stop clears the group's loop condition when the last
+// member stops.
+template <bool GROUP>
+__device__ __forceinline__ void mx_update_block(const MixArgs& a, unsigned blk, unsigned nblk, const GroupArgs& g) {
+    if (GROUP && a.ms->done) return;  // a member whose refinement converged in an earlier pass
     CgState* s = a.cg;
     __shared__ double prev[3];  // gamma_prev, alpha_prev, bb
     __shared__ float step[2];
@@ -671,8 +699,8 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     // sums and the step lengths, so that their latency overlaps that chain; not by a
     // thread that already sees the stop flag (set by an earlier kernel, or by this
     // one's block 0 when it stops the solve, in which case no block updates rows)
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    const int64_t i0 = (int64_t)blk * blockDim.x + threadIdx.x;
     float u0[MX_UPDATE_ROWS], w0[MX_UPDATE_ROWS], p0[MX_UPDATE_ROWS], s0[MX_UPDATE_ROWS], d0[MX_UPDATE_ROWS],
         r0[MX_UPDATE_ROWS], q0[MX_UPDATE_ROWS];
     const bool live = !s->done;
@@ -714,14 +742,19 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
         stop = st;
         step[0] = (float)alpha;
         step[1] = (float)beta;
-        if (blockIdx.x == 0) {
+        if (blk == 0) {
             s->runs += 1;
             *a.loop_kernels += 2;
             s->rr = rr;
             if (st) {
-                *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
+                *a.loop_kernels += 2 * (GROUP ? g.tail_pairs : a.tail_pairs);  // the rest of the body returns
                 s->done = 1;
-                if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+                if (GROUP) {
+                    if (atomicSub(&g.gs->inner_active, 1) == 1)
+                        cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_inner, 0u);
+                } else if (a.h_inner) {
+                    cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+                }
             } else {
                 s->nx_gamma = gamma;
                 s->nx_alpha = alpha;
@@ -755,6 +788,10 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
         }
     }
     for (int64_t i = i0 + MX_UPDATE_ROWS * stride; i < a.n; i += stride) mx_update_row(a, i, alpha, beta, first);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
+    mx_update_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
@@ -808,9 +845,13 @@ __global__ void k_mx_update_red(MixArgs a) {
 // r0 = b - A x0 formed in FP64 (k_mx_init); only the correction-sized term
 // A d of a pass is applied with the FP32 operator (an FP32 SpMV of d), so its
 // rounding is relative to the correction, not to b. Outer stop test.
-__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
+// One block of the end of a refinement pass (see k_mx_refine), block blk of nblk for the
+// machine of `a`; in a fused group the outer loop stops with the last member's convergence.
+template <bool GROUP>
+__device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, unsigned nblk, const GroupArgs& g) {
+    if (GROUP && a.ms->done) return;  // a member whose refinement converged in an earlier pass
     double v[1] = {0.0};
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
     if (i < a.n) {
         const float d = a.Dl[i];
         a.X[i] += (double)d;
@@ -823,7 +864,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
         v[0] += res * res;
     }
     double out[1];
-    if (reduce_last2<1>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
+    if (reduce_last2_at<1>(v, a.partials, a.gpartials, a.counter, out, blk, nblk) && threadIdx.x == 0) {
         MixState* s = a.ms;
         s->rr = out[0];
         s->passes += 1;
@@ -833,11 +874,93 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
         if (conv || s->passes >= a.max_refine) {
             s->done = 1;
             if (!conv) atomicExch(a.status, (int)SDC_ERR_NOT_CONVERGED);
-            if (a.h_outer) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
+            if (GROUP) {
+                if (atomicSub(&g.gs->outer_active, 1) == 1)
+                    cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_outer, 0u);
+            } else if (a.h_outer) {
+                cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_outer, 0u);
+            }
         } else {
             mx_begin_pass(a, out[0]);
+            if (GROUP) cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_inner, 1u);
         }
     }
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
+    mx_refine_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
+}
+
+// Fused group launches: the member of each block and its block within the member's range.
+__device__ __forceinline__ const MixArgs& group_member(const GroupArgs& g, const GroupLaunch& L, unsigned& blk,
+                                                       unsigned& nblk) {
+    const int m = L.member[blockIdx.x];
+    const int f = L.first[m];
+    blk = blockIdx.x - (unsigned)f;
+    nblk = (unsigned)(L.first[m + 1] - f);
+    return g.args[m];
+}
+
+// Start of a fused group's solve, after every member's k_mx_init: the refinement loop runs
+// if any member has a pass to do.
+__global__ void k_group_begin(GroupArgs g) {
+    if (threadIdx.x == 0) {
+        g.gs->passes = 0;
+        g.gs->launches = 0;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_outer, g.gs->outer_active > 0 ? 1u : 0u);
+    }
+}
+
+// End of a fused group's solve: the counters start the next solve at zero, whatever ended
+// this one.
+__global__ void k_group_end(GroupArgs g) {
+    if (threadIdx.x == 0) {
+        g.gs->outer_active = 0;
+        g.gs->inner_active = 0;
+    }
+}
+
+// The group's loops must end even if no member stops them: a caps count failure of the
+// group (every member's status gets SDC_ERR_NOT_CONVERGED).
+__device__ __forceinline__ void group_cap_failed(const GroupArgs& g) {
+    for (int m = 0; m < g.n_members; ++m) atomicExch(g.args[m].status, (int)SDC_ERR_NOT_CONVERGED);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_g(GroupArgs g) {
+    // the inner loop ends after this body when no member's CG runs (the counter changes only
+    // in the updates, outside this launch) or after launch_cap SpMV launches in the pass
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int n = ++g.gs->launches;
+        if (g.gs->inner_active <= 0 || n > g.launch_cap) {
+            cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_inner, 0u);
+            if (n > g.launch_cap) group_cap_failed(g);
+        }
+    }
+    unsigned blk, nblk;
+    const MixArgs& a = group_member(g, g.spmv, blk, nblk);
+    mx_spmv_block<true>(a, blk, nblk);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update_g(GroupArgs g) {
+    unsigned blk, nblk;
+    const MixArgs& a = group_member(g, g.update, blk, nblk);
+    mx_update_block<true>(a, blk, nblk, g);
+}
+
+__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine_g(GroupArgs g) {
+    // the outer loop ends after this pass when no member is refining or after pass_cap passes
+    // (members that go on set the inner loop's condition again for their next pass)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int n = ++g.gs->passes;
+        g.gs->launches = 0;
+        if (g.gs->outer_active <= 0 || n >= g.pass_cap) {
+            cudaGraphSetConditional((cudaGraphConditionalHandle)g.h_outer, 0u);
+            if (n >= g.pass_cap && g.gs->outer_active > 0) group_cap_failed(g);
+        }
+    }
+    unsigned blk, nblk;
+    const MixArgs& a = group_member(g, g.refine, blk, nblk);
+    mx_refine_block<true>(a, blk, nblk, g);
 }
 
 // Diagnostics of a mixed solve: the true residual ||b - (m x + dtau K x)|| / ||b|| with the

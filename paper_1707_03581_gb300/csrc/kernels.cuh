@@ -66,6 +66,37 @@ struct CgArgs {
 constexpr int MIX_DEFER_MAX_BLOCKS = 2048;
 constexpr int MX_UPDATE_ROWS = 2;       // rows a thread of k_mx_update loads before the dot sums
 
+// Counters of a fused group of machines (see GroupArgs) during one implicit solve.
+struct GroupState {
+    int outer_active;               // members whose refinement has not converged
+    int inner_active;               // members whose inner FP32 CG of the current pass runs
+    int passes;                     // refinement launches of the current solve
+    int launches;                   // SpMV launches of the current pass
+};
+
+struct MixArgs;
+
+// Block ranges of one fused launch: member m owns blocks [first[m], first[m + 1]).
+struct GroupLaunch {
+    const int* member;              // [blocks] member of each block
+    const int* first;               // [members + 1]
+};
+
+// Fused FP32 CG of several machines of a batch (one launch per kernel over all members'
+// blocks). Each member keeps its own MixArgs, block partition, partial sums and scalars,
+// so that its arithmetic is that of its own launches; the loop conditions are shared and
+// cleared when the last member stops.
+struct GroupArgs {
+    const MixArgs* args;            // [members] the members' arguments of this solve
+    GroupLaunch spmv, update, refine;
+    GroupState* gs;
+    unsigned long long h_outer, h_inner;
+    int tail_pairs;                 // (spmv, update) pairs after this one in the loop body
+    int n_members;
+    int launch_cap;                 // SpMV launches of a pass after which the inner loop stops
+    int pass_cap;                   // refinement launches after which the outer loop stops
+};
+
 struct MixArgs {
     EllDev A;                       // val (FP64) for residuals, val32 for the inner solves
     const double* mass;
@@ -94,6 +125,7 @@ struct MixArgs {
     double rtol2;                   // outer: ||b - A x||^2 <= rtol2 ||b||^2
     double inner_rtol2;             // inner: ||r||^2 <= inner_rtol2 ||r_0||^2
     unsigned long long h_outer, h_inner;
+    GroupState* grp;                // fused group the solve runs in, or NULL
 };
 
 // Right-hand side of the implicit stage.
@@ -282,6 +314,11 @@ __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_update_red(MixArgs a);
 __global__ void k_mx_refine(MixArgs a);
 __global__ void k_mx_true_residual(MixArgs a);
+__global__ void k_group_begin(GroupArgs g);
+__global__ void k_group_end(GroupArgs g);
+__global__ void k_mx_spmv_g(GroupArgs g);
+__global__ void k_mx_update_g(GroupArgs g);
+__global__ void k_mx_refine_g(GroupArgs g);
 __global__ void k_bulk_endpoint(BulkArgs a);
 __global__ void k_bulk_endpoint_mx(BulkArgs a);
 __global__ void k_fi_mx(FiDevArgs a);

@@ -110,3 +110,48 @@ def test_batch_of_large_machines_equals_members_alone(torch):
     b.close()
     for s in members:
         s.close()
+
+
+def test_fused_batch_equals_members_alone(torch):
+    # The block-diagonal form (sdc_batch_set_fused): the FP32 inner CG of the qualifying
+    # members (mixed precision, deferred-dot grids) runs as one launch per kernel over all of
+    # them. Members of four resolutions of the batched workload (12,902 to 313,646 DOF) and
+    # a machine of another scheme; an FP64 member does not qualify and keeps its own graph.
+    from paper_1707_03581_gb300 import Batch, SdcError
+    from synth.machines import batch_resolutions
+
+    first = batch_resolutions()
+    pool = machine_config(3, select={first[16], first[24], first[32], first[48]})
+    cases = [(m, "mixed") for m in pool] + [(machine_config(0), "mixed"), (pool[0], "fp64")]
+    steps = 3
+    alone = []
+    for mach, prec in cases:
+        s = _solver(torch, mach, prec)
+        s.run_horizon(steps)
+        alone.append(s.temperature())
+        s.close()
+    members = [_solver(torch, mach, prec) for mach, prec in cases]
+    b = Batch(0)
+    for s in members:
+        b.add(s)
+    b.set_fused(True)
+    assert b.fused_size() == 5  # the mixed members; machine_config(0) shares their scheme
+    b.step([1] * len(members), wait=False)
+    b.step([2] * len(members), wait=True)
+    for s, ref, (mach, prec) in zip(members, alone, cases):
+        assert np.array_equal(s.temperature(), ref), (mach.name, prec)
+    # fused members step together
+    with pytest.raises(SdcError):
+        b.step([1, 2, 1, 1, 1, 1], wait=True)
+    # and the batch goes on after fusion is switched off, still equal to members alone
+    b.set_fused(False)
+    assert b.fused_size() == 0
+    b.step([1] * len(members), wait=True)
+    for s, (mach, prec) in zip(members, cases):
+        r = _solver(torch, mach, prec)
+        r.run_horizon(steps + 1)
+        assert np.array_equal(s.temperature(), r.temperature()), (mach.name, prec)
+        r.close()
+    b.close()
+    for s in members:
+        s.close()
