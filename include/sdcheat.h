@@ -434,10 +434,13 @@ sdc_status sdc_solve(sdc_ctx* ctx, double dtau, const double* b_dev, double* x_d
  * grids and launch order as a macro step's CG loop. The stop test is disabled so that every
  * iteration works; spmv_only != 0 launches only the SpMV kernel of each iteration. *ms
  * receives the milliseconds of the n_iters iterations (CUDA events on the context's stream
- * around that graph; an initial-residual kernel runs before the first event). Uses the
- * step's work buffers, not T(t_n); waits. SDC_ERR_ARG unless 1 <= n_iters <= 4096, dtau > 0.
- * Needs sdc_set_temperature. */
-sdc_status sdc_time_cg_iterations(sdc_ctx* ctx, double dtau, int32_t n_iters, int32_t spmv_only, float* ms);
+ * around that graph; an initial-residual kernel runs before the first event). If ms_spmv is
+ * not NULL, the same iterations run again from the same start with event records around
+ * every SpMV inside the graph, and *ms_spmv receives the sum of the SpMVs' durations. Uses
+ * the step's work buffers, not T(t_n); waits. SDC_ERR_ARG unless 1 <= n_iters <= 4096 and
+ * dtau > 0. Needs sdc_set_temperature. */
+sdc_status sdc_time_cg_iterations(sdc_ctx* ctx, double dtau, int32_t n_iters, int32_t spmv_only, float* ms,
+                                  float* ms_spmv);
 
 /* f^E(T, t) on all DOFs (zero away from the contact): Sec. 2, the contact
  * and friction terms of Eq. femContFix / femContMov. */

@@ -107,7 +107,8 @@ _SIGS = {
     "sdc_set_wait_limit": (C.c_int, [_vp, C.c_int64]),
     "sdc_set_update_blocks": (C.c_int, [_vp, C.c_int]),
     "sdc_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(TuneReport)]),
-    "sdc_time_cg_iterations": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_float)]),
+    "sdc_time_cg_iterations": (C.c_int, [_vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                         C.POINTER(C.c_float)]),
     "sdc_contact_flux": (C.c_int, [_vp, _vp, C.c_double, _vp]),
     "sdc_heat_totals_noalloc": (C.c_int, [_vp, _vp, _vp]),
     "sdc_poll": (C.c_int, [_vp, C.POINTER(C.c_int)]),
@@ -450,12 +451,14 @@ class Solver:
         """Polls of each bounded exchange wait of the contact loop (0 = default; sdc_set_wait_limit)."""
         self._call("sdc_set_wait_limit", int(polls))
 
-    def time_cg_iterations(self, dtau: float, n_iters: int, spmv_only: bool = False) -> float:
+    def time_cg_iterations(self, dtau: float, n_iters: int, spmv_only: bool = False, per_spmv: bool = False):
         """Device milliseconds of n_iters consecutive CG iterations of the implicit stage in
-        the scheme's precision, launched as one CUDA graph (sdc_time_cg_iterations)."""
-        ms = C.c_float(0.0)
-        self._call("sdc_time_cg_iterations", float(dtau), int(n_iters), 1 if spmv_only else 0, C.byref(ms))
-        return float(ms.value)
+        the scheme's precision, launched as one CUDA graph (sdc_time_cg_iterations); with
+        per_spmv, also the summed durations of their SpMVs (events inside the graph)."""
+        ms, ms_spmv = C.c_float(0.0), C.c_float(0.0)
+        self._call("sdc_time_cg_iterations", float(dtau), int(n_iters), 1 if spmv_only else 0, C.byref(ms),
+                   C.byref(ms_spmv) if per_spmv else None)
+        return (float(ms.value), float(ms_spmv.value)) if per_spmv else float(ms.value)
 
     def solve(self, dtau, b, x0):
         b = self._dev(b)

@@ -359,6 +359,13 @@ struct Chain {
         SDC_CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributeClusterDimension, &v));
         last = nd;
     }
+    // event record node on the chain (graph mode only)
+    void event(cudaEvent_t e) {
+        cudaGraphNode_t nd;
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddEventRecordNode(&nd, g, d.data(), d.size(), e));
+        last = nd;
+    }
     void copy(void* dst, const void* src, size_t bytes) {
         if (is_eager) {
             SDC_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, eager));
@@ -2012,7 +2019,8 @@ sdc_status sdc_solve(sdc_ctx* c, double dtau, const double* b, double* x, int32_
     });
 }
 
-sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int32_t spmv_only, float* ms) {
+sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int32_t spmv_only, float* ms,
+                                  float* ms_spmv) {
     return guarded(c, [&] {
         require(n_iters >= 1 && n_iters <= 4096, SDC_ERR_ARG, "n_iters must be in 1..4096");
         require(ms != nullptr, SDC_ERR_ARG, "ms is NULL");
@@ -2033,42 +2041,64 @@ sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int3
         r.b_in = c->d_genv;
         r.x0 = c->Tn;
         r.pos = c->C.pos;
-        cudaGraph_t g[2];
-        SDC_CUDA_TRY(cudaGraphCreate(&g[0], 0));
-        std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> g0(g[0], &cudaGraphDestroy);
-        SDC_CUDA_TRY(cudaGraphCreate(&g[1], 0));
-        std::unique_ptr<CUgraph_st, decltype(&cudaGraphDestroy)> g1(g[1], &cudaGraphDestroy);
-        Chain init(g[0]), body(g[1]);
-        if (mixed) init.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, ma, r);
-        else init.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, ca, r);
-        for (int k = 0; k < n_iters; ++k) {
-            if (mixed) {
-                body.kernel(ma.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, ma);
-                if (!spmv_only)
-                    body.kernel(ma.defer ? k_mx_update : k_mx_update_red,
-                                ma.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, ma);
-            } else {
-                body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, ca);
-                if (!spmv_only) body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, ca);
-            }
-        }
-        cudaGraphExec_t ex[2] = {nullptr, nullptr};
-        cudaEvent_t ev[2] = {nullptr, nullptr};
+        // graph 0: the initial residual; graph 1: the iterations; graph 2 (ms_spmv): the same
+        // iterations with event records around every SpMV
+        const int n_graphs = ms_spmv ? 3 : 2;
+        std::vector<cudaGraph_t> g(n_graphs, nullptr);
+        std::vector<cudaGraphExec_t> ex(n_graphs, nullptr);
+        std::vector<cudaEvent_t> ev;
         auto release = [&] {
             for (auto e : ex)
                 if (e) cudaGraphExecDestroy(e);
-            for (auto e : ev)
-                if (e) cudaEventDestroy(e);
+            for (auto x : g)
+                if (x) cudaGraphDestroy(x);
+            for (auto e : ev) cudaEventDestroy(e);
         };
         try {
-            for (int k = 0; k < 2; ++k) SDC_CUDA_TRY(cudaGraphInstantiate(&ex[k], g[k], 0));
-            for (int k = 0; k < 2; ++k) SDC_CUDA_TRY(cudaEventCreate(&ev[k]));
+            for (int k = 0; k < n_graphs; ++k) SDC_CUDA_TRY(cudaGraphCreate(&g[k], 0));
+            const int n_ev = 2 + (ms_spmv ? 2 * n_iters : 0);
+            for (int k = 0; k < n_ev; ++k) {
+                cudaEvent_t e;
+                SDC_CUDA_TRY(cudaEventCreate(&e));
+                ev.push_back(e);
+            }
+            Chain init(g[0]);
+            if (mixed) init.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, ma, r);
+            else init.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, ca, r);
+            for (int gi = 1; gi < n_graphs; ++gi) {
+                Chain body(g[gi]);
+                for (int k = 0; k < n_iters; ++k) {
+                    if (gi == 2) body.event(ev[2 + 2 * k]);
+                    if (mixed) body.kernel(ma.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, ma);
+                    else body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, ca);
+                    if (gi == 2) body.event(ev[3 + 2 * k]);
+                    if (spmv_only) continue;
+                    if (mixed)
+                        body.kernel(ma.defer ? k_mx_update : k_mx_update_red,
+                                    ma.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, ma);
+                    else
+                        body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, ca);
+                }
+            }
+            for (int k = 0; k < n_graphs; ++k) SDC_CUDA_TRY(cudaGraphInstantiate(&ex[k], g[k], 0));
             SDC_CUDA_TRY(cudaGraphLaunch(ex[0], c->stream));
             SDC_CUDA_TRY(cudaEventRecord(ev[0], c->stream));
             SDC_CUDA_TRY(cudaGraphLaunch(ex[1], c->stream));
             SDC_CUDA_TRY(cudaEventRecord(ev[1], c->stream));
             SDC_CUDA_TRY(cudaEventSynchronize(ev[1]));
             SDC_CUDA_TRY(cudaEventElapsedTime(ms, ev[0], ev[1]));
+            if (ms_spmv) {  // the same iterations again from the same start, timed per SpMV
+                SDC_CUDA_TRY(cudaGraphLaunch(ex[0], c->stream));
+                SDC_CUDA_TRY(cudaGraphLaunch(ex[2], c->stream));
+                SDC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+                double sum = 0.0;
+                for (int k = 0; k < n_iters; ++k) {
+                    float t = 0.f;
+                    SDC_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 + 2 * k], ev[3 + 2 * k]));
+                    sum += t;
+                }
+                *ms_spmv = (float)sum;
+            }
         } catch (...) {
             release();
             throw;
