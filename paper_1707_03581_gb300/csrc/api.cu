@@ -98,6 +98,7 @@ struct sdc_ctx {
     double* ihat[2] = {nullptr, nullptr};
     double *cpre = nullptr, *fst = nullptr;
     double* fe_base = nullptr;      // mixed: f^E(T_{m-1}) at the interval's embedded nodes
+    double* Tc = nullptr;           // mixed: T_{m-1} on the contact DOFs (k_iface_tc)
     int iface_cluster = 0;          // CTAs of the substep-loop cluster
     int iface_chunk = 0;            // replica slots per CTA of that cluster
     bool iface_global = false;      // replicas in global memory (large interfaces)
@@ -970,6 +971,7 @@ void alloc_scheme_buffers(sdc_ctx* c) {
     // implicit Euler forms one slot in FP64 in both precisions (its coupling is in the matrix)
     c->ie_coef = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)MAXE * NI) : c->E.coef;
     c->fe_base = mixed ? dalloc_n<double>(c, c->pool_scheme, (size_t)(P + 1) * NI) : nullptr;
+    c->Tc = mixed ? dalloc_n<double>(c, c->pool_scheme, std::max<size_t>(NI, 1)) : nullptr;
     // dt-scaled weights
     std::vector<double> Stil(W.Stil), Semb(W.Semb), Shat(W.Shat), slot_pos(slots);
     for (double& v : Stil) v *= c->dt;
@@ -1083,6 +1085,12 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         pa.E = c->E;
         pa.slot0 = ii * (P + 1);
         pa.Tprev = c->Tstd[m - 1];
+        pa.Tc = c->Tc;
+        if (c->Tc) {  // mixed: the contact DOFs' T_{m-1} packed first, in the same branch
+            const cudaGraphNode_t t = ch.branch_kernel(on, k_iface_tc, dim3(blocks_for(std::max<int64_t>(NI, 1), 256)),
+                                                       dim3(256u), c->C, (const double*)c->Tstd[m - 1], c->Tc);
+            return ch.branch_kernel({t}, k_iface_prep, dim3(blocks_for((int64_t)(P + 1) * NI, 256)), dim3(256u), pa);
+        }
         return ch.branch_kernel(on, k_iface_prep, dim3(blocks_for((int64_t)(P + 1) * NI, 256)), dim3(256u), pa);
     };
     // the cluster loop of interval ii, after the bulk endpoint and the interval's prep
@@ -1449,7 +1457,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_cg_update, "k_cg_update"},
         {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
         {(const void*)k_iface_geom_mx, "k_iface_geom_mx"},
-        {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_loop, "k_iface_loop"},
+        {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_tc, "k_iface_tc"},   {(const void*)k_iface_loop, "k_iface_loop"},
         {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},

@@ -1423,6 +1423,13 @@ __device__ __forceinline__ double substep_dt(const IfaceArgs& a, double tn, int 
     return __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
 }
 
+// T on the contact DOFs by contact index, Tc[i] = T[dof[i]]: the gathers of k_iface_prep then
+// take one load a coupling entry instead of two dependent ones.
+__global__ void k_iface_tc(ContactDev C, const double* __restrict__ T, double* __restrict__ Tc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C.n_iface) Tc[i] = T[C.dof[i]];
+}
+
 // c_p of every substep and contact DOF (see PrepArgs); one thread per (p, DOF),
 // p = 0..P (p = 0 only forms base_0 in mixed precision).
 __global__ void k_iface_prep(PrepArgs a) {
@@ -1438,12 +1445,12 @@ __global__ void k_iface_prep(PrepArgs a) {
         const int slot = a.slot0 + p;
         const size_t so = (size_t)slot * NI + i;
         const int n = a.E.cnt[so];
-        const double Ta = a.Tprev[a.C.dof[i]];
+        const double Ta = a.Tc[i];
         double acc = a.E.cst[so];
         for (int k = 0; k < n; ++k) {
             const size_t o = ((size_t)slot * MAXE + k) * NI + i;
             const int j = a.E.idx[o];
-            acc = fma((double)a.E.coef32[o], a.Tprev[a.C.dof[j]] - Ta, acc);
+            acc = fma((double)a.E.coef32[o], a.Tc[j] - Ta, acc);
         }
         a.base[(size_t)p * NI + i] = acc;
     }

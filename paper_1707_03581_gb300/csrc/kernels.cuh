@@ -226,6 +226,7 @@ struct PrepArgs {
     CouplingOp E;                   // indices are contact-DOF ids
     int slot0;
     const double* Tprev;
+    const double* Tc;               // mixed: T_{m-1} on the contact DOFs, by contact index (k_iface_tc)
 };
 
 // Single-rate SDC on the contact DOFs: f^E at one slot, and the implicit stage's contact terms.
@@ -327,6 +328,7 @@ __global__ void k_iface_geom_mx(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,
                                 int phase);
 __global__ void k_iface_prep(PrepArgs a);
+__global__ void k_iface_tc(ContactDev C, const double* T, double* Tc);
 __global__ void k_iface_loop(IfaceArgs a);
 __global__ void k_iface_loop1(IfaceArgs a);
 __global__ void k_iface_loop_gl(IfaceArgs a);
