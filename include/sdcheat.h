@@ -210,8 +210,11 @@ sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
 
 /* Placement of the contact substep loop's replicas of the contact temperatures:
  * 0 (default) = shared memory of each CTA of the loop's cluster when they fit,
- * else global memory; 1 = always global memory (for tests and tuning).
- * Results are identical. */
+ * else global memory; 1 = always global memory; 2 = global memory and gathers from
+ * there. Global replicas are otherwise staged: after each substep one bulk copy brings
+ * the whole replica into the CTA's shared memory when it fits (one buffer), and the
+ * gathers read it there. For tests and tuning: results are identical; SDC_ERR_ARG
+ * outside 0..2. */
 sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
 
 /* Side branches in the macro-step graph (1, default): the contact coupling
@@ -248,7 +251,7 @@ typedef struct {
     int32_t contact_cluster_cap;  /* cap on the contact loop's cluster (sdc_set_contact_cluster; 0 =
                                      automatic)                                                     */
     int32_t contact_cluster;      /* the cluster size that results                                 */
-    int32_t contact_global;       /* 1: replicas in global memory                                  */
+    int32_t contact_global;       /* 1: replicas in global memory (staged), 2: global, unstaged     */
     int32_t graph_branches;       /* sdc_set_graph_branches                                        */
     int32_t trials;               /* option sets timed (0 when taken from the cache)               */
     int32_t cached;               /* 1: picks of an earlier context of the same shape              */

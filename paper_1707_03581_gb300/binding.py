@@ -299,9 +299,10 @@ class Solver:
         """True: plain kernel launches with host-driven CG loops (profiling/debugging)."""
         self._call("sdc_set_execution", 1 if eager else 0)
 
-    def set_contact_replicas(self, global_memory: bool):
-        """Force the contact loop's replicas into global memory (True) or choose automatically."""
-        self._call("sdc_set_contact_replicas", 1 if global_memory else 0)
+    def set_contact_replicas(self, global_memory):
+        """Replica placement of the contact loop: False/0 automatic, True/1 global memory
+        (staged in shared memory each substep when it fits), 2 global without staging."""
+        self._call("sdc_set_contact_replicas", int(global_memory))
 
     STEPPERS = {"mrsdc": 0, "sisdc": 1, "implicit_euler": 2}
 

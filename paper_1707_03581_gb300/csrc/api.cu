@@ -102,6 +102,7 @@ struct sdc_ctx {
     int iface_cluster = 0;          // CTAs of the substep-loop cluster
     int iface_chunk = 0;            // replica slots per CTA of that cluster
     bool iface_global = false;      // replicas in global memory (large interfaces)
+    bool iface_stage = false;       // global replicas staged in shared memory each substep
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
@@ -832,7 +833,8 @@ void do_assemble(sdc_ctx* c) {
 // (one DOF per thread when the chunk fits the block; global replicas when two
 // shared-memory replicas do not fit in a CTA).
 using IfaceKernel = void (*)(IfaceArgs);
-IfaceKernel iface_loop_kernel(bool mixed, int chunk, bool global) {
+IfaceKernel iface_loop_kernel(bool mixed, int chunk, bool global, bool stage = false) {
+    if (global && stage) return mixed ? k_iface_loop_mx_gls : k_iface_loop_gls;
     if (global) return mixed ? k_iface_loop_mx_gl : k_iface_loop_gl;
     const bool one = chunk <= IFACE_THREADS;
     if (mixed) return one ? k_iface_loop_mx1 : k_iface_loop_mx;
@@ -863,14 +865,16 @@ void pick_iface_cluster(sdc_ctx* c) {
     size_t smem_cap = (size_t)optin;
     for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
                           (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
-                          (const void*)k_iface_loop_mx_gl}) {
+                          (const void*)k_iface_loop_mx_gl, (const void*)k_iface_loop_gls,
+                          (const void*)k_iface_loop_mx_gls}) {
         cudaFuncAttributes fa{};
         SDC_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
         smem_cap = std::min(smem_cap, (size_t)optin - fa.sharedSizeBytes);
     }
     for (const void* k : {(const void*)k_iface_loop, (const void*)k_iface_loop1, (const void*)k_iface_loop_gl,
                           (const void*)k_iface_loop_mx, (const void*)k_iface_loop_mx1,
-                          (const void*)k_iface_loop_mx_gl}) {
+                          (const void*)k_iface_loop_mx_gl, (const void*)k_iface_loop_gls,
+                          (const void*)k_iface_loop_mx_gls}) {
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
@@ -897,8 +901,12 @@ void pick_iface_cluster(sdc_ctx* c) {
             if (chunk > IFACE_THREADS * IFACE_PER_THREAD_GL) continue;
             global = true;
         }
-        const size_t smem = global ? 0 : rep_bytes;
-        const void* kern = (const void*)iface_loop_kernel(mixed, chunk, global);
+        // global replicas are staged in shared memory (one buffer) when it fits, unless
+        // sdc_set_contact_replicas asked for the unstaged form
+        const size_t stage_bytes = (size_t)cs * chunk * esz;
+        const bool stage = global && c->force_global != 2 && stage_bytes <= smem_cap;
+        const size_t smem = global ? (stage ? stage_bytes : 0) : rep_bytes;
+        const void* kern = (const void*)iface_loop_kernel(mixed, chunk, global, stage);
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(iface_loop_threads(chunk, global));
@@ -916,6 +924,7 @@ void pick_iface_cluster(sdc_ctx* c) {
             c->iface_chunk = chunk;
             c->iface_smem = smem;
             c->iface_global = global;
+            c->iface_stage = stage;
             c->iface_rep = global ? dalloc(c, c->pool_scheme, rep_bytes) : nullptr;
             return;
         }
@@ -1122,7 +1131,8 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.rep_global = c->iface_rep;
         ia.sent = c->iface_sent;
         ia.poll_limit = c->poll_limit;
-        ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global),
+        ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global,
+                                            c->iface_stage),
                           (unsigned)c->iface_cluster, (unsigned)iface_loop_threads(c->iface_chunk, c->iface_global),
                           c->iface_smem,
                           (unsigned)c->iface_cluster, ia);
@@ -1461,6 +1471,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
+        {(const void*)k_iface_loop_gls, "k_iface_loop_gls"}, {(const void*)k_iface_loop_mx_gls, "k_iface_loop_mx_gls"},
         {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
         {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"}, {(const void*)k_ie_init, "k_ie_init"},
         {(const void*)k_ie_spmv, "k_ie_spmv"},
@@ -1765,7 +1776,8 @@ sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
 
 sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
     return guarded(c, [&] {
-        c->force_global = global ? 1 : 0;
+        require(global >= 0 && global <= 2, SDC_ERR_ARG, "replica placement is 0, 1 or 2");
+        c->force_global = global;
         c->buffers_ready = false;
         c->graph_ready = false;
     });
@@ -2824,8 +2836,16 @@ extern "C" sdc_status sdc_autotune(sdc_ctx* c, int32_t trial_steps, sdc_tune_rep
             const int auto_cs = c->iface_cluster;
             for (int cs = auto_cs / 2; cs >= 1 && cs >= auto_cs / 4; cs /= 2)
                 consider({best.unroll, best.update_bps, cs, best.global, best.branches});
-            if (!best.global && !c->iface_global)
+            // replica placement, from the layout the best options give
+            apply_opts(c, best);
+            ensure_ready(c);
+            const bool best_global = c->iface_global, best_stage = c->iface_stage;
+            if (!best_global) {
                 consider({best.unroll, best.update_bps, best.cluster_cap, 1, best.branches});
+                consider({best.unroll, best.update_bps, best.cluster_cap, 2, best.branches});
+            } else if (best_stage) {
+                consider({best.unroll, best.update_bps, best.cluster_cap, 2, best.branches});
+            }
             if (!c->in_batch) consider({best.unroll, best.update_bps, best.cluster_cap, best.global, 1 - best.branches});
             apply_opts(c, best);
             ensure_ready(c);

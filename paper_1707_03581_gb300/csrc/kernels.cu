@@ -1569,7 +1569,7 @@ __device__ bool iface_drain(const int* sent, int rank, int cs, int n_sent, int P
 //   stays FP64.
 // Every f^E of the current iterate is stored for the next sweep, and
 // ihat = sum_q dt shat_{m,q} f^E_q (its part of I_{m-1}^m) is accumulated.
-template <bool MIX, int PER, bool GL>
+template <bool MIX, int PER, bool GL, bool STG = false>
 __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     // one contact DOF per thread leaves registers to prefetch a whole typical row
     constexpr int B = PER == 1 ? (MIX ? 24 : 16) : (PER == 2 ? IFACE_BATCH : 4);
@@ -1584,8 +1584,14 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     const int chunk = a.chunk;
     const int P = a.P;
     // [2][cs * chunk]: shared memory, or (GL) global memory for interfaces whose replicas do not
-    // fit in shared memory; then owners store their chunk and a cluster barrier publishes it
+    // fit in shared memory; then owners store their chunk and a cluster barrier publishes it.
+    // Staged (GL and a.stage): after that barrier one bulk copy brings the whole replica of the
+    // substep into shared memory (one buffer), and the gathers read it there instead of
+    // making dependent round trips to L2; the values are the same.
     V* rep = GL ? (V*)a.rep_global : reinterpret_cast<V*>(dyn);
+    V* stg = reinterpret_cast<V*>(dyn);
+    bool stage_on = GL && STG;
+    unsigned stage_issued = 0;  // staged copies issued (one mbarrier phase each, mbar[0])
     const int nthr = (int)blockDim.x;
     // the substep lengths and quadrature weights, formed once (FP64 runs at a small
     // fraction of the FP32 rate, so no thread repeats this work inside the loop)
@@ -1684,6 +1690,31 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         }
         if constexpr (GL) {
             cluster.sync();  // the chunks of this substep are in global memory
+            if (stage_on) {
+                const unsigned sbar = smem_addr(&mbar[0]);
+                const unsigned sbytes = (unsigned)((size_t)cs * chunk * sizeof(V));
+                if (threadIdx.x == 0) {
+                    // the cluster's generic stores to global memory and this CTA's generic reads
+                    // of the previous staged replica, ordered before the async-proxy copy
+                    asm volatile("fence.proxy.async;" ::: "memory");
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(sbytes)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_addr(stg)),
+                        "l"(buf), "r"(sbytes), "r"(sbar)
+                        : "memory");
+                }
+                ++stage_issued;
+                if (!mbar_wait(sbar, (stage_issued - 1) & 1u, a.poll_limit)) my_to = true;
+                // a wait that gave up ends the staging for the whole CTA: no further copy is
+                // issued (the step reports SDC_ERR_TIMEOUT), and the outstanding one is drained
+                // before exit
+                if (__syncthreads_or(my_to)) {
+                    stage_on = false;
+                    cta_to = true;
+                }
+            }
         } else {
         // generic-proxy writes of the own chunk become visible to the bulk copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1717,11 +1748,23 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
         for (int r = 0; r < PER; ++r) {
             const int i = own[r];
             if (i < 0) continue;
-            if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
-            else fe[r] = coupling_apply_shared<B, GL>(a.E, a.slot0 + p, NI, i, row[r], buf);
+            // staged: the gathers read the CTA's shared-memory copy of the replica
+            constexpr bool FROM_GLOBAL = GL && !STG;
+            const V* src = STG ? stg : buf;
+            if constexpr (MIX) fe[r] = bp[r] + (double)coupling_apply_shared32<B, FROM_GLOBAL>(a.E, a.slot0 + p, NI, i, row[r], src);
+            else fe[r] = coupling_apply_shared<B, FROM_GLOBAL>(a.E, a.slot0 + p, NI, i, row[r], src);
             a.fe_new[(size_t)p * NI + i] = fe[r];
             ih[r] = fma(s_shat[p], fe[r], ih[r]);
         }
+    }
+    if constexpr (GL) {
+        if (cta_to && threadIdx.x == 0) {
+            atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+            // the one staged copy that may still be in flight into this CTA's shared memory
+            if (!mbar_wait(smem_addr(&mbar[0]), (stage_issued - 1) & 1u, IFACE_DRAIN_POLLS))
+                atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+        }
+        __syncthreads();
     }
     if constexpr (!GL) {
         if (!cta_to) cta_to = __syncthreads_or(my_to);  // a wait of the last substep
@@ -1756,6 +1799,9 @@ __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_gl(IfaceArgs a) { 
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx1(IfaceArgs a) { iface_loop_impl<true, 1, false>(a); }
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx(IfaceArgs a) { iface_loop_impl<true, 2, false>(a); }
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx_gl(IfaceArgs a) { iface_loop_impl<true, 4, true>(a); }
+// global replicas staged in shared memory after every substep (one buffer of cs x chunk values)
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_gls(IfaceArgs a) { iface_loop_impl<false, 4, true, true>(a); }
+__global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop_mx_gls(IfaceArgs a) { iface_loop_impl<true, 4, true, true>(a); }
 
 // ------------------------------------------------------------------ diagnostics
 

@@ -335,6 +335,8 @@ __global__ void k_iface_loop_gl(IfaceArgs a);
 __global__ void k_iface_loop_mx(IfaceArgs a);
 __global__ void k_iface_loop_mx1(IfaceArgs a);
 __global__ void k_iface_loop_mx_gl(IfaceArgs a);
+__global__ void k_iface_loop_gls(IfaceArgs a);
+__global__ void k_iface_loop_mx_gls(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,
                        unsigned int* counter, double* heat);

@@ -434,12 +434,14 @@ def test_contact_cluster_sizes_are_bitwise_equal(torch, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
-    # the loop form for interfaces too large for shared memory, forced on a small machine
+@pytest.mark.parametrize("placement", [1, 2])
+def test_global_replica_loop_equals_shared_memory_loop(torch, precision, placement):
+    # the loop form for interfaces too large for shared memory, forced on a small machine:
+    # staged into shared memory after every substep (1) or gathered from global memory (2)
     mach = machine_config(0)
     a = _solver(mach, precision=precision)
     b = _solver(mach, precision=precision)
-    b.set_contact_replicas(True)
+    b.set_contact_replicas(placement)
     for _ in range(3):
         a.step(report=True)
         b.step(report=True)
@@ -448,7 +450,6 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision):
     b.set_kernel_timing(True)
     b.step(report=True)
     assert any(k.endswith("_gl") for k in b.kernel_times())
-
 
 
 def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):

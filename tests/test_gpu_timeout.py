@@ -4,7 +4,9 @@ A wait budget of one poll (sdc_set_wait_limit) makes the exchange waits of the c
 substep loop give up on copies that are still on their way, so the give-up path runs
 without any fault: the CTA whose wait gave up stops exchanging, drains the copies still
 addressed to it and reports SDC_ERR_TIMEOUT (the protocol is checked on the host in
-test_contact_exchange_model.py). Afterwards the default budget restores normal steps,
+test_contact_exchange_model.py). With global replicas the wait that gives up is the one for
+the CTA's own copy of the replica into shared memory: the CTA issues no further copy and
+drains that one before exit. Afterwards the default budget restores normal steps,
 bitwise equal to a context that never timed out.
 """
 
@@ -24,8 +26,8 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_wait_budget_of_one_poll_times_out_and_context_recovers(torch, precision):
+@pytest.mark.parametrize("precision,placement", [("fp64", 0), ("mixed", 0), ("fp64", 1), ("mixed", 1)])
+def test_wait_budget_of_one_poll_times_out_and_context_recovers(torch, precision, placement):
     from paper_1707_03581_gb300 import SdcError, Solver
 
     # a 16-CTA loop cluster: the r = 24 machine of the batch (about a thousand contact DOFs)
@@ -35,10 +37,14 @@ def test_wait_budget_of_one_poll_times_out_and_context_recovers(torch, precision
         (mach,) = machine_config(3, select={batch_resolutions()[24]})
     else:
         mach = machine_config(1)
+    # placement 1: global replicas, staged into shared memory after every substep; the wait
+    # that gives up is the one for the CTA's own staging copy
     s = Solver(0)
     s.set_machine(mach, precision=precision)
+    s.set_contact_replicas(placement)
     ref = Solver(0)
     ref.set_machine(mach, precision=precision)
+    ref.set_contact_replicas(placement)
     s.set_wait_limit(1)
     timed_out = False
     for _ in range(20):
