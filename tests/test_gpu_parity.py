@@ -449,16 +449,17 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision, placeme
     b.set_execution(True)
     b.set_kernel_timing(True)
     b.step(report=True)
-    assert any(k.endswith("_gl") for k in b.kernel_times())
+    suffix = "_gls" if placement == 1 else "_gl"
+    assert any(k.endswith(suffix) for k in b.kernel_times())
 
 
 def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):
     # 3,950 contact DOFs: 16 CTAs give one DOF a thread (k_iface_loop_mx1), 4 CTAs two
-    # (k_iface_loop_mx), 2 CTAs too many for shared memory forms (global replicas, the form
-    # of the 5.75M-DOF machine: k_iface_loop_mx_gl)
+    # (k_iface_loop_mx), 2 CTAs too many for shared memory forms (global replicas staged in
+    # shared memory after every substep, the form of the 5.75M-DOF machine: k_iface_loop_mx_gls)
     mach = machine_config(1)
     ref = None
-    for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx_gl")):
+    for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx_gls")):
         s = _solver(mach, precision="mixed")
         s.set_contact_cluster(cap)
         for _ in range(2):
