@@ -213,8 +213,11 @@ sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
  * else global memory; 1 = always global memory; 2 = global memory and gathers from
  * there. Global replicas are otherwise staged: after each substep one bulk copy brings
  * the whole replica into the CTA's shared memory when it fits (one buffer), and the
- * gathers read it there. For tests and tuning: results are identical; SDC_ERR_ARG
- * outside 0..2. */
+ * gathers read it there. 3 = the grid-wide loop: no cluster, one contact DOF a thread on
+ * as many co-resident CTAs (a cooperative launch) as the interface needs, global replicas
+ * published by a grid barrier with bounded waits (the step report's contact_cluster is then
+ * its CTA count; if the device cannot hold them, the cluster forms are used). For tests and
+ * tuning: results are identical; SDC_ERR_ARG outside 0..3. */
 sdc_status sdc_set_contact_replicas(sdc_ctx* ctx, int global);
 
 /* Side branches in the macro-step graph (1, default): the contact coupling
@@ -251,7 +254,8 @@ typedef struct {
     int32_t contact_cluster_cap;  /* cap on the contact loop's cluster (sdc_set_contact_cluster; 0 =
                                      automatic)                                                     */
     int32_t contact_cluster;      /* the cluster size that results                                 */
-    int32_t contact_global;       /* 1: replicas in global memory (staged), 2: global, unstaged     */
+    int32_t contact_global;       /* 1: replicas in global memory (staged), 2: global, unstaged,
+                                     3: grid-wide loop (sdc_set_contact_replicas)                  */
     int32_t graph_branches;       /* sdc_set_graph_branches                                        */
     int32_t trials;               /* option sets timed (0 when taken from the cache)               */
     int32_t cached;               /* 1: picks of an earlier context of the same shape              */

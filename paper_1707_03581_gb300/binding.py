@@ -301,7 +301,8 @@ class Solver:
 
     def set_contact_replicas(self, global_memory):
         """Replica placement of the contact loop: False/0 automatic, True/1 global memory
-        (staged in shared memory each substep when it fits), 2 global without staging."""
+        (staged in shared memory each substep when it fits), 2 global without staging, 3 the
+        grid-wide loop (one contact DOF a thread, cooperative launch)."""
         self._call("sdc_set_contact_replicas", int(global_memory))
 
     STEPPERS = {"mrsdc": 0, "sisdc": 1, "implicit_euler": 2}

@@ -103,6 +103,8 @@ struct sdc_ctx {
     int iface_chunk = 0;            // replica slots per CTA of that cluster
     bool iface_global = false;      // replicas in global memory (large interfaces)
     bool iface_stage = false;       // global replicas staged in shared memory each substep
+    bool iface_grid = false;        // grid-wide loop (sdc_set_contact_replicas 3): CTAs = iface_cluster
+    unsigned* iface_gbar = nullptr; // its grid barrier's [count, generation]
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
@@ -359,6 +361,55 @@ struct Chain {
         v.clusterDim.y = 1;
         v.clusterDim.z = 1;
         SDC_CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributeClusterDimension, &v));
+        last = nd;
+    }
+    // cooperative launch (every block resident at once): kernels with a grid-wide barrier
+    template <typename... KArgs>
+    void kernel_coop(void (*f)(KArgs...), unsigned grid, unsigned block, KArgs... args) {
+        void* params[] = {(void*)&args...};
+        ++kernels;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        if (is_eager) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(block);
+            cfg.stream = eager;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            const int ev = begin_timed((const void*)f);
+            SDC_CUDA_TRY(cudaLaunchKernelExC(&cfg, (const void*)f, params));
+            end_timed(ev);
+            return;
+        }
+        cudaKernelNodeParams p{};
+        p.func = (void*)f;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.kernelParams = params;
+        cudaGraphNode_t nd;
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
+        SDC_CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributeCooperative, &at[0].val));
+        last = nd;
+    }
+    // zero `bytes` bytes of device memory (a memset node, or an async memset in eager mode)
+    void zero(void* dst, size_t bytes) {
+        if (is_eager) {
+            SDC_CUDA_TRY(cudaMemsetAsync(dst, 0, bytes, eager));
+            return;
+        }
+        cudaMemsetParams mp{};
+        mp.dst = dst;
+        mp.value = 0;
+        mp.elementSize = 1;
+        mp.width = bytes;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t nd;
+        const std::vector<cudaGraphNode_t> d = take_deps();
+        SDC_CUDA_TRY(cudaGraphAddMemsetNode(&nd, g, d.data(), d.size(), &mp));
         last = nd;
     }
     // event record node on the chain (graph mode only)
@@ -878,6 +929,27 @@ void pick_iface_cluster(sdc_ctx* c) {
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
         SDC_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
+    c->iface_grid = false;
+    if (c->force_global == 3) {
+        // grid-wide loop: one contact DOF a thread on as many co-resident CTAs as that takes
+        const void* kern = mixed ? (const void*)k_iface_loop_mx_grid : (const void*)k_iface_loop_grid;
+        const int blocks = (int)blocks_for(NI, IFACE_GRID_THREADS);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, IFACE_GRID_THREADS, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        if ((int64_t)per_sm * c->n_sms >= blocks) {
+            c->iface_grid = true;
+            c->iface_global = true;
+            c->iface_stage = false;
+            c->iface_cluster = blocks;
+            c->iface_chunk = NI;
+            c->iface_smem = 0;
+            c->iface_rep = dalloc(c, c->pool_scheme, 2 * (size_t)NI * esz);
+            return;
+        }
+    }
     int cs_max = IFACE_MAX_CLUSTER;
     while (c->max_cluster > 0 && cs_max > c->max_cluster) cs_max /= 2;
     // Preferred size: about IFACE_TARGET_CHUNK contact DOFs per CTA. Measured on GB300
@@ -967,6 +1039,7 @@ void alloc_scheme_buffers(sdc_ctx* c) {
         for (int j = c->nondeg[0]; j <= M; ++j) c->fe_std[1][j] = dalloc_n<double>(c, c->pool_scheme, NI);
     }
     c->iface_sent = dalloc_n<int>(c, c->pool_scheme, IFACE_MAX_CLUSTER);
+    c->iface_gbar = dalloc_n<unsigned>(c, c->pool_scheme, 2);
     c->cpre = dalloc_n<double>(c, c->pool_scheme, (size_t)P * NI);
     c->fst = dalloc_n<double>(c, c->pool_scheme, NI);
     pick_iface_cluster(c);
@@ -1130,7 +1203,14 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ia.dT = c->precision == SDC_MIXED_FP32 ? c->dTv : nullptr;
         ia.rep_global = c->iface_rep;
         ia.sent = c->iface_sent;
+        ia.gbar = c->iface_gbar;
         ia.poll_limit = c->poll_limit;
+        if (c->iface_grid) {
+            ch.zero(c->iface_gbar, 2 * sizeof(unsigned));
+            ch.kernel_coop(c->precision == SDC_MIXED_FP32 ? k_iface_loop_mx_grid : k_iface_loop_grid,
+                           (unsigned)c->iface_cluster, (unsigned)IFACE_GRID_THREADS, ia);
+            return;
+        }
         ch.kernel_cluster(iface_loop_kernel(c->precision == SDC_MIXED_FP32, c->iface_chunk, c->iface_global,
                                             c->iface_stage),
                           (unsigned)c->iface_cluster, (unsigned)iface_loop_threads(c->iface_chunk, c->iface_global),
@@ -1472,6 +1552,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
         {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
         {(const void*)k_iface_loop_gls, "k_iface_loop_gls"}, {(const void*)k_iface_loop_mx_gls, "k_iface_loop_mx_gls"},
+        {(const void*)k_iface_loop_grid, "k_iface_loop_grid"}, {(const void*)k_iface_loop_mx_grid, "k_iface_loop_mx_grid"},
         {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
         {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"}, {(const void*)k_ie_init, "k_ie_init"},
         {(const void*)k_ie_spmv, "k_ie_spmv"},
@@ -1776,7 +1857,7 @@ sdc_status sdc_set_execution(sdc_ctx* c, int eager) {
 
 sdc_status sdc_set_contact_replicas(sdc_ctx* c, int global) {
     return guarded(c, [&] {
-        require(global >= 0 && global <= 2, SDC_ERR_ARG, "replica placement is 0, 1 or 2");
+        require(global >= 0 && global <= 3, SDC_ERR_ARG, "replica placement is 0, 1, 2 or 3");
         c->force_global = global;
         c->buffers_ready = false;
         c->graph_ready = false;
@@ -2846,6 +2927,7 @@ extern "C" sdc_status sdc_autotune(sdc_ctx* c, int32_t trial_steps, sdc_tune_rep
             } else if (best_stage) {
                 consider({best.unroll, best.update_bps, best.cluster_cap, 2, best.branches});
             }
+            if (best.global != 3) consider({best.unroll, best.update_bps, best.cluster_cap, 3, best.branches});
             if (!c->in_batch) consider({best.unroll, best.update_bps, best.cluster_cap, best.global, 1 - best.branches});
             apply_opts(c, best);
             ensure_ready(c);

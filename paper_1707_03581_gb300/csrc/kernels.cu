@@ -1791,6 +1791,122 @@ __device__ __forceinline__ void iface_loop_impl(const IfaceArgs& a) {
     cluster.sync();
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): the CTAs arrive on a
+// counter, the last one resets it and advances the generation, the others poll the
+// generation, at most `polls` times. Returns false in every thread of a CTA that gave up; the
+// kernel goes on (every later wait is bounded too), so every CTA ends, and the step reports
+// SDC_ERR_TIMEOUT. Stores before the barrier are visible to loads through L2 after it.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long polls) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;  // the generation cannot advance before this CTA arrives
+        int done = 1;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it >= polls) {
+                    done = 0;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        ok = done;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The substeps of iface_loop_impl on a cooperative grid instead of one cluster: one contact
+// DOF per thread (DOF = global thread index), as many CTAs as the interface needs, global
+// replicas [2][NI] published by the grid barrier. The arithmetic of every DOF is that of the
+// cluster forms (same rows, same order), so results are bitwise those of the cluster loop.
+// A cluster has at most 16 CTAs; with 27,170 contact DOFs they give a thread four DOFs a
+// substep, which this form spreads over about a hundred CTAs.
+template <bool MIX>
+__device__ __forceinline__ void iface_loop_grid_impl(const IfaceArgs& a) {
+    constexpr int B = MIX ? 24 : 16;
+    using V = typename std::conditional<MIX, float, double>::type;
+    const ContactDev& C = a.C;
+    const int NI = C.n_iface;
+    const int P = a.P;
+    V* rep = (V*)a.rep_global;
+    __shared__ double s_dtp[MAX_P + 1], s_shat[MAX_P + 1];
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+        s_dtp[q + 1] = substep_dt(a, tn, q + 1);
+        s_shat[q + 1] = a.Shat[q];
+    }
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool own = i < NI;
+    // buffer 0 = the replica at tau_{m,0}: T_{m-1} (FP64) or zero deviations (mixed)
+    if (own) rep[i] = MIX ? V(0) : (V)a.Tprev[C.dof[i]];
+    bool ok = grid_barrier(a.gbar, gridDim.x, a.poll_limit);
+    double T = 0.0, T0 = 0.0, fe = 0.0, mi = 0.0, ih = 0.0, cn = 0.0, bn = 0.0, fs = 0.0;
+    if (own) {
+        T0 = a.Tprev[C.dof[i]];
+        T = T0;
+        mi = C.minv[i];
+        double f0;
+        if (a.first && a.mode == RHS_PRED) {
+            if constexpr (MIX) {
+                f0 = a.base[i];
+            } else {
+                CouplingRowT<B> row;
+                coupling_prefetch(a.E, a.slot0, NI, i, row);
+                f0 = coupling_apply_shared<B, true>(a.E, a.slot0, NI, i, row, rep);
+            }
+        } else {
+            f0 = a.first ? a.fe_old[i] : a.fe_prev_end[i];
+        }
+        fe = f0;
+        a.fe_new[i] = f0;
+        cn = a.mode == RHS_PRED ? 0.0 : a.cpre[i];
+        fs = a.fstar[i];
+        if constexpr (MIX) bn = a.base[(size_t)NI + i];
+    }
+    for (int p = 1; p <= P; ++p) {
+        V* buf = rep + (size_t)(p & 1) * NI;
+        const double dtp = s_dtp[p];
+        typename std::conditional<MIX, CouplingRow32T<B>, CouplingRowT<B>>::type row;
+        double bp = bn;
+        if (own) {
+            if constexpr (MIX) coupling_prefetch32(a.E, a.slot0 + p, NI, i, row);
+            else coupling_prefetch(a.E, a.slot0 + p, NI, i, row);
+            const double cp = fma(dtp, fs, cn);  // c_p (Algorithms 1 and 2)
+            if (p < P) {
+                cn = a.mode == RHS_PRED ? 0.0 : a.cpre[(size_t)p * NI + i];
+                if constexpr (MIX) bn = a.base[(size_t)(p + 1) * NI + i];
+            }
+            T = fma(fma(dtp, fe, cp), mi, T);
+            buf[i] = MIX ? (V)(T - T0) : (V)T;
+        }
+        ok = grid_barrier(a.gbar, gridDim.x, a.poll_limit) && ok;
+        if (own) {
+            if constexpr (MIX) fe = bp + (double)coupling_apply_shared32<B, true>(a.E, a.slot0 + p, NI, i, row, buf);
+            else fe = coupling_apply_shared<B, true>(a.E, a.slot0 + p, NI, i, row, buf);
+            a.fe_new[(size_t)p * NI + i] = fe;
+            ih = fma(s_shat[p], fe, ih);
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(a.status, (int)SDC_ERR_TIMEOUT);
+    if (own) {
+        a.Tout[C.dof[i]] = T;
+        if (a.dT) a.dT[C.dof[i]] = (float)(T - T0);
+        a.ihat_new[i] = ih;
+    }
+}
+
+__global__ void __launch_bounds__(IFACE_GRID_THREADS) k_iface_loop_grid(IfaceArgs a) { iface_loop_grid_impl<false>(a); }
+__global__ void __launch_bounds__(IFACE_GRID_THREADS) k_iface_loop_mx_grid(IfaceArgs a) { iface_loop_grid_impl<true>(a); }
+
 // shared-memory replicas with one (chunk <= IFACE_THREADS) or two contact DOFs per thread;
 // global replicas with up to four (interfaces too large for shared memory)
 __global__ void __launch_bounds__(IFACE_THREADS) k_iface_loop1(IfaceArgs a) { iface_loop_impl<false, 1, false>(a); }

@@ -274,6 +274,7 @@ struct IfaceArgs {
     void* rep_global;               // [2][cs * chunk] replica buffers of the global-replica loop
     int* status;                    // sticky status word (SDC_ERR_TIMEOUT if an exchange wait gives up)
     int* sent;                      // [IFACE_MAX_CLUSTER] chunks each CTA of the cluster sent (per launch)
+    unsigned* gbar;                 // grid form: [count, generation] of its grid barrier (zeroed per launch)
     long long poll_limit;           // polls of an exchange wait before it gives up
 };
 
@@ -336,6 +337,9 @@ __global__ void k_iface_loop_mx(IfaceArgs a);
 __global__ void k_iface_loop_mx1(IfaceArgs a);
 __global__ void k_iface_loop_mx_gl(IfaceArgs a);
 __global__ void k_iface_loop_gls(IfaceArgs a);
+__global__ void k_iface_loop_grid(IfaceArgs a);
+__global__ void k_iface_loop_mx_grid(IfaceArgs a);
+constexpr int IFACE_GRID_THREADS = 256;  // threads per CTA of the grid-wide loop (one contact DOF each)
 __global__ void k_iface_loop_mx_gls(IfaceArgs a);
 __global__ void k_residual(ResidualArgs a);
 __global__ void k_heat(const double* mass, const double* T, int64_t n, int64_t n_fix, double* partials,

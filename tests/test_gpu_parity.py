@@ -434,10 +434,11 @@ def test_contact_cluster_sizes_are_bitwise_equal(torch, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("placement", [1, 2])
+@pytest.mark.parametrize("placement", [1, 2, 3])
 def test_global_replica_loop_equals_shared_memory_loop(torch, precision, placement):
-    # the loop form for interfaces too large for shared memory, forced on a small machine:
-    # staged into shared memory after every substep (1) or gathered from global memory (2)
+    # the loop forms for interfaces too large for shared memory, forced on a small machine:
+    # staged into shared memory after every substep (1), gathered from global memory (2), or
+    # the grid-wide loop with one contact DOF a thread (3)
     mach = machine_config(0)
     a = _solver(mach, precision=precision)
     b = _solver(mach, precision=precision)
@@ -449,7 +450,7 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision, placeme
     b.set_execution(True)
     b.set_kernel_timing(True)
     b.step(report=True)
-    suffix = "_gls" if placement == 1 else "_gl"
+    suffix = {1: "_gls", 2: "_gl", 3: "_grid"}[placement]
     assert any(k.endswith(suffix) for k in b.kernel_times())
 
 

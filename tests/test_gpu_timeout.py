@@ -6,8 +6,10 @@ without any fault: the CTA whose wait gave up stops exchanging, drains the copie
 addressed to it and reports SDC_ERR_TIMEOUT (the protocol is checked on the host in
 test_contact_exchange_model.py). With global replicas the wait that gives up is the one for
 the CTA's own copy of the replica into shared memory: the CTA issues no further copy and
-drains that one before exit. Afterwards the default budget restores normal steps,
-bitwise equal to a context that never timed out.
+drains that one before exit. In the grid-wide loop (placement 3) it is a wait of the grid
+barrier: the CTA goes on (every later wait is bounded too) and no copy is in flight.
+Afterwards the default budget restores normal steps, bitwise equal to a context that never
+timed out.
 """
 
 import numpy as np
@@ -26,7 +28,8 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("precision,placement", [("fp64", 0), ("mixed", 0), ("fp64", 1), ("mixed", 1)])
+@pytest.mark.parametrize("precision,placement",
+                         [("fp64", 0), ("mixed", 0), ("fp64", 1), ("mixed", 1), ("fp64", 3), ("mixed", 3)])
 def test_wait_budget_of_one_poll_times_out_and_context_recovers(torch, precision, placement):
     from paper_1707_03581_gb300 import SdcError, Solver
 
