@@ -570,6 +570,8 @@ def _measure(m, n_int, args, local, torch, flush, world, precision, compare, e2e
     def make(prec):
         sv = Solver(local)
         sv.set_machine(m, precision=prec)
+        if args.contact_replicas is not None:
+            sv.set_contact_replicas(args.contact_replicas)
         if not args.no_tune and not args.eager:
             t = time.perf_counter()
             tune[prec] = sv.autotune(trial_steps=3)
@@ -1108,6 +1110,9 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="config 4: number of requests")
     ap.add_argument("--max-active", type=int, default=64, help="config 4: requests in flight at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--contact-replicas", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="placement of the contact loop's replicas (sdc_set_contact_replicas); "
+                         "default automatic")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch options (no sdc_autotune before timing)")
     ap.add_argument("--no-fused", action="store_true", help="config 3: skip the fused (block-diagonal) form")

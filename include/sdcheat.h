@@ -210,7 +210,8 @@ sdc_status sdc_set_execution(sdc_ctx* ctx, int eager);
 
 /* Placement of the contact substep loop's replicas of the contact temperatures:
  * 0 (default) = shared memory of each CTA of the loop's cluster when they fit,
- * else global memory; 1 = always global memory; 2 = global memory and gathers from
+ * else (with no sdc_set_contact_cluster cap) the grid-wide loop of 3 below, else global
+ * memory; 1 = always global memory; 2 = global memory and gathers from
  * there. Global replicas are otherwise staged: after each substep one bulk copy brings
  * the whole replica into the CTA's shared memory when it fits (one buffer), and the
  * gathers read it there. 3 = the grid-wide loop: no cluster, one contact DOF a thread on

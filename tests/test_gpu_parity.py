@@ -457,7 +457,8 @@ def test_global_replica_loop_equals_shared_memory_loop(torch, precision, placeme
 def test_mixed_loop_forms_are_bitwise_equal_on_a_large_interface(torch):
     # 3,950 contact DOFs: 16 CTAs give one DOF a thread (k_iface_loop_mx1), 4 CTAs two
     # (k_iface_loop_mx), 2 CTAs too many for shared memory forms (global replicas staged in
-    # shared memory after every substep, the form of the 5.75M-DOF machine: k_iface_loop_mx_gls)
+    # shared memory after every substep: k_iface_loop_mx_gls; a cluster cap keeps the loop off
+    # the grid-wide form that an uncapped interface this large for shared memory takes)
     mach = machine_config(1)
     ref = None
     for cap, form in ((0, "k_iface_loop_mx1"), (4, "k_iface_loop_mx"), (2, "k_iface_loop_mx_gls")):
