@@ -360,22 +360,28 @@ def _profile_traffic(kernel, n_dof):
 def _dominant_kernel(s, precision, kt, reps):
     """The CG SpMV of the timed path and its algorithmic bytes per launch that did work.
 
-    Per SpMV: every nonzero's value and int32 column index (FP32: 4 + 4 bytes;
-    FP64: 8 + 4) plus the row vectors it reads (u, r, m) and writes (w). The
+    Per SpMV: every nonzero's value and column (FP32 4 or FP64 8 bytes, and a 16-bit
+    offset from its 32-row slice's base, 2 bytes, or a 32-bit column, 4 bytes), the
+    slices' 4-byte bases, plus the row vectors it reads (u, r, m) and writes (w). The
     SpMVs that did work in the timed steps are the CG updates plus one stopping
     SpMV per inner solve (from the steps' reports); the loop bodies' later
     launches after a stop return at once, and their time stays in the total."""
     n, nnz = s.n, s.nnz
+    cb = s.matrix_columns() // 8
+    bases = 4 * ((n + 31) // 32) if cb == 2 else 0
     iters = sum(r["cg_iters_total"] for r in reps)
     if precision == "mixed":
         name = "k_mx_spmv" if "k_mx_spmv" in kt else "k_mx_spmv_red"
         upd = "k_mx_update" if name == "k_mx_spmv" else "k_mx_update_red"
         work = iters + sum(r["refinements_total"] for r in reps)
-        return (name, upd, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)", 8 * nnz + 16 * n,
-                48 * n, work, kt.get(name, (0, 0.0)), kt.get(upd, (0, 0.0)))
+        return (name, upd, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)",
+                (4 + cb) * nnz + 16 * n + bases, 48 * n, work, kt.get(name, (0, 0.0)), kt.get(upd, (0, 0.0)),
+                f"{4 + cb} B/nnz + 16 B/row + 4 B per 32-row slice" if cb == 2 else f"{4 + cb} B/nnz + 16 B/row")
     work = iters + sum(r["n_solves"] for r in reps)
     return ("k_cg_spmv", "k_cg_update", "FP64 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)",
-            12 * nnz + 32 * n, 96 * n, work, kt.get("k_cg_spmv", (0, 0.0)), kt.get("k_cg_update", (0, 0.0)))
+            (8 + cb) * nnz + 32 * n + bases, 96 * n, work, kt.get("k_cg_spmv", (0, 0.0)),
+            kt.get("k_cg_update", (0, 0.0)),
+            f"{8 + cb} B/nnz + 32 B/row + 4 B per 32-row slice" if cb == 2 else f"{8 + cb} B/nnz + 32 B/row")
 
 
 def _graph_cg(s, m, flush, n_iters=30, reps=3):
@@ -647,7 +653,7 @@ def _kernel_report(mres, precision, args, peak, peak_kind):
     """Roofline of the dominant kernel (the CG SpMV), the FP32/FP64 CG iteration in graph
     execution, and every kernel's share of the eager steps' kernel time."""
     s, kt, reps = mres["solver"], mres["kt"], mres["eager_reps"]
-    name, upd, desc, sp_bytes, up_bytes, n_work, (n_launched, ms_spmv), (_, ms_upd) = _dominant_kernel(
+    name, upd, desc, sp_bytes, up_bytes, n_work, (n_launched, ms_spmv), (_, ms_upd), sp_note = _dominant_kernel(
         s, precision, kt, reps)
     ms_per_spmv = ms_spmv / max(n_work, 1)
     eager_achieved = sp_bytes / (ms_per_spmv * 1e-3) / 1e9 if n_work else 0.0
@@ -658,7 +664,8 @@ def _kernel_report(mres, precision, args, peak, peak_kind):
     achieved = sp_bytes / (g_spmv * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if peak else None, "traffic": traffic, "traffic_source": traffic_note,
-            "kernel": f"{name} ({desc})", "algorithmic_bytes": sp_bytes, "ms_per_launch": g_spmv,
+            "kernel": f"{name} ({desc})", "algorithmic_bytes": sp_bytes, "bytes_note": sp_note,
+            "ms_per_launch": g_spmv,
             "peak_kind": peak_kind,
             "timing": "CUDA events recorded inside a CUDA graph of 30 back-to-back CG iterations of the "
                       "step's kernels, grids and launch order, around every SpMV (sdc_time_cg_iterations), "
@@ -669,8 +676,8 @@ def _kernel_report(mres, precision, args, peak, peak_kind):
                                   "timing": "CUDA events around each launch of live eager macro steps (host-driven "
                                             "CG loops; a launch that waits for the host counts that wait)"}}
     cg_it = {"kernels": f"{name} + {upd}", "algorithmic_bytes": it_bytes,
-             "bytes_note": (f"SpMV {sp_bytes} (8 B/nnz + 16 B/row) + update {up_bytes} (48 B/row)" if precision == "mixed"
-                            else f"SpMV {sp_bytes} (12 B/nnz + 32 B/row) + update {up_bytes} (96 B/row)"),
+             "bytes_note": (f"SpMV {sp_bytes} ({sp_note}) + update {up_bytes} (48 B/row)" if precision == "mixed"
+                            else f"SpMV {sp_bytes} ({sp_note}) + update {up_bytes} (96 B/row)"),
              "ms_graph": g_iter, "achieved": it_bytes / (g_iter * 1e-3) / 1e9,
              "frac": it_bytes / (g_iter * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
              "ms_eager": (ms_spmv + ms_upd) / max(n_work, 1),

@@ -393,6 +393,18 @@ sdc_status sdc_get_footprint(const sdc_ctx* ctx, int64_t* bytes);
 sdc_status sdc_scheme_weights(sdc_nodes nodes, int M, int P, int window, double* c, double* emb, double* S,
                               double* Shat, double* Stil, double* Semb);
 
+/* Column form of the stored matrix K (Eq. coupledFEM; sliced ELL of 32-row slices, read by
+ * every SpMV of the implicit solves, f^I and the bulk endpoints): 0 (default) = 16-bit offsets
+ * from each slice's smallest column when every slice spans at most 65,535 columns (2 bytes an
+ * entry instead of 4; a 27-point stencil numbered plane by plane spans about two node planes),
+ * else 32-bit columns; 32 = 32-bit columns always. Takes effect at the next sdc_assemble.
+ * Results are identical. SDC_ERR_ARG for other values. */
+sdc_status sdc_set_matrix_columns(sdc_ctx* ctx, int bits);
+
+/* Bits of a column index in the assembled matrix: 16 or 32. SDC_ERR_STATE before
+ * sdc_assemble. */
+sdc_status sdc_get_matrix_columns(const sdc_ctx* ctx, int32_t* bits);
+
 /* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
 sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,
                          int64_t* n_contact);

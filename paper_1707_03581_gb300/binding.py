@@ -98,6 +98,8 @@ _SIGS = {
     "sdc_run_horizon": (C.c_int, [_vp, C.c_int64, C.POINTER(StepReport)]),
     "sdc_synchronize": (C.c_int, [_vp]),
     "sdc_get_sizes": (C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p]),
+    "sdc_set_matrix_columns": (C.c_int, [_vp, C.c_int]),
+    "sdc_get_matrix_columns": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sdc_get_temperature": (C.c_int, [_vp, _vp, C.c_int64]),
     "sdc_get_temperature_device": (C.c_int, [_vp, C.POINTER(_vp)]),
     "sdc_get_heat_totals": (C.c_int, [_vp, C.POINTER(Heat)]),
@@ -317,6 +319,17 @@ class Solver:
     def set_cg_unroll(self, pairs: int):
         """(SpMV, update) pairs per CG loop body, 1..8; 0 = by grid size (sdc_set_cg_unroll)."""
         self._call("sdc_set_cg_unroll", int(pairs))
+
+    def set_matrix_columns(self, bits: int):
+        """Column form of the stored matrix from the next assembly (set_machine): 0 automatic
+        (16-bit offsets from each slice's base when they reach), 32 = 32-bit columns."""
+        self._call("sdc_set_matrix_columns", int(bits))
+
+    def matrix_columns(self) -> int:
+        """Bits of a column index in the assembled matrix (16 or 32)."""
+        b = C.c_int32()
+        self._call("sdc_get_matrix_columns", C.byref(b))
+        return b.value
 
     def set_graph_branches(self, on: bool):
         """Run solve-independent kernels beside the implicit solves (True) or in one chain."""

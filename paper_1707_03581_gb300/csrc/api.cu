@@ -108,6 +108,8 @@ struct sdc_ctx {
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
+    int columns = 0;                // sdc_set_matrix_columns: 0 automatic, 32 = 32-bit columns
+    bool c32 = false;               // the assembled matrix has 32-bit columns (else 16-bit offsets)
     int stepper = SDC_STEPPER_MRSDC;  // sdc_set_stepper
     int cg_unroll = 0;                // sdc_set_cg_unroll (0: by grid size)
     double* w_slot_ie = nullptr;      // implicit Euler: the unit position of t_{n+1} (one slot)
@@ -166,6 +168,9 @@ void* dalloc(sdc_ctx* c, std::vector<void*>& pool, size_t bytes) {
     (&pool == &c->pool_asm ? c->pool_asm_bytes : c->pool_scheme_bytes).push_back(bytes);
     return p;
 }
+
+// a kernel that reads the matrix, in the column form of the context's assembled matrix
+#define MK(c, k) k##_form((c)->c32)
 
 template <class T>
 T* dalloc_n(sdc_ctx* c, std::vector<void*>& pool, size_t count) {
@@ -519,7 +524,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     const int unroll = cg_unroll(c);
     if (ch.is_eager) {
         a.h_outer = a.h_inner = 0;
-        ch.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+        ch.kernel(MK(c, k_mx_init), row_grid(c, MK(c, k_mx_init)), RED_BLOCK, a, r);
         for (;;) {
             SDC_CUDA_TRY(cudaMemcpyAsync(c->done_host, &c->ms->passes, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                          ch.eager));
@@ -529,13 +534,13 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                 c, ch,
                 [&] {
                     for (int u = 0; u < unroll; ++u) {
-                        ch.kernel(a.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, a);
+                        ch.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
                         ch.kernel(a.defer ? k_mx_update : k_mx_update_red,
                                   a.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, a);
                     }
                 },
                 unroll);
-            ch.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
+            ch.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
         }
         return;
     }
@@ -543,7 +548,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, ch.g, 1u, cudaGraphCondAssignDefault));
     a.h_outer = (unsigned long long)ho;
     a.h_inner = 0;
-    ch.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+    ch.kernel(MK(c, k_mx_init), row_grid(c, MK(c, k_mx_init)), RED_BLOCK, a, r);
     Chain outer(ch.while_node(ho));
     // the inner loop's condition: 1 at each graph launch (first pass), and set to 1 again by
     // k_mx_refine for every later pass
@@ -554,25 +559,27 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     for (int u = 0; u < unroll; ++u) {
         MixArgs au = a;
         au.tail_pairs = unroll - 1 - u;
-        inner.kernel(a.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, au);
+        inner.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, au);
         inner.kernel(a.defer ? k_mx_update : k_mx_update_red, a.defer ? c->update_grid : row_grid(c, k_mx_update),
                      RED_BLOCK, au);
     }
-    outer.kernel(k_mx_refine, row_grid(c, k_mx_refine), RED_BLOCK, a);
+    outer.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
 }
 
 // init kernel, then WHILE { spmv, update, p-update }
-void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r, void (*init)(CgArgs, RhsArgs) = k_cg_init,
-               void (*spmv)(CgArgs) = k_cg_spmv) {
+void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r, void (*init)(CgArgs, RhsArgs) = nullptr,
+               void (*spmv)(CgArgs) = nullptr) {
+    if (!init) init = MK(c, k_cg_init);
+    if (!spmv) spmv = MK(c, k_cg_spmv);
     const int unroll = cg_unroll(c);
     if (ch.is_eager) {
         a.handle = 0;
-        ch.kernel(init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
+        ch.kernel(init, row_grid(c, MK(c, k_cg_init)), RED_BLOCK, a, r);
         eager_cg_loop(
             c, ch,
             [&] {
                 for (int u = 0; u < unroll; ++u) {
-                    ch.kernel(spmv, row_grid(c, k_cg_spmv), RED_BLOCK, a);
+                    ch.kernel(spmv, row_grid(c, MK(c, k_cg_spmv)), RED_BLOCK, a);
                     ch.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, a);
                 }
             },
@@ -582,12 +589,12 @@ void add_solve(sdc_ctx* c, Chain& ch, CgArgs a, const RhsArgs& r, void (*init)(C
     cudaGraphConditionalHandle h;
     SDC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, ch.g, 1u, cudaGraphCondAssignDefault));
     a.handle = (unsigned long long)h;
-    ch.kernel(init, row_grid(c, k_cg_init), RED_BLOCK, a, r);
+    ch.kernel(init, row_grid(c, MK(c, k_cg_init)), RED_BLOCK, a, r);
     Chain body(ch.while_node(h));
     for (int u = 0; u < unroll; ++u) {
         CgArgs au = a;
         au.tail_pairs = unroll - 1 - u;
-        body.kernel(spmv, row_grid(c, k_cg_spmv), RED_BLOCK, au);
+        body.kernel(spmv, row_grid(c, MK(c, k_cg_spmv)), RED_BLOCK, au);
         body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, au);
     }
 }
@@ -629,7 +636,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.refine_out = &c->st->refinements[solve_idx];
     a.true_res = &c->st->true_res[solve_idx];
     a.status = &c->st->status;
-    a.part_blocks = (int)row_grid(c, k_mx_spmv);
+    a.part_blocks = (int)row_grid(c, MK(c, k_mx_spmv));
     a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
     a.max_iter = std::min(max_iter, MIX_INNER_MAX);
     a.max_refine = MIX_MAX_REFINE;
@@ -647,7 +654,7 @@ void add_implicit_solve(sdc_ctx* c, Chain& ch, double dtau, int solve_idx, doubl
             return;
         }
         add_solve_mixed(c, ch, a, r);
-        if (c->true_res) ch.kernel(k_mx_true_residual, row_grid(c, k_mx_true_residual), RED_BLOCK, a);
+        if (c->true_res) ch.kernel(MK(c, k_mx_true_residual), row_grid(c, MK(c, k_mx_true_residual)), RED_BLOCK, a);
     } else {
         add_solve(c, ch, cg_args(c, dtau, solve_idx, rtol, max_iter), r);
     }
@@ -686,7 +693,32 @@ void build_ell(sdc_ctx* c) {
     c->A.n = n;
     c->A.n_slices = ns;
     c->A.slice_ptr = upload(c, c->pool_asm, sp);
-    c->A.col = upload(c, c->pool_asm, col);
+    // 16-bit offsets from each slice's smallest column when every slice spans at most 65,535
+    // columns (padding entries included: they hold a column of their slice), else 32-bit columns
+    std::vector<int32_t> base(ns);
+    bool narrow = c->columns != 32;
+    for (int64_t s = 0; s < ns && narrow; ++s) {
+        int32_t lo = INT32_MAX, hi = INT32_MIN;
+        for (int64_t o = sp[s]; o < sp[s + 1]; ++o) {
+            lo = std::min(lo, col[o]);
+            hi = std::max(hi, col[o]);
+        }
+        base[s] = sp[s + 1] > sp[s] ? lo : 0;
+        narrow = sp[s + 1] == sp[s] || (int64_t)hi - lo <= 65535;
+    }
+    c->c32 = !narrow;
+    c->A.base = nullptr;
+    c->A.off = nullptr;
+    c->A.col = nullptr;
+    if (narrow) {
+        std::vector<uint16_t> off(sp[ns]);
+        for (int64_t s = 0; s < ns; ++s)
+            for (int64_t o = sp[s]; o < sp[s + 1]; ++o) off[o] = (uint16_t)(col[o] - base[s]);
+        c->A.base = upload(c, c->pool_asm, base);
+        c->A.off = upload(c, c->pool_asm, off);
+    } else {
+        c->A.col = upload(c, c->pool_asm, col);
+    }
     c->A.val = upload(c, c->pool_asm, val);
     std::vector<float> v32(val.begin(), val.end());
     c->A.val32 = upload(c, c->pool_asm, v32);
@@ -1115,7 +1147,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
     // F^I(T_n) + g in FP64 (the only pass over K in FP64 of a mixed-precision step); a
     // standard node at t_n (Lobatto) shares it. It also zeroes the step's count of CG-loop
     // kernels (no kernel that counts runs before or beside it).
-    ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->Fn,
+    ch.kernel(MK(c, k_fi), row_grid(c, MK(c, k_fi)), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv, (const double*)c->Tn, c->Fn,
               &c->st->loop_kernels);
     const bool mixed = c->precision == SDC_MIXED_FP32;
     // F^I + g at standard node j (0 = t_n) of iterate set s
@@ -1131,9 +1163,9 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             fa.dT = c->dTv;
             fa.F = c->FI[set][m - 1];
             fa.n = c->n;
-            ch.kernel(k_fi_mx, row_grid(c, k_fi_mx), (unsigned)RED_BLOCK, fa);
+            ch.kernel(MK(c, k_fi_mx), row_grid(c, MK(c, k_fi_mx)), (unsigned)RED_BLOCK, fa);
         } else {
-            ch.kernel(k_fi, row_grid(c, k_fi), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv,
+            ch.kernel(MK(c, k_fi), row_grid(c, MK(c, k_fi)), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv,
                       (const double*)c->Tstd[m], c->FI[set][m - 1], (int*)nullptr);
         }
     };
@@ -1148,7 +1180,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.Fx0 = Fx0;
             b.dT = c->dTv;
         }
-        auto kern = mixed ? k_bulk_endpoint_mx : k_bulk_endpoint;
+        auto kern = mixed ? MK(c, k_bulk_endpoint_mx) : MK(c, k_bulk_endpoint);
         b.rows = BULK_CONTACT;
         ch.kernel(kern, blocks_for(std::max(NI, 1), 256), 256u, b);
         b.rows = BULK_OFF_CONTACT;
@@ -1278,7 +1310,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
         ca.ie.E = ga.E;
         ca.ie.slot = 0;
         ca.ie.NI = NI;
-        add_solve(c, ch, ca, r, k_ie_init, k_ie_spmv);
+        add_solve(c, ch, ca, r, MK(c, k_ie_init), MK(c, k_ie_spmv));
         ch.copy(c->Tstd[M], c->X, (size_t)c->n * sizeof(double));
         // the step's contact heat for the ledger: dt f^E(T_{n+1}, t_{n+1})
         SisdcArgs f = a;
@@ -1556,26 +1588,36 @@ void ensure_ready(sdc_ctx* c) {
 
 const char* kernel_name(const void* f) {
     static const std::pair<const void*, const char*> names[] = {
-        {(const void*)k_cg_init, "k_cg_init"},         {(const void*)k_cg_spmv, "k_cg_spmv"},
-        {(const void*)k_cg_update, "k_cg_update"},
-        {(const void*)k_bulk_endpoint, "k_bulk_endpoint"}, {(const void*)k_iface_geom, "k_iface_geom"},
-        {(const void*)k_iface_geom_mx, "k_iface_geom_mx"},
-        {(const void*)k_iface_prep, "k_iface_prep"},   {(const void*)k_iface_tc, "k_iface_tc"},   {(const void*)k_iface_loop, "k_iface_loop"},
-        {(const void*)k_iface_loop_mx, "k_iface_loop_mx"},
-        {(const void*)k_iface_loop1, "k_iface_loop1"},  {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"},
-        {(const void*)k_iface_loop_gl, "k_iface_loop_gl"}, {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"},
-        {(const void*)k_iface_loop_gls, "k_iface_loop_gls"}, {(const void*)k_iface_loop_mx_gls, "k_iface_loop_mx_gls"},
-        {(const void*)k_iface_loop_grid, "k_iface_loop_grid"}, {(const void*)k_iface_loop_mx_grid, "k_iface_loop_mx_grid"},
-        {(const void*)k_sisdc_fe, "k_sisdc_fe"},       {(const void*)k_sisdc_rhs, "k_sisdc_rhs"},
-        {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"}, {(const void*)k_ie_init, "k_ie_init"},
-        {(const void*)k_ie_spmv, "k_ie_spmv"},
-        {(const void*)k_fi, "k_fi"},                   {(const void*)k_residual, "k_residual"},
-        {(const void*)k_heat, "k_heat"},               {(const void*)k_step_end, "k_step_end"},
-        {(const void*)k_mx_init, "k_mx_init"},
-        {(const void*)k_mx_spmv, "k_mx_spmv"},         {(const void*)k_mx_spmv_red, "k_mx_spmv_red"},
-        {(const void*)k_mx_update, "k_mx_update"},     {(const void*)k_mx_update_red, "k_mx_update_red"},
-        {(const void*)k_mx_refine, "k_mx_refine"},     {(const void*)k_mx_true_residual, "k_mx_true_residual"},
-        {(const void*)k_bulk_endpoint_mx, "k_bulk_endpoint_mx"}, {(const void*)k_fi_mx, "k_fi_mx"},
+        {(const void*)k_cg_update, "k_cg_update"}, {(const void*)k_iface_geom, "k_iface_geom"},
+        {(const void*)k_iface_geom_mx, "k_iface_geom_mx"}, {(const void*)k_iface_prep, "k_iface_prep"},
+        {(const void*)k_iface_tc, "k_iface_tc"}, {(const void*)k_iface_loop, "k_iface_loop"},
+        {(const void*)k_iface_loop_mx, "k_iface_loop_mx"}, {(const void*)k_iface_loop1, "k_iface_loop1"},
+        {(const void*)k_iface_loop_mx1, "k_iface_loop_mx1"}, {(const void*)k_iface_loop_gl, "k_iface_loop_gl"},
+        {(const void*)k_iface_loop_mx_gl, "k_iface_loop_mx_gl"}, {(const void*)k_iface_loop_gls, "k_iface_loop_gls"},
+        {(const void*)k_iface_loop_mx_gls, "k_iface_loop_mx_gls"},
+        {(const void*)k_iface_loop_grid, "k_iface_loop_grid"},
+        {(const void*)k_iface_loop_mx_grid, "k_iface_loop_mx_grid"}, {(const void*)k_sisdc_fe, "k_sisdc_fe"},
+        {(const void*)k_sisdc_rhs, "k_sisdc_rhs"}, {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"},
+        {(const void*)k_residual, "k_residual"}, {(const void*)k_heat, "k_heat"},
+        {(const void*)k_step_end, "k_step_end"}, {(const void*)k_mx_update, "k_mx_update"},
+        {(const void*)k_mx_update_red, "k_mx_update_red"},
+        {(const void*)k_cg_init_form(false), "k_cg_init"}, {(const void*)k_cg_init_form(true), "k_cg_init"},
+        {(const void*)k_cg_spmv_form(false), "k_cg_spmv"}, {(const void*)k_cg_spmv_form(true), "k_cg_spmv"},
+        {(const void*)k_bulk_endpoint_form(false), "k_bulk_endpoint"},
+        {(const void*)k_bulk_endpoint_form(true), "k_bulk_endpoint"},
+        {(const void*)k_ie_init_form(false), "k_ie_init"}, {(const void*)k_ie_init_form(true), "k_ie_init"},
+        {(const void*)k_ie_spmv_form(false), "k_ie_spmv"}, {(const void*)k_ie_spmv_form(true), "k_ie_spmv"},
+        {(const void*)k_fi_form(false), "k_fi"}, {(const void*)k_fi_form(true), "k_fi"},
+        {(const void*)k_mx_init_form(false), "k_mx_init"}, {(const void*)k_mx_init_form(true), "k_mx_init"},
+        {(const void*)k_mx_spmv_form(false), "k_mx_spmv"}, {(const void*)k_mx_spmv_form(true), "k_mx_spmv"},
+        {(const void*)k_mx_spmv_red_form(false), "k_mx_spmv_red"},
+        {(const void*)k_mx_spmv_red_form(true), "k_mx_spmv_red"},
+        {(const void*)k_mx_refine_form(false), "k_mx_refine"}, {(const void*)k_mx_refine_form(true), "k_mx_refine"},
+        {(const void*)k_mx_true_residual_form(false), "k_mx_true_residual"},
+        {(const void*)k_mx_true_residual_form(true), "k_mx_true_residual"},
+        {(const void*)k_bulk_endpoint_mx_form(false), "k_bulk_endpoint_mx"},
+        {(const void*)k_bulk_endpoint_mx_form(true), "k_bulk_endpoint_mx"},
+        {(const void*)k_fi_mx_form(false), "k_fi_mx"}, {(const void*)k_fi_mx_form(true), "k_fi_mx"},
     };
     for (const auto& n : names)
         if (n.first == f) return n.second;
@@ -2028,6 +2070,22 @@ sdc_status sdc_synchronize(sdc_ctx* c) {
     });
 }
 
+sdc_status sdc_set_matrix_columns(sdc_ctx* c, int bits) {
+    return guarded(c, [&] {
+        require(bits == 0 || bits == 32, SDC_ERR_ARG, "bits must be 0 (automatic) or 32");
+        c->columns = bits;
+    });
+}
+
+sdc_status sdc_get_matrix_columns(const sdc_ctx* cc, int32_t* bits) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(bits != nullptr, SDC_ERR_ARG, "bits is null");
+        *bits = c->c32 ? 32 : 16;
+    });
+}
+
 sdc_status sdc_get_sizes(const sdc_ctx* cc, int64_t* n_dof, int64_t* n_stand, int64_t* nnz, int64_t* n_contact) {
     sdc_ctx* c = const_cast<sdc_ctx*>(cc);
     return guarded(c, [&] {
@@ -2097,7 +2155,8 @@ sdc_status sdc_apply_operator(sdc_ctx* c, double dtau, const double* x, double* 
     return guarded(c, [&] {
         require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
         require(x && y, SDC_ERR_ARG, "null buffer");
-        k_apply_operator<<<row_grid(c, k_apply_operator), RED_BLOCK, 0, c->stream>>>(c->A, c->d_mass, dtau, x, y);
+        auto apply = MK(c, k_apply_operator);
+        apply<<<row_grid(c, apply), RED_BLOCK, 0, c->stream>>>(c->A, c->d_mass, dtau, x, y);
         SDC_CUDA_TRY(cudaGetLastError());
     });
 }
@@ -2177,14 +2236,14 @@ sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int3
                 ev.push_back(e);
             }
             Chain init(g[0]);
-            if (mixed) init.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, ma, r);
-            else init.kernel(k_cg_init, row_grid(c, k_cg_init), RED_BLOCK, ca, r);
+            if (mixed) init.kernel(MK(c, k_mx_init), row_grid(c, MK(c, k_mx_init)), RED_BLOCK, ma, r);
+            else init.kernel(MK(c, k_cg_init), row_grid(c, MK(c, k_cg_init)), RED_BLOCK, ca, r);
             for (int gi = 1; gi < n_graphs; ++gi) {
                 Chain body(g[gi]);
                 for (int k = 0; k < n_iters; ++k) {
                     if (gi == 2) body.event(ev[2 + 2 * k]);
-                    if (mixed) body.kernel(ma.defer ? k_mx_spmv : k_mx_spmv_red, row_grid(c, k_mx_spmv), RED_BLOCK, ma);
-                    else body.kernel(k_cg_spmv, row_grid(c, k_cg_spmv), RED_BLOCK, ca);
+                    if (mixed) body.kernel(ma.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, ma);
+                    else body.kernel(MK(c, k_cg_spmv), row_grid(c, MK(c, k_cg_spmv)), RED_BLOCK, ca);
                     if (gi == 2) body.event(ev[3 + 2 * k]);
                     if (spmv_only) continue;
                     if (mixed)
@@ -2478,7 +2537,7 @@ bool fusable(const sdc_ctx* c, const sdc_ctx* ref) {
                     blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS;
     if (!ok || !ref) return ok;
     return c->W.kind == ref->W.kind && c->W.M == ref->W.M && c->W.P == ref->W.P && c->W.w == ref->W.w &&
-           c->K_sweeps == ref->K_sweeps && c->dt == ref->dt && c->nondeg == ref->nondeg;
+           c->K_sweeps == ref->K_sweeps && c->dt == ref->dt && c->nondeg == ref->nondeg && c->c32 == ref->c32;
 }
 
 void group_release(sdc_batch* b) {
@@ -2546,7 +2605,7 @@ void build_group(sdc_batch* b) {
             a.grp = gs;
             a.h_outer = a.h_inner = 0;
             a.tail_pairs = 0;
-            chh.kernel(k_mx_init, row_grid(c, k_mx_init), RED_BLOCK, a, r);
+            chh.kernel(MK(c, k_mx_init), row_grid(c, MK(c, k_mx_init)), RED_BLOCK, a, r);
             in[i].push_back(chh.last);
             cudaGraphNode_t e;
             SDC_CUDA_TRY(cudaGraphAddEmptyNode(&e, G, nullptr, 0));
@@ -2566,7 +2625,7 @@ void build_group(sdc_batch* b) {
     }
     std::vector<int> n_spmv(nm), n_upd(nm);
     for (size_t i = 0; i < nm; ++i) {
-        n_spmv[i] = (int)row_grid(b->group[i], k_mx_spmv);
+        n_spmv[i] = (int)row_grid(b->group[i], MK(b->group[i], k_mx_spmv));
         n_upd[i] = (int)b->group[i]->update_grid;
     }
     unsigned t_spmv = 0, t_upd = 0, t_ref = 0;
@@ -2598,10 +2657,10 @@ void build_group(sdc_batch* b) {
         for (int u = 0; u < unroll; ++u) {
             GroupArgs gu = g;
             gu.tail_pairs = unroll - 1 - u;
-            inner.kernel(k_mx_spmv_g, t_spmv, (unsigned)RED_BLOCK, gu);
+            inner.kernel(MK(b->group[0], k_mx_spmv_g), t_spmv, (unsigned)RED_BLOCK, gu);
             inner.kernel(k_mx_update_g, t_upd, (unsigned)RED_BLOCK, gu);
         }
-        outer.kernel(k_mx_refine_g, t_ref, (unsigned)RED_BLOCK, g);
+        outer.kernel(MK(b->group[0], k_mx_refine_g), t_ref, (unsigned)RED_BLOCK, g);
         gc.kernel(k_group_end, 1u, 32u, g);
         for (size_t i = 0; i < nm; ++i) SDC_CUDA_TRY(cudaGraphAddDependencies(G, &gc.last, &out[i][k], nullptr, 1));
     }

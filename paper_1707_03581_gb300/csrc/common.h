@@ -84,10 +84,16 @@ ContactHost build_contact(const BodyInput& stand, const BodyInput& stock, const 
 // ----------------------------------------------------------------- device data
 
 // Sliced ELL, slice height 32: entry (slice s, k, lane) at slice_ptr[s] + 32 k + lane.
+// Column of an entry: base[s] + off[entry] when base[s] >= 0 (every column of the slice lies
+// within 65,535 of the slice's smallest), else col[entry] (a wide slice; col is allocated only
+// when the matrix has one). A 27-point stencil numbered plane by plane has slices spanning
+// about two node planes, so its columns cost 2 bytes an entry instead of 4.
 struct EllDev {
     int64_t n = 0;
     int64_t n_slices = 0;
     const int64_t* slice_ptr = nullptr;
+    const int32_t* base = nullptr;
+    const uint16_t* off = nullptr;
     const int32_t* col = nullptr;
     const double* val = nullptr;
     const float* val32 = nullptr;

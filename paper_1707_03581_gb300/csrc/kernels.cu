@@ -33,12 +33,15 @@ __device__ __forceinline__ double warp_max(double v) {
 // Entries are taken CH at a time: the CH value and column loads of a chunk
 // are all issued before its CH gathers of x, so a row costs ceil(w / CH)
 // dependent memory round trips instead of w. Summation stays in entry order.
-template <int CH, typename V, typename X>
-__device__ __forceinline__ V ell_row_t(const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-                                       const V* __restrict__ val, int64_t row, const X* __restrict__ x) {
+// C32: the matrix's column form (a kernel template parameter, so that each kernel has the
+// registers of one form): 32-bit columns, or 16-bit offsets from each slice's base.
+template <bool C32, int CH, typename V, typename X>
+__device__ __forceinline__ V ell_row_t(const EllDev& A, const V* __restrict__ val, int64_t row,
+                                       const X* __restrict__ x) {
     const int64_t s = row >> 5;
     const int lane = (int)(row & 31);
-    const int64_t b = slice_ptr[s], e = slice_ptr[s + 1];
+    const int64_t b = A.slice_ptr[s], e = A.slice_ptr[s + 1];
+    const int32_t cb = C32 ? 0 : __ldg(A.base + s);
     V acc = V(0);
     for (int64_t k0 = b + lane; k0 < e; k0 += (int64_t)CH * SLICE) {
         V v[CH];
@@ -48,7 +51,8 @@ __device__ __forceinline__ V ell_row_t(const int64_t* __restrict__ slice_ptr, co
             const int64_t k = k0 + (int64_t)j * SLICE;
             const bool in = k < e;
             v[j] = in ? __ldg(val + k) : V(0);
-            c[j] = in ? (int64_t)__ldg(col + k) : 0;
+            if constexpr (C32) c[j] = in ? (int64_t)__ldg(A.col + k) : 0;
+            else c[j] = in ? (int64_t)(cb + (int32_t)__ldg(A.off + k)) : 0;
         }
         X xv[CH];
 #pragma unroll
@@ -59,8 +63,9 @@ __device__ __forceinline__ V ell_row_t(const int64_t* __restrict__ slice_ptr, co
     return acc;
 }
 
+template <bool C32>
 __device__ __forceinline__ double ell_row(const EllDev& A, int64_t row, const double* __restrict__ x) {
-    return ell_row_t<8, double, double>(A.slice_ptr, A.col, A.val, row, x);
+    return ell_row_t<C32, 8, double, double>(A, A.val, row, x);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -158,8 +163,9 @@ __device__ bool reduce_last(W (&v)[NQ], double* partials, unsigned int* counter,
 }
 
 // FP32 row of the sliced ELL: sum_k K32[row, k] x[k]
+template <bool C32>
 __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const float* __restrict__ x) {
-    return ell_row_t<8, float, float>(A.slice_ptr, A.col, A.val32, row, x);
+    return ell_row_t<C32, 8, float, float>(A, A.val32, row, x);
 }
 
 // Two-level form of reduce_last for the CG kernels. Block totals go to
@@ -292,21 +298,23 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
 // ------------------------------------------------------------------ operator
 
 // y = m .* x + dtau K x
+template <bool C32>
 __global__ void k_apply_operator(EllDev A, const double* __restrict__ mass, double dtau,
                                  const double* __restrict__ x, double* __restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < A.n) {
-        y[i] = fma(dtau, ell_row(A, i, x), mass[i] * x[i]);
+        y[i] = fma(dtau, ell_row<C32>(A, i, x), mass[i] * x[i]);
     }
 }
 
 // F = -K T + g   (f^I(T) + g of Eq. ivp)
+template <bool C32>
 __global__ void k_fi(EllDev A, const double* __restrict__ g, const double* __restrict__ T, double* __restrict__ F,
                      int* step_counts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (step_counts && i == 0) *step_counts = 0;  // step start: kernels launched in the CG loops
     if (i < A.n) {
-        F[i] = g[i] - ell_row(A, i, T);
+        F[i] = g[i] - ell_row<C32>(A, i, T);
     }
 }
 
@@ -333,7 +341,7 @@ __device__ __forceinline__ double ie_contact(const IeOp& o, int64_t i, const dou
 // Algorithm 2: m T^{k+1}_{m-1} - dtau f^I(T^k_m) + I_{m-1}^m), the initial
 // residual r = b - (m x0 + dtau K x0), u = D r, and the stop test.
 // IE: the operator is m + dtau (K - L_E(t_{n+1})) (contact coupling in the matrix).
-template <bool IE>
+template <bool C32, bool IE>
 __device__ __forceinline__ void cg_init_impl(const CgArgs& a, const RhsArgs& r) {
     double v[2] = {0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,7 +365,7 @@ __device__ __forceinline__ void cg_init_impl(const CgArgs& a, const RhsArgs& r) 
                 b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
             }
             const double x0 = r.x0[i];
-            double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row<C32>(a.A, i, r.x0);
             if constexpr (IE) Kx0 -= ie_contact(a.ie, i, r.x0);
             const double Ax = fma(a.dtau, Kx0, m * x0);
             const double res = b - Ax;
@@ -384,21 +392,23 @@ __device__ __forceinline__ void cg_init_impl(const CgArgs& a, const RhsArgs& r) 
     }
 }
 
-__global__ void k_cg_init(CgArgs a, RhsArgs r) { cg_init_impl<false>(a, r); }
-__global__ void k_ie_init(CgArgs a, RhsArgs r) { cg_init_impl<true>(a, r); }
+template <bool C32>
+__global__ void k_cg_init(CgArgs a, RhsArgs r) { cg_init_impl<C32, false>(a, r); }
+template <bool C32>
+__global__ void k_ie_init(CgArgs a, RhsArgs r) { cg_init_impl<C32, true>(a, r); }
 
 // w = m u + dtau K u (IE: m u + dtau (K - L_E) u); gamma = (r, u), delta = (w, u),
 // rr = (r, r). The last block tests ||r|| <= rtol ||b|| (stop) or sets the step
 // lengths:
 //   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev).
-template <bool IE>
+template <bool C32, bool IE>
 __device__ __forceinline__ void cg_spmv_impl(const CgArgs& a) {
     if (a.cg->done) return;  // an iteration queued after convergence (host-driven loop)
     double v[3] = {0.0, 0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
             const double u = a.U[i];
-            double Ku = ell_row(a.A, i, a.U);
+            double Ku = ell_row<C32>(a.A, i, a.U);
             if constexpr (IE) Ku -= ie_contact(a.ie, i, a.U);
             const double w = fma(a.dtau, Ku, a.mass[i] * u);
             const double res = a.R[i];
@@ -437,8 +447,10 @@ __device__ __forceinline__ void cg_spmv_impl(const CgArgs& a) {
     }
 }
 
-__global__ void k_cg_spmv(CgArgs a) { cg_spmv_impl<false>(a); }
-__global__ void k_ie_spmv(CgArgs a) { cg_spmv_impl<true>(a); }
+template <bool C32>
+__global__ void k_cg_spmv(CgArgs a) { cg_spmv_impl<C32, false>(a); }
+template <bool C32>
+__global__ void k_ie_spmv(CgArgs a) { cg_spmv_impl<C32, true>(a); }
 
 // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D r
 __global__ void k_cg_update(CgArgs a) {
@@ -497,6 +509,7 @@ __device__ __forceinline__ void mx_done_on_entry(const MixArgs& a) {
 
 // FP64: b of the implicit stage (as k_cg_init), x = x0, r = b - A x0, and
 // the outer stop test; FP32 inverse diagonal for the inner solves.
+template <bool C32>
 __global__ void k_mx_init(MixArgs a, RhsArgs r) {
     double v[2] = {0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -520,7 +533,7 @@ __global__ void k_mx_init(MixArgs a, RhsArgs r) {
                 b = m * r.Tprev[i] - a.dtau * (r.FIm[i] - r.g[i]) + I;
             }
             const double x0 = r.x0[i];
-            const double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row(a.A, i, r.x0);
+            const double Kx0 = r.Fx0 ? r.g[i] - r.Fx0[i] : ell_row<C32>(a.A, i, r.x0);
             const double res = b - fma(a.dtau, Kx0, m * x0);
             a.B[i] = b;
             a.X[i] = x0;
@@ -627,9 +640,10 @@ __device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G,
 //    lengths.
 
 // FP32 SpMV row i: w = m u + dtau K32 u, and its terms of (r,u), (w,u), (r,r).
+template <bool C32>
 __device__ __forceinline__ void mx_spmv_row(const MixArgs& a, int64_t i, float (&v)[3]) {
     const float u = a.Ul[i];
-    const float w = fmaf((float)a.dtau, ell_row32(a.A, i, a.Ul), a.mass32[i] * u);
+    const float w = fmaf((float)a.dtau, ell_row32<C32>(a.A, i, a.Ul), a.mass32[i] * u);
     const float res = a.Rl[i];
     a.Wl[i] = w;
     v[0] = res * u;
@@ -655,7 +669,7 @@ __device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float
 // 5.75M rows a probe of this SpMV took 218 us at 8 blocks a SM against 244 us at 6.
 // One block of the deferred-dot FP32 SpMV: block blk of a launch of nblk blocks for the
 // machine of `a` (its own launch, or its range of a fused group launch).
-template <bool GROUP>
+template <bool C32, bool GROUP>
 __device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, unsigned nblk) {
     CgState* s = a.cg;
     if (s->done) {  // an iteration after the stop (rest of the loop body, host-driven lookahead)
@@ -670,11 +684,14 @@ __device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, un
     }
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i < a.n) mx_spmv_row(a, i, v);
+    if (i < a.n) mx_spmv_row<C32>(a, i, v);
     block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials), blk, nblk);
 }
 
-__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv(MixArgs a) { mx_spmv_block<false>(a, blockIdx.x, gridDim.x); }
+template <bool C32>
+__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv(MixArgs a) {
+    mx_spmv_block<C32, false>(a, blockIdx.x, gridDim.x);
+}
 
 // One block of the FP32 CG update (deferred dots), block blk of nblk for the machine of
 // `a`; in a fused group (GROUP) the stop clears the group's loop condition when the last
@@ -794,6 +811,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     mx_update_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
     if (a.cg->done) {  // an iteration queued after convergence (host-driven loop)
         mx_done_on_entry(a);
@@ -801,7 +819,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
     }
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) mx_spmv_row(a, i, v);
+    if (i < a.n) mx_spmv_row<C32>(a, i, v);
     double out[3];
     if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
         CgState* s = a.cg;
@@ -847,7 +865,7 @@ __global__ void k_mx_update_red(MixArgs a) {
 // rounding is relative to the correction, not to b. Outer stop test.
 // One block of the end of a refinement pass (see k_mx_refine), block blk of nblk for the
 // machine of `a`; in a fused group the outer loop stops with the last member's convergence.
-template <bool GROUP>
+template <bool C32, bool GROUP>
 __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, unsigned nblk, const GroupArgs& g) {
     if (GROUP && a.ms->done) return;  // a member whose refinement converged in an earlier pass
     double v[1] = {0.0};
@@ -856,7 +874,7 @@ __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, 
         const float d = a.Dl[i];
         a.X[i] += (double)d;
         a.Dsum[i] += d;
-        const float Ad = fmaf((float)a.dtau, ell_row32(a.A, i, a.Dl), a.mass32[i] * d);
+        const float Ad = fmaf((float)a.dtau, ell_row32<C32>(a.A, i, a.Dl), a.mass32[i] * d);
         const double res = a.R[i] - (double)Ad;
         a.R[i] = res;
         a.Rl[i] = (float)res;  // the next pass's FP32 residual and u (unread if none follows)
@@ -887,8 +905,9 @@ __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, 
     }
 }
 
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
-    mx_refine_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
+    mx_refine_block<C32, false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
 // Fused group launches: the member of each block and its block within the member's range.
@@ -926,6 +945,7 @@ __device__ __forceinline__ void group_cap_failed(const GroupArgs& g) {
     for (int m = 0; m < g.n_members; ++m) atomicExch(g.args[m].status, (int)SDC_ERR_NOT_CONVERGED);
 }
 
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_g(GroupArgs g) {
     // the inner loop ends after this body when no member's CG runs (the counter changes only
     // in the updates, outside this launch) or after launch_cap SpMV launches in the pass
@@ -938,7 +958,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_g(GroupArgs g) {
     }
     unsigned blk, nblk;
     const MixArgs& a = group_member(g, g.spmv, blk, nblk);
-    mx_spmv_block<true>(a, blk, nblk);
+    mx_spmv_block<C32, true>(a, blk, nblk);
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update_g(GroupArgs g) {
@@ -947,6 +967,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update_g(GroupArgs g) {
     mx_update_block<true>(a, blk, nblk, g);
 }
 
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine_g(GroupArgs g) {
     // the outer loop ends after this pass when no member is refining or after pass_cap passes
     // (members that go on set the inner loop's condition again for their next pass)
@@ -960,17 +981,18 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine_g(GroupArgs g) {
     }
     unsigned blk, nblk;
     const MixArgs& a = group_member(g, g.refine, blk, nblk);
-    mx_refine_block<true>(a, blk, nblk, g);
+    mx_refine_block<C32, true>(a, blk, nblk, g);
 }
 
 // Diagnostics of a mixed solve: the true residual ||b - (m x + dtau K x)|| / ||b|| with the
 // FP64 operator and the FP64 iterate, after the refinement stopped on the carried residual.
+template <bool C32>
 __global__ void k_mx_true_residual(MixArgs a) {
     double v[2] = {0.0, 0.0};
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) {
         const double b = a.B[i];
-        const double r = b - fma(a.dtau, ell_row(a.A, i, a.X), a.mass[i] * a.X[i]);
+        const double r = b - fma(a.dtau, ell_row<C32>(a.A, i, a.X), a.mass[i] * a.X[i]);
         v[0] = r * r;
         v[1] = b * b;
     }
@@ -995,10 +1017,11 @@ __device__ __forceinline__ int64_t bulk_row(const BulkArgs& a) {
     return (a.rows == BULK_OFF_CONTACT && a.pos[t] >= 0) ? -1 : t;
 }
 
+template <bool C32>
 __global__ void k_bulk_endpoint(BulkArgs a) {
     const int64_t i = bulk_row(a);
     if (i >= 0) {
-        const double KX = ell_row(a.A, i, a.X);
+        const double KX = ell_row<C32>(a.A, i, a.X);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
             fstar = a.g[i] - KX;
@@ -1019,10 +1042,11 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
 //   predictor: f*_m = F^I(T*) + g = F(x0) - K dX
 //   sweep:     f*_m = f^I(T*) - f^I(T^k_m) = -K dX          (x0 = T^k_m)
 // K dX as an FP32 SpMV; the increment of every row goes to dT for k_fi_mx.
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_bulk_endpoint_mx(BulkArgs a) {
     const int64_t i = bulk_row(a);
     if (i >= 0) {
-        const double KdX = (double)ell_row32(a.A, i, a.dX);
+        const double KdX = (double)ell_row32<C32>(a.A, i, a.dX);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
             fstar = a.Fx0[i] - KdX;
@@ -1045,10 +1069,33 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_bulk_endpoint_mx(BulkArgs a) {
 }
 
 // F^I(T_m) + g = F^I(T_prev) + g - K dT (mixed precision; FP32 SpMV of the increment)
+template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_fi_mx(FiDevArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) a.F[i] = a.Fprev[i] - (double)ell_row32(a.A, i, a.dT);
+    if (i < a.n) a.F[i] = a.Fprev[i] - (double)ell_row32<C32>(a.A, i, a.dT);
 }
+
+// Both column forms of every kernel that reads the matrix (EllDev), for the host code of
+// other translation units (the stubs of template kernels are local to this one)
+#define SDC_MATRIX_KERNEL(name, type) \
+    type name##_form(bool c32) { return c32 ? name<true> : name<false>; }
+SDC_MATRIX_KERNEL(k_apply_operator, KEllOp)
+SDC_MATRIX_KERNEL(k_fi, KEllFi)
+SDC_MATRIX_KERNEL(k_cg_init, KCgInit)
+SDC_MATRIX_KERNEL(k_ie_init, KCgInit)
+SDC_MATRIX_KERNEL(k_cg_spmv, KCg)
+SDC_MATRIX_KERNEL(k_ie_spmv, KCg)
+SDC_MATRIX_KERNEL(k_mx_init, KMxInit)
+SDC_MATRIX_KERNEL(k_mx_spmv, KMx)
+SDC_MATRIX_KERNEL(k_mx_spmv_red, KMx)
+SDC_MATRIX_KERNEL(k_mx_refine, KMx)
+SDC_MATRIX_KERNEL(k_mx_true_residual, KMx)
+SDC_MATRIX_KERNEL(k_mx_spmv_g, KGroup)
+SDC_MATRIX_KERNEL(k_mx_refine_g, KGroup)
+SDC_MATRIX_KERNEL(k_bulk_endpoint, KBulk)
+SDC_MATRIX_KERNEL(k_bulk_endpoint_mx, KBulk)
+SDC_MATRIX_KERNEL(k_fi_mx, KFi)
+#undef SDC_MATRIX_KERNEL
 
 // ------------------------------------------------------------------ contact geometry
 

@@ -299,31 +299,42 @@ struct ResidualArgs {
 };
 
 // kernels (defined in kernels.cu)
-__global__ void k_apply_operator(EllDev A, const double* mass, double dtau, const double* x, double* y);
-__global__ void k_fi(EllDev A, const double* g, const double* T, double* F, int* step_counts);
+// Kernels that read the matrix come in both column forms of EllDev (32-bit columns, or 16-bit
+// offsets from each slice's base); name##_form(c32) returns the one for a matrix.
+using KEllOp = void (*)(EllDev, const double*, double, const double*, double*);
+using KEllFi = void (*)(EllDev, const double*, const double*, double*, int*);
+using KCgInit = void (*)(CgArgs, RhsArgs);
+using KCg = void (*)(CgArgs);
+using KMxInit = void (*)(MixArgs, RhsArgs);
+using KMx = void (*)(MixArgs);
+using KGroup = void (*)(GroupArgs);
+using KBulk = void (*)(BulkArgs);
+using KFi = void (*)(FiDevArgs);
+KEllOp k_apply_operator_form(bool c32);
+KEllFi k_fi_form(bool c32);
+KCgInit k_cg_init_form(bool c32);
+KCg k_cg_spmv_form(bool c32);
+KCgInit k_ie_init_form(bool c32);
+KCg k_ie_spmv_form(bool c32);
+KMxInit k_mx_init_form(bool c32);
+KMx k_mx_spmv_form(bool c32);
+KMx k_mx_spmv_red_form(bool c32);
+KMx k_mx_refine_form(bool c32);
+KMx k_mx_true_residual_form(bool c32);
+KGroup k_mx_spmv_g_form(bool c32);
+KGroup k_mx_refine_g_form(bool c32);
+KBulk k_bulk_endpoint_form(bool c32);
+KBulk k_bulk_endpoint_mx_form(bool c32);
+KFi k_fi_mx_form(bool c32);
 __global__ void k_sisdc_fe(SisdcArgs a);
 __global__ void k_sisdc_rhs(SisdcArgs a);
 __global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* Tout, float* dT, int64_t n);
-__global__ void k_cg_init(CgArgs a, RhsArgs r);
-__global__ void k_cg_spmv(CgArgs a);
-__global__ void k_ie_init(CgArgs a, RhsArgs r);
-__global__ void k_ie_spmv(CgArgs a);
 __global__ void k_cg_update(CgArgs a);
-__global__ void k_mx_init(MixArgs a, RhsArgs r);
-__global__ void k_mx_spmv(MixArgs a);
-__global__ void k_mx_spmv_red(MixArgs a);
 __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_update_red(MixArgs a);
-__global__ void k_mx_refine(MixArgs a);
-__global__ void k_mx_true_residual(MixArgs a);
 __global__ void k_group_begin(GroupArgs g);
 __global__ void k_group_end(GroupArgs g);
-__global__ void k_mx_spmv_g(GroupArgs g);
 __global__ void k_mx_update_g(GroupArgs g);
-__global__ void k_mx_refine_g(GroupArgs g);
-__global__ void k_bulk_endpoint(BulkArgs a);
-__global__ void k_bulk_endpoint_mx(BulkArgs a);
-__global__ void k_fi_mx(FiDevArgs a);
 __global__ void k_iface_geom(GeomArgs g);
 __global__ void k_iface_geom_mx(GeomArgs g);
 __global__ void k_contact_apply(ContactDev C, CouplingOp E, int slot, const double* T, double* Ti, double* out,

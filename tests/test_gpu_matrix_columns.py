@@ -1,0 +1,97 @@
+"""Column forms of the stored matrix K (sdc_set_matrix_columns).
+
+Every SpMV of the path (CG, f^I, bulk endpoints, refinement) reads K through the sliced
+ELL. Its columns are stored as 16-bit offsets from each 32-row slice's smallest column
+when every slice spans at most 65,535 columns, else as 32-bit columns. Either way the
+kernels read the same values and columns in the same order, so:
+  * the two forms give bitwise equal steps, in both precisions;
+  * a node numbering whose slices span more columns (a random renumbering of the stand)
+    takes 32-bit columns by itself and gives the steps of the natural numbering, permuted,
+    to rounding (the rows' entries are then summed in another order).
+"""
+
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from synth import machine_config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def _solver(mach, precision, bits):
+    from paper_1707_03581_gb300 import Solver
+
+    s = Solver(0)
+    s.set_matrix_columns(bits)
+    s.set_machine(mach, precision=precision)
+    return s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("idx", [0, 1])
+def test_column_forms_are_bitwise_equal(torch, precision, idx):
+    mach = machine_config(idx)
+    a = _solver(mach, precision, 0)
+    b = _solver(mach, precision, 32)
+    assert a.matrix_columns() == 16 and b.matrix_columns() == 32
+    for _ in range(3):
+        ra = a.step(report=True)
+        rb = b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    assert ra["cg_iters_total"] == rb["cg_iters_total"]
+    a.close()
+    b.close()
+
+
+def _renumber_stand(mach, perm):
+    """The same machine with stand node j the old node perm[j]."""
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    st = mach.stand
+    mesh = replace(st.mesh, xyz=st.mesh.xyz[perm], hex8=inv[st.mesh.hex8])
+    extra = tuple((inv[q], h, T) for q, h, T in st.robin_extra)
+    stand = replace(st, mesh=mesh, robin_quads=inv[st.robin_quads], robin_extra=extra)
+    return replace(mach, stand=stand, stand_contact=inv[mach.stand_contact])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scrambled_numbering_takes_32_bit_columns(torch, precision):
+    mach = machine_config(1)
+    nf = mach.stand.mesh.n_nodes
+    perm = np.random.default_rng(5).permutation(nf)
+    scr = _renumber_stand(mach, perm)
+    a = _solver(mach, precision, 0)
+    b = _solver(scr, precision, 0)
+    assert a.matrix_columns() == 16 and b.matrix_columns() == 32
+    for _ in range(2):
+        a.step(report=True)
+        b.step(report=True)
+    Ta, Tb = a.temperature(), b.temperature()
+    Tb_nat = Tb.copy()
+    Tb_nat[perm] = Tb[:nf]
+    rise = np.linalg.norm(Ta - mach.T0)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(Tb_nat - Ta) <= tol * rise, np.linalg.norm(Tb_nat - Ta) / rise
+    a.close()
+    b.close()
+
+
+def test_matrix_columns_argument_checks(torch):
+    from paper_1707_03581_gb300 import SdcError, Solver
+
+    s = Solver(0)
+    with pytest.raises(SdcError):
+        s.matrix_columns()  # before assembly
+    with pytest.raises(SdcError):
+        s.set_matrix_columns(16)
+    s.close()
