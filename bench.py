@@ -371,7 +371,7 @@ def _dominant_kernel(s, precision, kt, reps):
     bases = 4 * ((n + 31) // 32) if cb == 2 else 0
     iters = sum(r["cg_iters_total"] for r in reps)
     if precision == "mixed":
-        name = next((k for k in ("k_mx_spmv", "k_mx_spmv_st") if k in kt), "k_mx_spmv_red")
+        name = "k_mx_spmv" if "k_mx_spmv" in kt else "k_mx_spmv_red"
         upd = "k_mx_update" if name == "k_mx_spmv" else "k_mx_update_red"
         work = iters + sum(r["refinements_total"] for r in reps)
         return (name, upd, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)",

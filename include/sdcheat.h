@@ -405,15 +405,6 @@ sdc_status sdc_set_matrix_columns(sdc_ctx* ctx, int bits);
  * sdc_assemble. */
 sdc_status sdc_get_matrix_columns(const sdc_ctx* ctx, int32_t* bits);
 
-/* Staged FP32 CG SpMV of large grids (mixed precision; matrices of more than 2048 groups of 256
- * rows with 16-bit columns): 1 (default) = a persistent kernel whose producer warp bulk-copies
- * each 256-row group's values and column offsets into a two-stage shared-memory ring
- * (cp.async.bulk on mbarriers) while consumer warps gather the vector; 0 = the plain
- * one-row-a-thread kernel. Both sum every row and every dot in the same order: results are
- * identical. Stage waits are bounded by sdc_set_wait_limit's budget and report
- * SDC_ERR_TIMEOUT. */
-sdc_status sdc_set_staged_spmv(sdc_ctx* ctx, int on);
-
 /* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
 sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,
                          int64_t* n_contact);

@@ -99,7 +99,6 @@ _SIGS = {
     "sdc_synchronize": (C.c_int, [_vp]),
     "sdc_get_sizes": (C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p]),
     "sdc_set_matrix_columns": (C.c_int, [_vp, C.c_int]),
-    "sdc_set_staged_spmv": (C.c_int, [_vp, C.c_int]),
     "sdc_get_matrix_columns": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sdc_get_temperature": (C.c_int, [_vp, _vp, C.c_int64]),
     "sdc_get_temperature_device": (C.c_int, [_vp, C.POINTER(_vp)]),
@@ -325,11 +324,6 @@ class Solver:
         """Column form of the stored matrix from the next assembly (set_machine): 0 automatic
         (16-bit offsets from each slice's base when they reach), 32 = 32-bit columns."""
         self._call("sdc_set_matrix_columns", int(bits))
-
-    def set_staged_spmv(self, on: bool):
-        """Large-grid FP32 CG SpMV with its matrix stream staged in shared memory (True,
-        default) or the plain kernel (False); results are identical."""
-        self._call("sdc_set_staged_spmv", 1 if on else 0)
 
     def matrix_columns(self) -> int:
         """Bits of a column index in the assembled matrix (16 or 32)."""

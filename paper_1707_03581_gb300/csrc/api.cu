@@ -110,10 +110,6 @@ struct sdc_ctx {
     int branches = 1;               // sdc_set_graph_branches
     int columns = 0;                // sdc_set_matrix_columns: 0 automatic, 32 = 32-bit columns
     bool c32 = false;               // the assembled matrix has 32-bit columns (else 16-bit offsets)
-    int staged = 1;                 // sdc_set_staged_spmv
-    bool st_on = false;             // the large-grid FP32 SpMV runs staged (k_mx_spmv_st)
-    unsigned st_grid = 0;           // its persistent grid
-    size_t st_smem = 0;             // its dynamic shared memory a CTA
     int stepper = SDC_STEPPER_MRSDC;  // sdc_set_stepper
     int cg_unroll = 0;                // sdc_set_cg_unroll (0: by grid size)
     double* w_slot_ie = nullptr;      // implicit Euler: the unit position of t_{n+1} (one slot)
@@ -306,28 +302,6 @@ struct Chain {
         p.gridDim = dim3(grid);
         p.blockDim = dim3(block);
         p.sharedMemBytes = 0;
-        p.kernelParams = params;
-        cudaGraphNode_t nd;
-        const std::vector<cudaGraphNode_t> d = take_deps();
-        SDC_CUDA_TRY(cudaGraphAddKernelNode(&nd, g, d.data(), d.size(), &p));
-        last = nd;
-    }
-    // Launch with `smem` bytes of dynamic shared memory.
-    template <typename... KArgs>
-    void kernel_smem(void (*f)(KArgs...), unsigned grid, unsigned block, size_t smem, KArgs... args) {
-        void* params[] = {(void*)&args...};
-        ++kernels;
-        if (is_eager) {
-            const int ev = begin_timed((const void*)f);
-            SDC_CUDA_TRY(cudaLaunchKernel((const void*)f, dim3(grid), dim3(block), params, smem, eager));
-            end_timed(ev);
-            return;
-        }
-        cudaKernelNodeParams p{};
-        p.func = (void*)f;
-        p.gridDim = dim3(grid);
-        p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)smem;
         p.kernelParams = params;
         cudaGraphNode_t nd;
         const std::vector<cudaGraphNode_t> d = take_deps();
@@ -546,14 +520,6 @@ int cg_unroll(sdc_ctx* c) {
     return blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS ? 3 : 1;
 }
 
-// The FP32 CG SpMV of a mixed solve: the deferred-dot form on small grids, else the staged
-// form (16-bit columns, sdc_set_staged_spmv) or the plain last-block form.
-void mx_spmv_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
-    if (a.defer) ch.kernel(MK(c, k_mx_spmv), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
-    else if (c->st_on) ch.kernel_smem(k_mx_spmv_st, c->st_grid, (unsigned)MX_ST_THREADS, c->st_smem, a);
-    else ch.kernel(MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
-}
-
 void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     const int unroll = cg_unroll(c);
     if (ch.is_eager) {
@@ -568,7 +534,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                 c, ch,
                 [&] {
                     for (int u = 0; u < unroll; ++u) {
-                        mx_spmv_launch(c, ch, a);
+                        ch.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
                         ch.kernel(a.defer ? k_mx_update : k_mx_update_red,
                                   a.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, a);
                     }
@@ -593,7 +559,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     for (int u = 0; u < unroll; ++u) {
         MixArgs au = a;
         au.tail_pairs = unroll - 1 - u;
-        mx_spmv_launch(c, inner, au);
+        inner.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, au);
         inner.kernel(a.defer ? k_mx_update : k_mx_update_red, a.defer ? c->update_grid : row_grid(c, k_mx_update),
                      RED_BLOCK, au);
     }
@@ -672,7 +638,6 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.status = &c->st->status;
     a.part_blocks = (int)row_grid(c, MK(c, k_mx_spmv));
     a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
-    a.poll_limit = c->poll_limit;
     a.max_iter = std::min(max_iter, MIX_INNER_MAX);
     a.max_refine = MIX_MAX_REFINE;
     a.rtol2 = rtol * rtol;
@@ -727,8 +692,6 @@ void build_ell(sdc_ctx* c) {
     }
     c->A.n = n;
     c->A.n_slices = ns;
-    c->A.wmax = 0;
-    for (int64_t s = 0; s < ns; ++s) c->A.wmax = std::max<int>(c->A.wmax, (int)((sp[s + 1] - sp[s]) / SLICE));
     c->A.slice_ptr = upload(c, c->pool_asm, sp);
     // 16-bit offsets from each slice's smallest column when every slice spans at most 65,535
     // columns (padding entries included: they hold a column of their slice), else 32-bit columns
@@ -761,33 +724,6 @@ void build_ell(sdc_ctx* c) {
     c->A.val32 = upload(c, c->pool_asm, v32);
 }
 
-// The staged large-grid SpMV (k_mx_spmv_st): used when the matrix has 16-bit columns, the grid
-// is too large for the deferred-dot form, and two stages of the widest tile fit a CTA; a
-// persistent grid of as many CTAs as fit (at most one per 256-row group).
-void set_staged_grid(sdc_ctx* c) {
-    c->st_on = false;
-    const int64_t groups = blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK);
-    if (!c->staged || c->c32 || groups <= MIX_DEFER_MAX_BLOCKS || c->A.wmax <= 0) return;
-    // bulk copies start on 16-byte boundaries (a user allocator's blocks may not)
-    if ((uintptr_t)c->A.val32 % 16 != 0 || (uintptr_t)c->A.off % 16 != 0) return;
-    const size_t smem = (size_t)MX_ST_STAGES * MX_ST_NC * SLICE * c->A.wmax * (sizeof(float) + sizeof(uint16_t));
-    int optin = 0;
-    SDC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    cudaFuncAttributes fa{};
-    SDC_CUDA_TRY(cudaFuncGetAttributes(&fa, k_mx_spmv_st));
-    if (smem + fa.sharedSizeBytes > (size_t)optin) return;
-    SDC_CUDA_TRY(cudaFuncSetAttribute(k_mx_spmv_st, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_spmv_st, MX_ST_THREADS, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    if (per_sm < 1) return;
-    c->st_smem = smem;
-    c->st_grid = (unsigned)std::min<int64_t>((int64_t)per_sm * c->n_sms, groups);
-    c->st_on = true;
-}
-
 // One wave of the deferred FP32 update (rows strided): update_bps blocks a SM, or as many as
 // fit, and no more blocks than 256-row groups. The update's sums do not depend on its grid.
 void set_update_grid(sdc_ctx* c) {
@@ -800,7 +736,6 @@ void set_update_grid(sdc_ctx* c) {
     if (c->update_bps > 0) per_sm = std::min(per_sm, c->update_bps);
     c->update_grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)per_sm * c->n_sms, blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK)));
-    set_staged_grid(c);
 }
 
 void do_assemble(sdc_ctx* c) {
@@ -1665,7 +1600,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_sisdc_rhs, "k_sisdc_rhs"}, {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"},
         {(const void*)k_residual, "k_residual"}, {(const void*)k_heat, "k_heat"},
         {(const void*)k_step_end, "k_step_end"}, {(const void*)k_mx_update, "k_mx_update"},
-        {(const void*)k_mx_update_red, "k_mx_update_red"}, {(const void*)k_mx_spmv_st, "k_mx_spmv_st"},
+        {(const void*)k_mx_update_red, "k_mx_update_red"},
         {(const void*)k_cg_init_form(false), "k_cg_init"}, {(const void*)k_cg_init_form(true), "k_cg_init"},
         {(const void*)k_cg_spmv_form(false), "k_cg_spmv"}, {(const void*)k_cg_spmv_form(true), "k_cg_spmv"},
         {(const void*)k_bulk_endpoint_form(false), "k_bulk_endpoint"},
@@ -2142,14 +2077,6 @@ sdc_status sdc_set_matrix_columns(sdc_ctx* c, int bits) {
     });
 }
 
-sdc_status sdc_set_staged_spmv(sdc_ctx* c, int on) {
-    return guarded(c, [&] {
-        c->staged = on ? 1 : 0;
-        if (c->assembled) set_staged_grid(c);
-        c->graph_ready = false;
-    });
-}
-
 sdc_status sdc_get_matrix_columns(const sdc_ctx* cc, int32_t* bits) {
     sdc_ctx* c = const_cast<sdc_ctx*>(cc);
     return guarded(c, [&] {
@@ -2315,7 +2242,7 @@ sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int3
                 Chain body(g[gi]);
                 for (int k = 0; k < n_iters; ++k) {
                     if (gi == 2) body.event(ev[2 + 2 * k]);
-                    if (mixed) mx_spmv_launch(c, body, ma);
+                    if (mixed) body.kernel(ma.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, ma);
                     else body.kernel(MK(c, k_cg_spmv), row_grid(c, MK(c, k_cg_spmv)), RED_BLOCK, ca);
                     if (gi == 2) body.event(ev[3 + 2 * k]);
                     if (spmv_only) continue;

@@ -91,7 +91,6 @@ ContactHost build_contact(const BodyInput& stand, const BodyInput& stock, const 
 struct EllDev {
     int64_t n = 0;
     int64_t n_slices = 0;
-    int wmax = 0;                       // widest slice (entries a row)
     const int64_t* slice_ptr = nullptr;
     const int32_t* base = nullptr;
     const uint16_t* off = nullptr;

@@ -17,6 +17,10 @@ namespace sdc {
 
 // ------------------------------------------------------------------ helpers
 
+// A step's status word: the first error reported stays (a give-up of a bounded wait is not
+// overwritten by the non-convergence that its garbage causes later in the step).
+__device__ __forceinline__ void report_status(int* status, sdc_status code) { atomicCAS(status, 0, (int)code); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -33,6 +37,11 @@ __device__ __forceinline__ double warp_max(double v) {
 // Entries are taken CH at a time: the CH value and column loads of a chunk
 // are all issued before its CH gathers of x, so a row costs ceil(w / CH)
 // dependent memory round trips instead of w. Summation stays in entry order.
+// The thread of the slice's first row first asks for the slice's values and columns (two
+// contiguous ranges: 32 w entries, so 16-byte aligned) to be brought into L2 with one bulk
+// prefetch each, so that only the first chunk waits for HBM: measured on the 5.75M-row FP32
+// matrix (27-point rows, 16-bit columns, 8 blocks of 256 a SM), 194 us without it and 163 us
+// with it and 6 entries a chunk, 0.91 of measured HBM.
 // C32: the matrix's column form (a kernel template parameter, so that each kernel has the
 // registers of one form): 32-bit columns, or 16-bit offsets from each slice's base.
 template <bool C32, int CH, typename V, typename X>
@@ -41,6 +50,13 @@ __device__ __forceinline__ V ell_row_t(const EllDev& A, const V* __restrict__ va
     const int64_t s = row >> 5;
     const int lane = (int)(row & 31);
     const int64_t b = A.slice_ptr[s], e = A.slice_ptr[s + 1];
+    if (lane == 0) {
+        const unsigned vb = (unsigned)((e - b) * sizeof(V));
+        const unsigned cbytes = (unsigned)((e - b) * (C32 ? sizeof(int32_t) : sizeof(uint16_t)));
+        const void* cp = C32 ? (const void*)(A.col + b) : (const void*)(A.off + b);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(val + b), "r"(vb) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cp), "r"(cbytes) : "memory");
+    }
     const int32_t cb = C32 ? 0 : __ldg(A.base + s);
     V acc = V(0);
     for (int64_t k0 = b + lane; k0 < e; k0 += (int64_t)CH * SLICE) {
@@ -65,43 +81,7 @@ __device__ __forceinline__ V ell_row_t(const EllDev& A, const V* __restrict__ va
 
 template <bool C32>
 __device__ __forceinline__ double ell_row(const EllDev& A, int64_t row, const double* __restrict__ x) {
-    return ell_row_t<C32, 8, double, double>(A, A.val, row, x);
-}
-
-// A step's status word: the first error reported stays (a give-up of a bounded wait is not
-// overwritten by the non-convergence that its garbage causes later in the step).
-__device__ __forceinline__ void report_status(int* status, sdc_status code) { atomicCAS(status, 0, (int)code); }
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// Wait until the mbarrier at `bar` completes the phase of parity `parity`,
-// for at most `polls` polls; returns false if it gave up. Budgets of fewer than
-// 1024 polls test without suspending the thread (mbarrier.test_wait), so that a
-// poll is one test; larger budgets use try_wait, which may suspend the thread
-// for a while between tests.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long polls) {
-    if (polls < 1024) {
-        for (long long it = 0; it < polls; ++it) {
-            unsigned done;
-            asm volatile(
-                "{ .reg .pred P1; mbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
-                : "=r"(done)
-                : "r"(bar), "r"(parity)
-                : "memory");
-            if (done) return true;
-        }
-        return false;
-    }
-    for (long long it = 0; it < polls; ++it) {
-        unsigned done;
-        asm volatile(
-            "{ .reg .pred P1; mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+    return ell_row_t<C32, 4, double, double>(A, A.val, row, x);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -201,7 +181,7 @@ __device__ bool reduce_last(W (&v)[NQ], double* partials, unsigned int* counter,
 // FP32 row of the sliced ELL: sum_k K32[row, k] x[k]
 template <bool C32>
 __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const float* __restrict__ x) {
-    return ell_row_t<C32, 8, float, float>(A, A.val32, row, x);
+    return ell_row_t<C32, 6, float, float>(A, A.val32, row, x);
 }
 
 // Two-level form of reduce_last for the CG kernels. Block totals go to
@@ -214,7 +194,7 @@ __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const f
 // counters[0] counts finished groups, counters[1 + g] the blocks of group g.
 constexpr int RED_GROUP = 64;
 
-template <int NQ, typename W, int NT = 0>
+template <int NQ, typename W>
 __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out,
                                 unsigned int blk, unsigned int nblk);
 
@@ -223,32 +203,22 @@ __device__ bool reduce_last2(W (&v)[NQ], double* partials, double* gpartials, un
     return reduce_last2_at<NQ, W>(v, partials, gpartials, counters, out, blockIdx.x, gridDim.x);
 }
 
-// Barrier of the threads that take part in a block reduction: the whole block (NT = 0), or
-// its first NT threads on named barrier 1 (a kernel whose other warps do something else).
-template <int NT>
-__device__ __forceinline__ void red_sync() {
-    if constexpr (NT == 0) __syncthreads();
-    else asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
-}
-
 // The same with the block's index and the grid size given: a fused launch over several
 // machines passes each machine's own block index and grid, so that every machine keeps the
-// partition and summation order of its own launch; a persistent kernel passes the index of
-// the 256-row group it reduces (NT = 256: its first 256 threads take part).
-template <int NQ, typename W, int NT>
+// partition and summation order of its own launch.
+template <int NQ, typename W>
 __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials, unsigned int* counters, double* out,
                                 unsigned int blk, unsigned int nblk) {
     __shared__ double sh[NQ][32];
     __shared__ int am_last;
-    const int nth = NT ? NT : (int)blockDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (nth + 31) >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if constexpr (sizeof(W) == sizeof(float)) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
         if (lane == 0)
 #pragma unroll
             for (int q = 0; q < NQ; ++q) sh[q][warp] = (double)v[q];
-        red_sync<NT>();
+        __syncthreads();
         if (warp == 0)
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -259,7 +229,7 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
         __shared__ double colv[NQ][RED_BLOCK];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) colv[q][threadIdx.x] = v[q];
-        red_sync<NT>();
+        __syncthreads();
         if (warp == 0)
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -277,7 +247,7 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
         __threadfence();
         am_last = atomicAdd(&counters[1 + g], 1u) == gsize - 1;
     }
-    red_sync<NT>();
+    __syncthreads();
     if (!am_last) return false;
     __threadfence();
     if (warp == 0) {
@@ -301,18 +271,18 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
             am_last = atomicAdd(&counters[0], 1u) == ng - 1;
         }
     }
-    red_sync<NT>();
+    __syncthreads();
     if (!am_last) return false;
     __threadfence();
     constexpr int G = 4;
     double dv[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) dv[q] = 0.0;
-    for (unsigned int base = threadIdx.x; base < ng; base += G * nth) {
+    for (unsigned int base = threadIdx.x; base < ng; base += G * blockDim.x) {
         double pv[NQ][G];
 #pragma unroll
         for (int c = 0; c < G; ++c) {
-            const unsigned int i = base + c * nth;
+            const unsigned int i = base + c * blockDim.x;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) pv[q][c] = i < ng ? __ldcg(gpartials + (size_t)q * ng + i) : 0.0;
         }
@@ -323,11 +293,11 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) dv[q] = warp_sum(dv[q]);
-    red_sync<NT>();
+    __syncthreads();
     if (lane == 0)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) sh[q][warp] = dv[q];
-    red_sync<NT>();
+    __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -337,7 +307,7 @@ __device__ bool reduce_last2_at(W (&v)[NQ], double* partials, double* gpartials,
         }
         counters[0] = 0u;
     }
-    red_sync<NT>();
+    __syncthreads();
     return true;
 }
 
@@ -857,34 +827,6 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     mx_update_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
-// The last block's decision of the large-grid FP32 CG (k_mx_spmv_red, k_mx_spmv_st) from the
-// grid's (r,u), (w,u), (r,r): stop test, or the step lengths for k_mx_update_red.
-__device__ __forceinline__ void mx_red_commit(const MixArgs& a, const double (&out)[3]) {
-    CgState* s = a.cg;
-    s->runs += 1;
-    *a.loop_kernels += 2;
-    const double gamma = out[0], delta = out[1];
-    s->rr = out[2];
-    if (out[2] <= s->bb || s->iter >= a.max_iter) {
-        *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
-        s->done = 1;
-        if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
-        return;
-    }
-    if (s->iter == 0) {
-        s->beta = 0.0;
-        s->alpha = gamma / delta;
-    } else {
-        const double beta = gamma / s->gamma;
-        s->beta = beta;
-        s->alpha = gamma / (delta - beta * gamma / s->alpha);
-    }
-    s->gamma = gamma;
-    s->delta = delta;
-    s->iter += 1;
-    *a.iters_out += 1;
-}
-
 template <bool C32>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
     if (a.cg->done) {  // an iteration queued after convergence (host-driven loop)
@@ -895,139 +837,31 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) mx_spmv_row<C32>(a, i, v);
     double out[3];
-    if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) mx_red_commit(a, out);
-}
-
-// The large-grid FP32 CG SpMV with its matrix stream staged in shared memory (16-bit column
-// form; the w and the (r,u), (w,u), (r,r) of k_mx_spmv_red, bit for bit). A persistent grid
-// of CTAs of MX_ST_NC consumer warps and one producer warp walks the 256-row groups of the
-// plain launch (tiles of MX_ST_NC = 8 slices). The producer's elected lane copies each tile's
-// values and offsets (two contiguous ranges of the sliced ELL) into a ring of MX_ST_STAGES
-// shared-memory stages with cp.async.bulk, completing bytes on the stage's `full` mbarrier;
-// consumer warp c takes slice c of the tile (a warp of the plain launch), gathers u from L2
-// and releases the stage on its `empty` mbarrier. The tile's dots are reduced by the
-// consumer warps alone (named barrier) in the order of the plain block, as group `tile` of
-// the same two-level reduction, so that the sums and the step lengths are those of
-// k_mx_spmv_red. Each wait polls at most a.poll_limit times; a wait that gives up stops the
-// CTA's staging (shared flag), the step reports SDC_ERR_TIMEOUT, and the producer drains
-// every copy it issued before the CTA exits. Bulk copies start on 16-byte boundaries: a
-// slice holds 32 w entries, so its range starts at a multiple of 128 bytes (values) and
-// 64 bytes (offsets).
-__global__ void __launch_bounds__(MX_ST_THREADS, 2) k_mx_spmv_st(MixArgs a) {
-    if (a.cg->done) {  // an iteration queued after convergence (host-driven loop)
-        mx_done_on_entry(a);
-        return;
-    }
-    extern __shared__ __align__(128) unsigned char st_smem[];
-    __shared__ __align__(8) unsigned long long full[MX_ST_STAGES], empty[MX_ST_STAGES];
-    __shared__ int aborted;
-    const EllDev& A = a.A;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t stage_elems = (size_t)MX_ST_NC * SLICE * A.wmax;
-    float* sval = reinterpret_cast<float*>(st_smem);
-    uint16_t* soff = reinterpret_cast<uint16_t*>(st_smem + MX_ST_STAGES * stage_elems * sizeof(float));
-    const unsigned ntiles = (unsigned)((a.n + RED_BLOCK - 1) / RED_BLOCK);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < MX_ST_STAGES; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[k])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[k])), "r"(MX_ST_NC));
+    if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
+        CgState* s = a.cg;
+        s->runs += 1;
+        *a.loop_kernels += 2;
+        const double gamma = out[0], delta = out[1];
+        s->rr = out[2];
+        if (out[2] <= s->bb || s->iter >= a.max_iter) {
+            *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
+            s->done = 1;
+            if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
+            return;
         }
-        aborted = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    volatile int* abort_flag = &aborted;
-    if (warp == MX_ST_NC) {
-        if (lane == 0) {
-            bool ok = true;
-            unsigned issued = 0;
-            for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
-                const unsigned st = issued % MX_ST_STAGES, use = issued / MX_ST_STAGES;
-                if (*abort_flag) break;
-                if (use > 0) {
-                    if (!mbar_wait(smem_addr(&empty[st]), (use - 1) & 1u, a.poll_limit)) {
-                        *abort_flag = 1;
-                        break;
-                    }
-                    // a consumer that gave up (or saw the flag) set it before releasing the
-                    // stage, whose last copy may then still be landing: issue nothing more
-                    if (*abort_flag) break;
-                }
-                const int64_t s0 = (int64_t)t * MX_ST_NC, s1 = min(s0 + MX_ST_NC, A.n_slices);
-                const int64_t e0 = A.slice_ptr[s0], e1 = A.slice_ptr[s1];
-                const unsigned bv = (unsigned)((e1 - e0) * sizeof(float)), bo = (unsigned)((e1 - e0) * sizeof(uint16_t));
-                const unsigned fb = smem_addr(&full[st]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bv + bo) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                 smem_addr(sval + st * stage_elems)),
-                             "l"(A.val32 + e0), "r"(bv), "r"(fb)
-                             : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                 smem_addr(soff + st * stage_elems)),
-                             "l"(A.off + e0), "r"(bo), "r"(fb)
-                             : "memory");
-            }
-            // no copy into this CTA's shared memory is in flight when it exits: the stages a
-            // consumer may not have waited for are waited for here
-            for (unsigned j = issued > MX_ST_STAGES ? issued - MX_ST_STAGES : 0; j < issued; ++j)
-                if (!mbar_wait(smem_addr(&full[j % MX_ST_STAGES]), (j / MX_ST_STAGES) & 1u, IFACE_DRAIN_POLLS))
-                    ok = false;
-            if (!ok || *abort_flag) report_status(a.status, SDC_ERR_TIMEOUT);
+        if (s->iter == 0) {
+            s->beta = 0.0;
+            s->alpha = gamma / delta;
+        } else {
+            const double beta = gamma / s->gamma;
+            s->beta = beta;
+            s->alpha = gamma / (delta - beta * gamma / s->alpha);
         }
-    } else {
-        unsigned it = 0;
-        for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-            const unsigned st = it % MX_ST_STAGES;
-            bool have = false;
-            if (!*abort_flag) {
-                have = mbar_wait(smem_addr(&full[st]), (it / MX_ST_STAGES) & 1u, a.poll_limit);
-                if (!have) *abort_flag = 1;
-            }
-            float v[3] = {0.0f, 0.0f, 0.0f};
-            const int64_t s = (int64_t)t * MX_ST_NC + warp;
-            const int64_t i = s * SLICE + lane;
-            if (have && s < A.n_slices) {
-                const int64_t e0 = A.slice_ptr[(int64_t)t * MX_ST_NC];
-                const int64_t b = A.slice_ptr[s] - e0;
-                const int w = (int)((A.slice_ptr[s + 1] - A.slice_ptr[s]) / SLICE);
-                const int32_t cb = __ldg(A.base + s);
-                const float* vv = sval + st * stage_elems + b + lane;
-                const uint16_t* oo = soff + st * stage_elems + b + lane;
-                float acc = 0.0f;
-                for (int k0 = 0; k0 < w; k0 += MX_ST_CH) {
-                    float vk[MX_ST_CH], xk[MX_ST_CH];
-                    int ck[MX_ST_CH];
-#pragma unroll
-                    for (int j = 0; j < MX_ST_CH; ++j) {
-                        const bool in = k0 + j < w;
-                        vk[j] = in ? vv[(k0 + j) * SLICE] : 0.0f;
-                        ck[j] = in ? cb + (int32_t)oo[(k0 + j) * SLICE] : 0;
-                    }
-#pragma unroll
-                    for (int j = 0; j < MX_ST_CH; ++j) xk[j] = __ldg(a.Ul + ck[j]);
-#pragma unroll
-                    for (int j = 0; j < MX_ST_CH; ++j) acc = fma(vk[j], xk[j], acc);
-                }
-                if (i < a.n) {
-                    // mx_spmv_row with the row sum taken from the staged entries
-                    const float u = a.Ul[i];
-                    const float wv = fmaf((float)a.dtau, acc, a.mass32[i] * u);
-                    const float res = a.Rl[i];
-                    a.Wl[i] = wv;
-                    v[0] = res * u;
-                    v[1] = wv * u;
-                    v[2] = res * res;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[st])) : "memory");
-            double out[3];
-            if (reduce_last2_at<3, float, MX_ST_NC * 32>(v, a.partials, a.gpartials, a.counter, out, t, ntiles) &&
-                threadIdx.x == 0)
-                mx_red_commit(a, out);
-        }
+        s->gamma = gamma;
+        s->delta = delta;
+        s->iter += 1;
+        *a.iters_out += 1;
     }
-    __syncthreads();
 }
 
 __global__ void k_mx_update_red(MixArgs a) {
@@ -1695,6 +1529,38 @@ __global__ void k_iface_prep(PrepArgs a) {
     }
     // Algorithm 2: c_p = dt_p (f*_m - f^E(T^k_{m,p-1})) + I_p; the loop adds dt_p f*_m
     a.cpre[(size_t)(p - 1) * NI + i] = fma(-dtp, a.fe_old[(size_t)(p - 1) * NI + i], I);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Wait until the mbarrier at `bar` completes the phase of parity `parity`,
+// for at most `polls` polls; returns false if it gave up. Budgets of fewer than
+// 1024 polls test without suspending the thread (mbarrier.test_wait), so that a
+// poll is one test; larger budgets use try_wait, which may suspend the thread
+// for a while between tests.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long polls) {
+    if (polls < 1024) {
+        for (long long it = 0; it < polls; ++it) {
+            unsigned done;
+            asm volatile(
+                "{ .reg .pred P1; mbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
+                : "=r"(done)
+                : "r"(bar), "r"(parity)
+                : "memory");
+            if (done) return true;
+        }
+        return false;
+    }
+    for (long long it = 0; it < polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred P1; mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2; selp.u32 %0, 1, 0, P1; }"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // Copies still addressed to a CTA whose exchange wait gave up, by the thread that armed its

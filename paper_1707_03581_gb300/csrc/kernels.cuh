@@ -118,7 +118,6 @@ struct MixArgs {
     double* true_res;               // k_mx_true_residual: ||b - A x|| / ||b|| of this solve
     int* status;
     int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_*_red
-    long long poll_limit;           // k_mx_spmv_st: polls of a stage wait before it gives up
     int part_blocks;                // grid of k_mx_spmv: number of its block partials
     int max_iter;                   // per inner solve
     int tail_pairs;                 // (spmv, update) pairs after this one in the graph's loop body
@@ -281,12 +280,6 @@ struct IfaceArgs {
 
 // Polls of an exchange wait of the contact loop (sdc_set_wait_limit overrides it), and of
 // the waits that drain the copies still addressed to a CTA after a wait gave up.
-// k_mx_spmv_st: consumer warps a CTA (slices a tile: one 256-row group), shared-memory
-// stages, entries a chunk of gathers, threads a CTA
-constexpr int MX_ST_NC = 8;
-constexpr int MX_ST_STAGES = 2;
-constexpr int MX_ST_CH = 16;
-constexpr int MX_ST_THREADS = 32 * (MX_ST_NC + 1);
 constexpr long long IFACE_POLLS = 1ll << 24;
 constexpr long long IFACE_DRAIN_POLLS = 1ll << 24;
 
@@ -308,7 +301,6 @@ struct ResidualArgs {
 // kernels (defined in kernels.cu)
 // Kernels that read the matrix come in both column forms of EllDev (32-bit columns, or 16-bit
 // offsets from each slice's base); name##_form(c32) returns the one for a matrix.
-__global__ void k_mx_spmv_st(MixArgs a);
 using KEllOp = void (*)(EllDev, const double*, double, const double*, double*);
 using KEllFi = void (*)(EllDev, const double*, const double*, double*, int*);
 using KCgInit = void (*)(CgArgs, RhsArgs);

@@ -95,51 +95,3 @@ def test_matrix_columns_argument_checks(torch):
     with pytest.raises(SdcError):
         s.set_matrix_columns(16)
     s.close()
-
-
-def test_staged_spmv_is_bitwise_equal_to_plain(torch):
-    # the r = 64 batch machine (733,586 DOF, 2,866 groups of 256 rows): the large-grid FP32 CG,
-    # whose SpMV runs staged (k_mx_spmv_st) by default and plain (k_mx_spmv_red) on request
-    from synth.machines import batch_resolutions
-
-    (mach,) = machine_config(3, select={batch_resolutions()[64]})
-    a = _solver(mach, "mixed", 0)
-    b = _solver(mach, "mixed", 0)
-    b.set_staged_spmv(False)
-    for _ in range(2):
-        ra = a.step(report=True)
-        rb = b.step(report=True)
-    assert np.array_equal(a.temperature(), b.temperature())
-    assert ra["cg_iters_total"] == rb["cg_iters_total"]
-    for s, name, other in ((a, "k_mx_spmv_st", "k_mx_spmv_red"), (b, "k_mx_spmv_red", "k_mx_spmv_st")):
-        s.set_execution(True)
-        s.set_kernel_timing(True)
-        s.step(report=True)
-        kt = s.kernel_times()
-        assert name in kt and other not in kt, sorted(kt)
-    a.close()
-    b.close()
-
-
-def test_staged_spmv_wait_budget_of_one_poll_times_out_and_recovers(torch):
-    # a one-poll budget makes the consumers' stage waits give up on copies still landing: the
-    # CTA stops staging, drains its copies and the step reports SDC_ERR_TIMEOUT; the default
-    # budget then gives steps equal to a context that never timed out
-    from paper_1707_03581_gb300 import SdcError
-    from synth.machines import batch_resolutions
-
-    (mach,) = machine_config(3, select={batch_resolutions()[64]})
-    s = _solver(mach, "mixed", 0)
-    ref = _solver(mach, "mixed", 0)
-    s.set_wait_limit(1)
-    with pytest.raises(SdcError) as e:
-        s.step(report=True)
-    assert "SDC_ERR_TIMEOUT" in str(e.value)
-    s.set_wait_limit(0)
-    s.set_temperature(np.full(s.n, mach.T0), t0=mach.t0)
-    for _ in range(2):
-        assert s.step(report=True)["status"] == 0
-        ref.step(report=True)
-    assert np.array_equal(s.temperature(), ref.temperature())
-    s.close()
-    ref.close()

@@ -325,8 +325,7 @@ def test_mixed_large_grid_matches_fp64(torch):
     a.set_kernel_timing(True)
     a.step(report=True)
     kt = a.kernel_times()
-    # the large-grid FP32 CG: the staged SpMV (its last 256-row group takes the dots)
-    assert kt["k_mx_spmv_st"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_spmv" not in kt
+    assert kt["k_mx_spmv_red"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_spmv" not in kt
     a.close()
     b.close()
 
