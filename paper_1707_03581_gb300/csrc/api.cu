@@ -520,6 +520,25 @@ int cg_unroll(sdc_ctx* c) {
     return blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS ? 3 : 1;
 }
 
+// The FP32 CG pair of a mixed solve: the deferred-dot SpMV and update on small grids, else
+// the last-block SpMV and the update of four rows a thread (one a thread if a vector is not
+// 16-byte aligned, as a user allocator's blocks may be).
+void mx_spmv_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
+    if (a.defer) ch.kernel(MK(c, k_mx_spmv), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
+    else ch.kernel(MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
+}
+
+void mx_update_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
+    if (a.defer) {
+        ch.kernel(k_mx_update, c->update_grid, RED_BLOCK, a);
+        return;
+    }
+    bool aligned = true;
+    for (const float* p : {a.Ul, a.Wl, a.Rl, a.Dinv, a.Pl, a.Sl, a.Dl}) aligned = aligned && (uintptr_t)p % 16 == 0;
+    if (aligned) ch.kernel(k_mx_update_red4, (unsigned)blocks_for((c->n + 3) / 4, RED_BLOCK), RED_BLOCK, a);
+    else ch.kernel(k_mx_update_red, row_grid(c, k_mx_update), RED_BLOCK, a);
+}
+
 void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     const int unroll = cg_unroll(c);
     if (ch.is_eager) {
@@ -534,9 +553,8 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                 c, ch,
                 [&] {
                     for (int u = 0; u < unroll; ++u) {
-                        ch.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
-                        ch.kernel(a.defer ? k_mx_update : k_mx_update_red,
-                                  a.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, a);
+                        mx_spmv_launch(c, ch, a);
+                        mx_update_launch(c, ch, a);
                     }
                 },
                 unroll);
@@ -559,9 +577,8 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
     for (int u = 0; u < unroll; ++u) {
         MixArgs au = a;
         au.tail_pairs = unroll - 1 - u;
-        inner.kernel(a.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, au);
-        inner.kernel(a.defer ? k_mx_update : k_mx_update_red, a.defer ? c->update_grid : row_grid(c, k_mx_update),
-                     RED_BLOCK, au);
+        mx_spmv_launch(c, inner, au);
+        mx_update_launch(c, inner, au);
     }
     outer.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
 }
@@ -1600,7 +1617,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_sisdc_rhs, "k_sisdc_rhs"}, {(const void*)k_sisdc_endpoint, "k_sisdc_endpoint"},
         {(const void*)k_residual, "k_residual"}, {(const void*)k_heat, "k_heat"},
         {(const void*)k_step_end, "k_step_end"}, {(const void*)k_mx_update, "k_mx_update"},
-        {(const void*)k_mx_update_red, "k_mx_update_red"},
+        {(const void*)k_mx_update_red, "k_mx_update_red"}, {(const void*)k_mx_update_red4, "k_mx_update_red"},
         {(const void*)k_cg_init_form(false), "k_cg_init"}, {(const void*)k_cg_init_form(true), "k_cg_init"},
         {(const void*)k_cg_spmv_form(false), "k_cg_spmv"}, {(const void*)k_cg_spmv_form(true), "k_cg_spmv"},
         {(const void*)k_bulk_endpoint_form(false), "k_bulk_endpoint"},
@@ -2242,13 +2259,12 @@ sdc_status sdc_time_cg_iterations(sdc_ctx* c, double dtau, int32_t n_iters, int3
                 Chain body(g[gi]);
                 for (int k = 0; k < n_iters; ++k) {
                     if (gi == 2) body.event(ev[2 + 2 * k]);
-                    if (mixed) body.kernel(ma.defer ? MK(c, k_mx_spmv) : MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, ma);
+                    if (mixed) mx_spmv_launch(c, body, ma);
                     else body.kernel(MK(c, k_cg_spmv), row_grid(c, MK(c, k_cg_spmv)), RED_BLOCK, ca);
                     if (gi == 2) body.event(ev[3 + 2 * k]);
                     if (spmv_only) continue;
                     if (mixed)
-                        body.kernel(ma.defer ? k_mx_update : k_mx_update_red,
-                                    ma.defer ? c->update_grid : row_grid(c, k_mx_update), RED_BLOCK, ma);
+                        mx_update_launch(c, body, ma);
                     else
                         body.kernel(k_cg_update, row_grid(c, k_cg_update), RED_BLOCK, ca);
                 }

@@ -873,6 +873,54 @@ __global__ void k_mx_update_red(MixArgs a) {
     if (i < a.n) mx_update_row(a, i, (float)a.cg->alpha, (float)a.cg->beta, a.cg->iter == 1);
 }
 
+// k_mx_update_red on four consecutive rows a thread with 16-byte loads and stores (vectors
+// 16-byte aligned): four times the bytes in flight a thread, the arithmetic of mx_update_row
+// on every row. The last rows, past the last multiple of four, take mx_update_row.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float& c4(float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+__global__ void k_mx_update_red4(MixArgs a) {
+    const int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= a.n) return;
+    if (a.cg->done) {
+        if (a.cg->iter == 0)
+            for (int64_t i = i0; i < min(i0 + 4, a.n); ++i) a.Dl[i] = 0.0f;
+        return;
+    }
+    const float alpha = (float)a.cg->alpha, beta = (float)a.cg->beta;
+    const bool first = a.cg->iter == 1;
+    if (i0 + 4 > a.n) {
+        for (int64_t i = i0; i < a.n; ++i) mx_update_row(a, i, alpha, beta, first);
+        return;
+    }
+    const float4 u = ld4(a.Ul + i0), w = ld4(a.Wl + i0), rr = ld4(a.Rl + i0), di = ld4(a.Dinv + i0);
+    float4 p = u, sp = w, d = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!first) {
+        p = ld4(a.Pl + i0);
+        sp = ld4(a.Sl + i0);
+        d = ld4(a.Dl + i0);
+    }
+    float4 res, un;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 uu = u, ww = w, r4 = rr, dd = di;
+        const float pk = first ? c4(uu, k) : fmaf(beta, c4(p, k), c4(uu, k));
+        const float sk = first ? c4(ww, k) : fmaf(beta, c4(sp, k), c4(ww, k));
+        c4(p, k) = pk;
+        c4(sp, k) = sk;
+        c4(d, k) = first ? alpha * pk : fmaf(alpha, pk, c4(d, k));
+        const float rk = fmaf(-alpha, sk, c4(r4, k));
+        c4(res, k) = rk;
+        c4(un, k) = rk * c4(dd, k);
+    }
+    st4(a.Pl + i0, p);
+    st4(a.Sl + i0, sp);
+    st4(a.Dl + i0, d);
+    st4(a.Rl + i0, res);
+    st4(a.Ul + i0, un);
+}
+
 // End of a refinement pass: x += d and r -= A d, with r and x in FP64. The
 // residual r = b - A x of the corrected iterate is thereby carried as
 //   r = r0 - A (x - x0),

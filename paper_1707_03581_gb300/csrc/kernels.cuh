@@ -332,6 +332,7 @@ __global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* T
 __global__ void k_cg_update(CgArgs a);
 __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_update_red(MixArgs a);
+__global__ void k_mx_update_red4(MixArgs a);
 __global__ void k_group_begin(GroupArgs g);
 __global__ void k_group_end(GroupArgs g);
 __global__ void k_mx_update_g(GroupArgs g);
