@@ -178,10 +178,11 @@ __device__ bool reduce_last(W (&v)[NQ], double* partials, unsigned int* counter,
     return true;
 }
 
-// FP32 row of the sliced ELL: sum_k K32[row, k] x[k]
-template <bool C32>
+// FP32 row of the sliced ELL: sum_k K32[row, k] x[k], CH entries a chunk (6; the fused batch
+// group's kernels, which hold their member's tables too, take 4 to keep within 32 registers)
+template <bool C32, int CH = 6>
 __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const float* __restrict__ x) {
-    return ell_row_t<C32, 6, float, float>(A, A.val32, row, x);
+    return ell_row_t<C32, CH, float, float>(A, A.val32, row, x);
 }
 
 // Two-level form of reduce_last for the CG kernels. Block totals go to
@@ -656,10 +657,10 @@ __device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G,
 //    lengths.
 
 // FP32 SpMV row i: w = m u + dtau K32 u, and its terms of (r,u), (w,u), (r,r).
-template <bool C32>
+template <bool C32, int CH = 6>
 __device__ __forceinline__ void mx_spmv_row(const MixArgs& a, int64_t i, float (&v)[3]) {
     const float u = a.Ul[i];
-    const float w = fmaf((float)a.dtau, ell_row32<C32>(a.A, i, a.Ul), a.mass32[i] * u);
+    const float w = fmaf((float)a.dtau, ell_row32<C32, CH>(a.A, i, a.Ul), a.mass32[i] * u);
     const float res = a.Rl[i];
     a.Wl[i] = w;
     v[0] = res * u;
@@ -700,7 +701,7 @@ __device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, un
     }
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i < a.n) mx_spmv_row<C32>(a, i, v);
+    if (i < a.n) mx_spmv_row<C32, GROUP ? 4 : 6>(a, i, v);
     block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials), blk, nblk);
 }
 
@@ -938,7 +939,7 @@ __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, 
         const float d = a.Dl[i];
         a.X[i] += (double)d;
         a.Dsum[i] += d;
-        const float Ad = fmaf((float)a.dtau, ell_row32<C32>(a.A, i, a.Dl), a.mass32[i] * d);
+        const float Ad = fmaf((float)a.dtau, ell_row32<C32, GROUP ? 4 : 6>(a.A, i, a.Dl), a.mass32[i] * d);
         const double res = a.R[i] - (double)Ad;
         a.R[i] = res;
         a.Rl[i] = (float)res;  // the next pass's FP32 residual and u (unread if none follows)
