@@ -480,12 +480,12 @@ CgArgs cg_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_iter
 // iteration j+1 is queued before the stop flag after iteration j is examined,
 // so the GPU never waits for the host; an iteration queued after convergence
 // finds the flag set and returns at once. An `iteration` here is one body of
-// the graph's loop: `pairs` (SpMV, update) pairs, each counting a run in
-// CgState::runs when it works. Bodies that did no work are neither counted
+// the graph's loop: `pairs` (SpMV, update) pairs of `pair_kernels` launches, each counting a
+// run in CgState::runs when it works. Bodies that did no work are neither counted
 // nor timed; the pairs after the stop within the last body are, as in the graph.
 template <class Iter>
-void eager_cg_loop(sdc_ctx* c, Chain& ch, Iter iteration, int pairs) {
-    const int KPI = 2 * pairs;  // kernels per iteration
+void eager_cg_loop(sdc_ctx* c, Chain& ch, Iter iteration, int pairs, int pair_kernels = 2) {
+    const int KPI = pair_kernels * pairs;  // kernels per iteration
     iteration();
     int queued = 1;
     for (;;) {
@@ -521,11 +521,11 @@ int cg_unroll(sdc_ctx* c) {
 }
 
 // The FP32 CG pair of a mixed solve: the deferred-dot SpMV and update on small grids, else
-// the last-block SpMV and the update of four rows a thread (one a thread if a vector is not
+// the SpMV, one block that reduces its partials (k_mx_dots), and the update of four rows a thread (one a thread if a vector is not
 // 16-byte aligned, as a user allocator's blocks may be).
 void mx_spmv_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
-    if (a.defer) ch.kernel(MK(c, k_mx_spmv), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
-    else ch.kernel(MK(c, k_mx_spmv_red), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
+    ch.kernel(MK(c, k_mx_spmv), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
+    if (!a.defer) ch.kernel(k_mx_dots, 1u, (unsigned)MX_DOTS_THREADS, a);
 }
 
 void mx_update_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
@@ -557,7 +557,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                         mx_update_launch(c, ch, a);
                     }
                 },
-                unroll);
+                unroll, a.pair_kernels);
             ch.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
         }
         return;
@@ -655,6 +655,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.status = &c->st->status;
     a.part_blocks = (int)row_grid(c, MK(c, k_mx_spmv));
     a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
+    a.pair_kernels = a.defer ? 2 : 3;
     a.max_iter = std::min(max_iter, MIX_INNER_MAX);
     a.max_refine = MIX_MAX_REFINE;
     a.rtol2 = rtol * rtol;
@@ -1618,6 +1619,7 @@ const char* kernel_name(const void* f) {
         {(const void*)k_residual, "k_residual"}, {(const void*)k_heat, "k_heat"},
         {(const void*)k_step_end, "k_step_end"}, {(const void*)k_mx_update, "k_mx_update"},
         {(const void*)k_mx_update_red, "k_mx_update_red"}, {(const void*)k_mx_update_red4, "k_mx_update_red"},
+        {(const void*)k_mx_dots, "k_mx_dots"},
         {(const void*)k_cg_init_form(false), "k_cg_init"}, {(const void*)k_cg_init_form(true), "k_cg_init"},
         {(const void*)k_cg_spmv_form(false), "k_cg_spmv"}, {(const void*)k_cg_spmv_form(true), "k_cg_spmv"},
         {(const void*)k_bulk_endpoint_form(false), "k_bulk_endpoint"},
@@ -1627,8 +1629,6 @@ const char* kernel_name(const void* f) {
         {(const void*)k_fi_form(false), "k_fi"}, {(const void*)k_fi_form(true), "k_fi"},
         {(const void*)k_mx_init_form(false), "k_mx_init"}, {(const void*)k_mx_init_form(true), "k_mx_init"},
         {(const void*)k_mx_spmv_form(false), "k_mx_spmv"}, {(const void*)k_mx_spmv_form(true), "k_mx_spmv"},
-        {(const void*)k_mx_spmv_red_form(false), "k_mx_spmv_red"},
-        {(const void*)k_mx_spmv_red_form(true), "k_mx_spmv_red"},
         {(const void*)k_mx_refine_form(false), "k_mx_refine"}, {(const void*)k_mx_refine_form(true), "k_mx_refine"},
         {(const void*)k_mx_true_residual_form(false), "k_mx_true_residual"},
         {(const void*)k_mx_true_residual_form(true), "k_mx_true_residual"},

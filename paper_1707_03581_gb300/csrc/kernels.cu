@@ -519,7 +519,7 @@ __device__ __forceinline__ void mx_done_on_entry(const MixArgs& a) {
     CgState* s = a.cg;
     if (blockIdx.x == 0 && threadIdx.x == 0 && s->runs == 0) {
         s->runs = -1;
-        *a.loop_kernels += 2 * (1 + a.tail_pairs);
+        *a.loop_kernels += a.pair_kernels * (1 + a.tail_pairs);
         if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
     }
 }
@@ -641,8 +641,8 @@ __device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G,
     __syncthreads();  // sh is reused by the next call
 }
 
-// FP32 CG iteration in two launches (Chronopoulos-Gear form); the kernel
-// boundary serves as the grid-wide barrier. Step lengths (FP64):
+// FP32 CG iteration in two or three launches (Chronopoulos-Gear form); the kernel
+// boundaries serve as the grid-wide barriers. Step lengths (FP64):
 //   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev).
 // Two forms, chosen by the SpMV grid:
 //  * deferred (a.defer, at most MIX_DEFER_MAX_BLOCKS blocks): k_mx_spmv leaves
@@ -651,10 +651,9 @@ __device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G,
 //    decision and forms the step lengths, so that no kernel has a last-block
 //    reduction. The blocks of an update all read the previous step lengths,
 //    so block 0 of the next k_mx_spmv commits the new ones;
-//  * last-block (larger grids, where every block reading every partial would
-//    cost more than that tail): the last block of k_mx_spmv_red sums the
-//    partials (two-level), decides and commits; k_mx_update_red reads the step
-//    lengths.
+//  * three launches (larger grids, where every block reading every partial would
+//    cost more): k_mx_spmv leaves its partials, one block (k_mx_dots) sums them,
+//    decides and commits, and k_mx_update_red4 reads the step lengths.
 
 // FP32 SpMV row i: w = m u + dtau K32 u, and its terms of (r,u), (w,u), (r,r).
 template <bool C32, int CH = 6>
@@ -828,40 +827,74 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update(MixArgs a) {
     mx_update_block<false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
-template <bool C32>
-__global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_red(MixArgs a) {
-    if (a.cg->done) {  // an iteration queued after convergence (host-driven loop)
-        mx_done_on_entry(a);
+// The decision of the large-grid FP32 CG from the grid's (r,u), (w,u), (r,r): stop test, or the
+// step lengths that k_mx_update_red4 reads.
+__device__ __forceinline__ void mx_red_commit(const MixArgs& a, const double (&out)[3]) {
+    CgState* s = a.cg;
+    s->runs += 1;
+    *a.loop_kernels += a.pair_kernels;
+    const double gamma = out[0], delta = out[1];
+    s->rr = out[2];
+    if (out[2] <= s->bb || s->iter >= a.max_iter) {
+        *a.loop_kernels += a.pair_kernels * a.tail_pairs;  // the rest of the loop body runs and returns
+        s->done = 1;
+        if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
         return;
     }
-    float v[3] = {0.0f, 0.0f, 0.0f};
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) mx_spmv_row<C32>(a, i, v);
-    double out[3];
-    if (reduce_last2<3>(v, a.partials, a.gpartials, a.counter, out) && threadIdx.x == 0) {
-        CgState* s = a.cg;
-        s->runs += 1;
-        *a.loop_kernels += 2;
-        const double gamma = out[0], delta = out[1];
-        s->rr = out[2];
-        if (out[2] <= s->bb || s->iter >= a.max_iter) {
-            *a.loop_kernels += 2 * a.tail_pairs;  // the rest of the loop body runs and returns
-            s->done = 1;
-            if (a.h_inner) cudaGraphSetConditional((cudaGraphConditionalHandle)a.h_inner, 0u);
-            return;
+    if (s->iter == 0) {
+        s->beta = 0.0;
+        s->alpha = gamma / delta;
+    } else {
+        const double beta = gamma / s->gamma;
+        s->beta = beta;
+        s->alpha = gamma / (delta - beta * gamma / s->alpha);
+    }
+    s->gamma = gamma;
+    s->delta = delta;
+    s->iter += 1;
+    *a.iters_out += 1;
+}
+
+// The dots of the large-grid FP32 CG from k_mx_spmv's FP32 block partials: one block of
+// MX_DOTS_THREADS sums every block's partial (thread t takes t, t + MX_DOTS_THREADS, ... in
+// index order, in FP32 like the deferred form's sums; FP32 warp butterflies; FP64 over the warp
+// sums) and commits. One SM's FP64 pipe is too narrow for 67k FP64 adds (54 us measured at
+// 5.75M rows); in FP32 the kernel is a few round trips of loads. In a probe on the 5.75M-row
+// FP32 structure (back-to-back SpMVs) the SpMV with stored partials took 175 us against 198 us
+// with a last-block reduction in the SpMV itself, whose fence and atomic keep every block
+// resident for a round trip more.
+__global__ void __launch_bounds__(MX_DOTS_THREADS) k_mx_dots(MixArgs a) {
+    if (a.cg->done) return;  // the SpMV counted the rest of the loop body
+    const float* part = reinterpret_cast<const float*>(a.partials);
+    const int G = a.part_blocks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float t[3] = {0.0f, 0.0f, 0.0f};
+    constexpr int BATCH = 8;  // loads issued together, then added in index order
+    for (int k0 = threadIdx.x; k0 < G; k0 += BATCH * MX_DOTS_THREADS) {
+        float x[3][BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int k = k0 + j * MX_DOTS_THREADS;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) x[q][j] = k < G ? __ldg(part + (size_t)q * G + k) : 0.0f;
         }
-        if (s->iter == 0) {
-            s->beta = 0.0;
-            s->alpha = gamma / delta;
-        } else {
-            const double beta = gamma / s->gamma;
-            s->beta = beta;
-            s->alpha = gamma / (delta - beta * gamma / s->alpha);
-        }
-        s->gamma = gamma;
-        s->delta = delta;
-        s->iter += 1;
-        *a.iters_out += 1;
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) t[q] += x[q][j];
+    }
+    __shared__ double sh[3][32];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        t[q] = warp_sum(t[q]);
+        if (lane == 0) sh[q][warp] = (double)t[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double out[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) out[q] = warp_sum(sh[q][lane]);
+        if (lane == 0) mx_red_commit(a, out);
     }
 }
 
@@ -1152,7 +1185,6 @@ SDC_MATRIX_KERNEL(k_cg_spmv, KCg)
 SDC_MATRIX_KERNEL(k_ie_spmv, KCg)
 SDC_MATRIX_KERNEL(k_mx_init, KMxInit)
 SDC_MATRIX_KERNEL(k_mx_spmv, KMx)
-SDC_MATRIX_KERNEL(k_mx_spmv_red, KMx)
 SDC_MATRIX_KERNEL(k_mx_refine, KMx)
 SDC_MATRIX_KERNEL(k_mx_true_residual, KMx)
 SDC_MATRIX_KERNEL(k_mx_spmv_g, KGroup)

@@ -64,6 +64,7 @@ struct CgArgs {
 // Largest grid of the FP32 SpMV whose dot partials every block of the update
 // sums itself (above it: last-block reduction in the SpMV).
 constexpr int MIX_DEFER_MAX_BLOCKS = 2048;
+constexpr int MX_DOTS_THREADS = 1024;  // k_mx_dots: one block
 constexpr int MX_UPDATE_ROWS = 2;       // rows a thread of k_mx_update loads before the dot sums
 
 // Counters of a fused group of machines (see GroupArgs) during one implicit solve.
@@ -117,7 +118,9 @@ struct MixArgs {
     int* refine_out;                // refinement passes of this solve
     double* true_res;               // k_mx_true_residual: ||b - A x|| / ||b|| of this solve
     int* status;
-    int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_*_red
+    int defer;                      // 1: k_mx_spmv + k_mx_update (deferred dots), 0: k_mx_spmv +
+                                    // k_mx_dots + k_mx_update_red4 (large grids)
+    int pair_kernels;               // kernels of one CG iteration (2 or 3): launch counting
     int part_blocks;                // grid of k_mx_spmv: number of its block partials
     int max_iter;                   // per inner solve
     int tail_pairs;                 // (spmv, update) pairs after this one in the graph's loop body
@@ -318,7 +321,6 @@ KCgInit k_ie_init_form(bool c32);
 KCg k_ie_spmv_form(bool c32);
 KMxInit k_mx_init_form(bool c32);
 KMx k_mx_spmv_form(bool c32);
-KMx k_mx_spmv_red_form(bool c32);
 KMx k_mx_refine_form(bool c32);
 KMx k_mx_true_residual_form(bool c32);
 KGroup k_mx_spmv_g_form(bool c32);
@@ -332,6 +334,7 @@ __global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* T
 __global__ void k_cg_update(CgArgs a);
 __global__ void k_mx_update(MixArgs a);
 __global__ void k_mx_update_red(MixArgs a);
+__global__ void k_mx_dots(MixArgs a);
 __global__ void k_mx_update_red4(MixArgs a);
 __global__ void k_group_begin(GroupArgs g);
 __global__ void k_group_end(GroupArgs g);

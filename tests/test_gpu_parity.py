@@ -325,7 +325,8 @@ def test_mixed_large_grid_matches_fp64(torch):
     a.set_kernel_timing(True)
     a.step(report=True)
     kt = a.kernel_times()
-    assert kt["k_mx_spmv_red"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_spmv" not in kt
+    # the large-grid FP32 CG: SpMV, one block for its dots, update of four rows a thread
+    assert kt["k_mx_spmv"][0] == kt["k_mx_dots"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_update" not in kt
     a.close()
     b.close()
 

@@ -111,10 +111,10 @@ def test_batch_member_of_each_resolution_one_macro_step(torch, r):
         rel, rise = _rel(s.temperature(), ref, mach.T0)
         assert rel <= tol_t and rise <= tol_r, (r, precision, rel, rise)
         if precision == "mixed" and r == 64:
-            # the large-grid FP32 CG: the SpMV's last block takes the dots
+            # the large-grid FP32 CG: one block (k_mx_dots) takes the SpMV's dots
             s.set_execution(True)
             s.set_kernel_timing(True)
             s.step(report=True)
             kt = s.kernel_times()
-            assert kt["k_mx_spmv_red"][0] > 0 and "k_mx_spmv" not in kt
+            assert kt["k_mx_dots"][0] > 0 and kt["k_mx_update_red"][0] > 0 and "k_mx_update" not in kt
         s.close()
