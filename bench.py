@@ -158,7 +158,7 @@ import os, sys, time, json, numpy as np
 sys.path.insert(0, {root!r})
 from synth import machine_config
 from oracle.machine import MachineProblem
-from oracle.mrsdc import mrsdc_step
+from oracle.mrsdc import mrsdc_step, mrsdc_step_reduced
 from oracle.weights import mrsdc_weights
 m = machine_config({idx}); s = m.scheme
 t = time.perf_counter()
@@ -169,7 +169,10 @@ T = np.full(prob.n, m.T0)
 times = []
 for n in range({warmup} + {steps}):
     t = time.perf_counter()
-    T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)
+    if {reduced}:
+        T = mrsdc_step_reduced(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)
+    else:
+        T, _ = mrsdc_step(prob, T, m.t0 + n * s.dt, s.dt, W, s.sweeps)
     if n >= {warmup}:
         times.append(time.perf_counter() - t)
 if {save_to!r}:
@@ -185,7 +188,7 @@ import os, sys, time, json, numpy as np
 sys.path.insert(0, {root!r})
 from synth import machine_config
 from oracle.machine import MachineProblem
-from oracle.mrsdc import predictor_interval
+from oracle.mrsdc import predictor_interval, predictor_interval_reduced
 from oracle.weights import mrsdc_weights
 m = machine_config({idx}); s = m.scheme
 t = time.perf_counter()
@@ -200,7 +203,10 @@ T = np.full(prob.n, m.T0)
 times, it = [], 0
 for n in range({warmup} + {reps}):
     t = time.perf_counter()
-    Temb, it = predictor_interval(prob, T, tau_l, tau_r, emb, n_substeps={substeps})
+    if {reduced}:
+        _, Temb, it = predictor_interval_reduced(prob, T, tau_l, tau_r, emb, n_substeps={substeps})
+    else:
+        Temb, it = predictor_interval(prob, T, tau_l, tau_r, emb, n_substeps={substeps})
     if n >= {warmup}:
         times.append(time.perf_counter() - t)
 print(json.dumps({{"seconds": times, "n": prob.n, "assembly_s": asm, "interval": k + 1, "cg_iters": it,
@@ -221,14 +227,15 @@ def _oracle_finish(proc, timeout=3600):
     return json.loads(out.strip().splitlines()[-1])
 
 
-def _oracle_steps(config_idx, steps, warmup=0, save_to=None):
+def _oracle_steps(config_idx, steps, warmup=0, save_to=None, reduced=False):
+    """reduced: the oracle's interface-only form (substeps on the contact DOFs only)."""
     return _oracle_start(_ORACLE_STEPS.format(root=ROOT, idx=config_idx, steps=steps, warmup=warmup,
-                                              save_to=save_to))
+                                              save_to=save_to, reduced=reduced))
 
 
-def _oracle_sample(config_idx, substeps, reps, warmup=0):
+def _oracle_sample(config_idx, substeps, reps, warmup=0, reduced=False):
     return _oracle_start(_ORACLE_SAMPLE.format(root=ROOT, idx=config_idx, substeps=substeps, reps=reps,
-                                               warmup=warmup))
+                                               warmup=warmup, reduced=reduced))
 
 
 # Workloads whose oracle macro step does not fit a bounded CPU sample: the sample is part of
@@ -245,6 +252,23 @@ def _sample_desc(m, n_int, substeps, res):
             f"and {m.scheme.sweeps} sweeps, whose quadratures and f^E differences the sample leaves out, so this "
             f"rate bounds the oracle's macro-step rate from above; single-threaded numpy/scipy "
             f"(oracle assembly, {res['assembly_s']:.0f} s, not timed)")
+
+
+def _reduced_baseline(proc, m, n_int, config_idx, units_per_step):
+    """The fairer CPU number: the oracle with the substeps on the interface only
+    (oracle.mrsdc.*_reduced), on the same sample, credited the same DOF-substeps."""
+    import numpy as np
+
+    res = _oracle_finish(proc)
+    if config_idx in SAMPLE_SUBSTEPS:
+        S = SAMPLE_SUBSTEPS[config_idx]
+        v = res["n"] * S / float(np.mean(res["seconds"]))
+        sample = (f"the sample above with its {S} substeps on the {m.n_dof}-DOF workload's interface only and "
+                  f"the interval's bulk update skipped (it follows the last substep)")
+    else:
+        v = units_per_step / float(np.mean(res["seconds"]))
+        sample = "one macro step with every embedded substep on the interface only and one bulk update an interval"
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle, interface-only substeps", "sample": sample}
 
 
 def _cpu_baseline_line(value, cores_note, sample, host):
@@ -764,10 +788,13 @@ def run_gpu(args, rank, world):
         # the oracle runs in child processes on the host cores while the GPU work proceeds
         if args.config in SAMPLE_SUBSTEPS:
             oracle["main"] = _oracle_sample(args.config, SAMPLE_SUBSTEPS[args.config], reps=1)
+            oracle["main_red"] = _oracle_sample(args.config, SAMPLE_SUBSTEPS[args.config], reps=1, reduced=True)
         else:
             oracle["main"] = _oracle_steps(args.config, 1, save_to=os.path.join(tmp, "main.npy"))
+            oracle["main_red"] = _oracle_steps(args.config, 1, reduced=True)
         if side_idx is not None:
             oracle["side"] = _oracle_steps(side_idx, 1, save_to=os.path.join(tmp, "side.npy"))
+            oracle["side_red"] = _oracle_steps(side_idx, 1, reduced=True)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     mres = _measure(m, n_int, args, local, torch, flush, world, args.precision, compare)
@@ -839,6 +866,8 @@ def run_gpu(args, rank, world):
                 acc = line.setdefault("accuracy", {})
                 acc.update(_oracle_accuracy(m, args.precision, compare, local, np.load(os.path.join(tmp, "main.npy"))))
             line["cpu_baseline"] = _cpu_baseline_line(v, "1 (BLAS threads = 1)", sample, host)
+            line["cpu_baseline"]["reduced"] = _reduced_baseline(oracle["main_red"], m, n_int, args.config,
+                                                                units_per_step)
         except Exception as e:  # reported, not fatal
             line["cpu_baseline"] = {"error": str(e)[:300]}
         if "side" in oracle:
@@ -849,6 +878,8 @@ def run_gpu(args, rank, world):
                 line["workload_313k"]["cpu_baseline"] = _cpu_baseline_line(
                     side_units / float(np.mean(res["seconds"])), "1 (BLAS threads = 1)",
                     "one full macro step of the 313,646-DOF workload, single-threaded numpy/scipy", host)
+                line["workload_313k"]["cpu_baseline"]["reduced"] = _reduced_baseline(
+                    oracle["side_red"], ms_, ni_, side_idx, side_units)
                 line["workload_313k"].setdefault("accuracy", {}).update(
                     _oracle_accuracy(ms_, args.precision, compare, local, np.load(os.path.join(tmp, "side.npy"))))
             except Exception as e:

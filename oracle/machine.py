@@ -9,6 +9,8 @@ DOFs are numbered stand first, then stock.
 
 Parity: inherits the pins of oracle.fem and oracle.contact; the assembled
 coupled system is additionally pinned by tests/test_oracle_bruteforce.py.
+fE_iface (f^E on the interface DOFs only, for the interface-only form of the
+stepper) is pinned to fE by tests/test_oracle_reduced.py.
 """
 
 from __future__ import annotations
@@ -51,6 +53,10 @@ class MachineProblem:
             raise ValueError("stand and stock contact faces lie in different planes")
         self.fe_calls = 0
         self.cg_total = 0
+        # the interface: every DOF of a contact face, the only DOFs where f^E can be nonzero
+        self.iface = np.unique(np.concatenate([self.fix_quads.ravel(), self.mov_quads.ravel()]))
+        self._fix_local = np.searchsorted(self.iface, self.fix_quads)
+        self._mov_local = np.searchsorted(self.iface, self.mov_quads)
 
     # ---- the stationary initial state of Sec. 5 ----
     def stationary_state(self):
@@ -80,6 +86,16 @@ class MachineProblem:
         du, dv = self.offset(t)
         return ct.contact_flux(T, self.fix_quads, self.mov_quads, self.fix_rect, self.mov_rect,
                                du, dv, self.h_c, self.flux_q(t), self.n)
+
+    def fE_iface(self, Ti, t):
+        """f^E on the interface DOFs (self.iface order) from the temperatures Ti there: the
+        same contact integrals as fE with the faces' nodes numbered within the interface."""
+        self.fe_calls += 1
+        if not self.with_contact:
+            return np.zeros(self.iface.size)
+        du, dv = self.offset(t)
+        return ct.contact_flux(Ti, self._fix_local, self._mov_local, self.fix_rect, self.mov_rect,
+                               du, dv, self.h_c, self.flux_q(t), self.iface.size)
 
     def solve(self, dtau, rhs, x0):
         if dtau == 0.0:

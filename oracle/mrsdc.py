@@ -31,7 +31,10 @@ I_{m,p-1}^p (Eq. embedded_quad) from iterate k; T_0 = T(t_n); for m = 1..M:
 
 Full vectors are kept at every embedded node; nothing is specialised to the
 location of the contact, so the fast library path (which runs the P substeps
-only on contact DOFs) is checked against this plain form.
+only on contact DOFs) is checked against this plain form. mrsdc_step_reduced
+and predictor_interval_reduced take the substeps on the interface only (the
+fairer CPU baseline); they are pinned to the literal form by
+tests/test_oracle_reduced.py and serve no parity test.
 
 Residual (Eq. residual, with the sum index read as j, i.e. sum_{j<=m} I_{j-1}^j):
     r^k = max_m || M T^k_m - M T(t_n) - sum_{j=1}^m I_{j-1}^j ||_inf
@@ -168,6 +171,92 @@ def mrsdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False, keep_nodes=F
     if keep_nodes:
         res.T_std, res.T_emb = T_std, T_emb
     return T_std[M].copy(), res
+
+
+# ---------------------------------------------------------------------------
+# The same step with the embedded substeps taken on the interface only (the fairer CPU
+# baseline). Off the contact f^E vanishes, so there the P substeps of an interval add up to
+#   M T_m = M T_{m-1} + dtau_m f*_m + I_{m-1}^m
+# (sum_p dt_{m,p} = dtau_m; sum_p S~[m,p,j] = S[m,j] and sum_p S_emb[m,p,q] = S^[m,q], and the
+# f^E terms of I_{m-1}^m are zero there), and only the interface DOFs (prob.iface, with
+# prob.fE_iface) need every substep. Equal to mrsdc_step up to the order of rounding.
+# The problem object also provides iface (sorted interface DOFs) and fE_iface(Ti, t).
+
+
+def predictor_interval_reduced(prob, T_left, tau_left, tau_right, tau_emb_m, n_substeps=None):
+    """predictor_interval with the substeps on the interface: returns (T_m, the interface
+    temperatures [T_{m,0}, ..., T_{m,P}] there, CG iterations). n_substeps < P stops after that
+    many interface substeps (a bounded sample; T_m is then None)."""
+    mass, I = prob.mass, prob.iface
+    P = len(tau_emb_m) - 1
+    dtau = tau_right - tau_left
+    rhs = mass * T_left + dtau * prob.g(tau_right)
+    Tstar, it = prob.solve(dtau, rhs, T_left)
+    fstar = prob.fI(Tstar) + prob.g(tau_right)
+    Ti = [T_left[I].copy()]
+    mi, fi = mass[I], fstar[I]
+    for p in range(1, (P if n_substeps is None else min(P, n_substeps)) + 1):
+        dtp = tau_emb_m[p] - tau_emb_m[p - 1]
+        Ti.append(Ti[p - 1] + dtp * (fi + prob.fE_iface(Ti[p - 1], tau_emb_m[p - 1])) / mi)
+    if len(Ti) < P + 1:
+        return None, Ti, it
+    T_m = T_left + dtau * fstar / mass
+    T_m[I] = Ti[P]
+    return T_m, Ti, it
+
+
+def mrsdc_step_reduced(prob, T_n, t_n, dt, W, sweeps):
+    """One macro step as mrsdc_step, substeps on the interface only; returns T(t_n + dt)."""
+    M, P = W["M"], W["P"]
+    c, emb = W["c"], W["emb"]
+    tau = [t_n + dt * c[m] for m in range(M + 1)]
+    tau_emb = [[t_n + dt * emb[m][p] for p in range(P + 1)] for m in range(M)]
+    mass, I = prob.mass, prob.iface
+    mi = mass[I]
+
+    # Algorithm 1, and f^E of the predictor at every embedded node of the interface
+    T_std = [T_n.copy()] + [None] * M
+    FE = [None] * M
+    for m in range(M):
+        T_std[m + 1], Ti, _ = predictor_interval_reduced(prob, T_std[m], tau[m], tau[m + 1], tau_emb[m])
+        FE[m] = [prob.fE_iface(Ti[q], tau_emb[m][q]) for q in range(P + 1)]
+
+    # Algorithm 2
+    for k in range(sweeps):
+        FI = [prob.fI(T_std[j + 1]) + prob.g(tau[j + 1]) for j in range(M)]
+        new_std = [T_n.copy()] + [None] * M
+        new_FE = [None] * M
+        for m in range(M):
+            dtau = tau[m + 1] - tau[m]
+            I_std = np.zeros_like(T_n)
+            for j in range(M):
+                I_std = I_std + dt * W["S"][m, j] * FI[j]
+            for q in range(P):
+                I_std[I] = I_std[I] + dt * W["Shat"][m, q] * FE[m][q + 1]
+            fI_old = FI[m] - prob.g(tau[m + 1])
+            rhs = mass * new_std[m] - dtau * fI_old + I_std
+            Tstar, _ = prob.solve(dtau, rhs, T_std[m + 1])
+            fstar = prob.fI(Tstar) - fI_old
+            # off the contact: the substeps' sum
+            T_m = new_std[m] + (dtau * fstar + I_std) / mass
+            # on the contact: every substep
+            Ti = new_std[m][I].copy()
+            fe_row = [prob.fE_iface(Ti, tau_emb[m][0])]
+            for p in range(1, P + 1):
+                dtp = tau_emb[m][p] - tau_emb[m][p - 1]
+                I_emb = np.zeros(I.size)
+                for j in range(M):
+                    I_emb = I_emb + dt * W["Stil"][m, p - 1, j] * FI[j][I]
+                for q in range(P):
+                    I_emb = I_emb + dt * W["Semb"][m, p - 1, q] * FE[m][q + 1]
+                fe_new = fe_row[p - 1]
+                Ti = Ti + (dtp * fstar[I] + dtp * (fe_new - FE[m][p - 1]) + I_emb) / mi
+                fe_row.append(prob.fE_iface(Ti, tau_emb[m][p]))
+            T_m[I] = Ti
+            new_std[m + 1] = T_m
+            new_FE[m] = fe_row
+        T_std, FE = new_std, new_FE
+    return T_std[M].copy()
 
 
 def sisdc_step(prob, T_n, t_n, dt, W, sweeps, want_residuals=False):
