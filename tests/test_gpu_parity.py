@@ -310,25 +310,35 @@ def test_mixed_eager_matches_graph(torch):
 
 
 def test_mixed_large_grid_matches_fp64(torch):
-    # 733,586 DOFs: grids above the deferred-dot limit, where the SpMV's last
-    # block hands the dots to the update; the FP64 path is the oracle-pinned one.
+    # 733,586 DOFs: grids above the deferred-dot limit, where one block (k_mx_dots) sums the
+    # SpMV's partials; the FP64 path is the oracle-pinned one
     mach = machine_config(3, truncate=1)[0]
     a = _solver(mach, precision="mixed")
     b = _solver(mach, precision="fp64")
+    c = _solver(mach, precision="mixed")
+    c.set_execution(True)
     for _ in range(2):
         a.step(report=True)
         b.step(report=True)
+        c.step(report=True)
     Ta, Tb = a.temperature(), b.temperature()
     assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb) <= 1e-9
     assert np.linalg.norm(Ta - Tb) / np.linalg.norm(Tb - mach.T0) <= REL_MIXED
-    a.set_execution(True)
-    a.set_kernel_timing(True)
-    a.step(report=True)
-    kt = a.kernel_times()
+    # eager execution: the same results as the graph, and the same launches (one timed step)
+    assert np.array_equal(Ta, c.temperature())
+    c.set_kernel_timing(True)
+    ra = a.step(report=True)
+    rc = c.step(report=True)
+    assert np.array_equal(a.temperature(), c.temperature())
+    assert ra["kernel_launches"] == rc["kernel_launches"]
+    kt = c.kernel_times()
+    assert sum(n for n, _ in kt.values()) == rc["kernel_launches"]
     # the large-grid FP32 CG: SpMV, one block for its dots, update of four rows a thread
     assert kt["k_mx_spmv"][0] == kt["k_mx_dots"][0] == kt["k_mx_update_red"][0] > 0 and "k_mx_update" not in kt
+    assert kt["k_mx_refine"][0] == rc["refinements_total"]
     a.close()
     b.close()
+    c.close()
 
 
 def test_config2_full_size_mixed_matches_fp64(torch):
