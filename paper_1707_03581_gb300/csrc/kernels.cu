@@ -1312,15 +1312,32 @@ __device__ __forceinline__ void iface_geom_impl(const GeomArgs& g) {
                 for (int t = B.ptr[bin]; t < B.ptr[bin + 1]; ++t) {
                     const int Rf = B.item[t];
                     Rect4 Rr = C.rect[Rf];
-                    if (!stock) {
-                        Rr.x += du; Rr.z += du; Rr.y += dv; Rr.w += dv;
+                    R ua_, ub_, va_, vb_, rlu, rhu, rlv, rhv;
+                    if constexpr (std::is_same<R, float>::value) {
+                        // mixed: four FP64 differences to the low corner of Q in the partner's
+                        // frame (qlu = Q.x - shift), then FP32; the overlap test keeps its sign
+                        // exactly (a rounded difference is zero only when the FP64 one is)
+                        const double qlu = Q.x - su, qlv = Q.y - sv;
+                        rlu = (R)(Rr.x - qlu);
+                        rhu = (R)(Rr.z - qlu);
+                        rlv = (R)(Rr.y - qlv);
+                        rhv = (R)(Rr.w - qlv);
+                        ua_ = fmaxf(R(0), rlu);
+                        ub_ = fminf(qwu, rhu);
+                        va_ = fmaxf(R(0), rlv);
+                        vb_ = fminf(qwv, rhv);
+                        if (!(ub_ > ua_ && vb_ > va_)) continue;
+                    } else {
+                        if (!stock) {
+                            Rr.x += du; Rr.z += du; Rr.y += dv; Rr.w += dv;
+                        }
+                        const double ua = fmax(Q.x, Rr.x), ub = fmin(Q.z, Rr.z);
+                        const double va = fmax(Q.y, Rr.y), vb = fmin(Q.w, Rr.w);
+                        if (!(ub > ua && vb > va)) continue;
+                        // coordinates relative to the low corner of Q
+                        ua_ = (R)(ua - Q.x); ub_ = (R)(ub - Q.x); va_ = (R)(va - Q.y); vb_ = (R)(vb - Q.y);
+                        rlu = (R)(Rr.x - Q.x); rhu = (R)(Rr.z - Q.x); rlv = (R)(Rr.y - Q.y); rhv = (R)(Rr.w - Q.y);
                     }
-                    const double ua = fmax(Q.x, Rr.x), ub = fmin(Q.z, Rr.z);
-                    const double va = fmax(Q.y, Rr.y), vb = fmin(Q.w, Rr.w);
-                    if (!(ub > ua && vb > va)) continue;
-                    // coordinates relative to the low corner of Q
-                    const R ua_ = (R)(ua - Q.x), ub_ = (R)(ub - Q.x), va_ = (R)(va - Q.y), vb_ = (R)(vb - Q.y);
-                    const R rlu = (R)(Rr.x - Q.x), rhu = (R)(Rr.z - Q.x), rlv = (R)(Rr.y - Q.y), rhv = (R)(Rr.w - Q.y);
                     const double2 ri = C.rinv[Rf];
                     const R rix = (R)ri.x, riy = (R)ri.y;
                     const int4 rn = C.qnode[Rf];
