@@ -1593,9 +1593,27 @@ __global__ void k_iface_tc(ContactDev C, const double* __restrict__ T, double* _
 
 // c_p of every substep and contact DOF (see PrepArgs); one thread per (p, DOF),
 // p = 0..P (p = 0 only forms base_0 in mixed precision).
+// Length of substep p of the interval of a k_iface_prep launch (the embedded nodes' times at
+// this step, as the substep loop forms them).
+__device__ __forceinline__ double prep_dtp(const PrepArgs& a, int p) {
+    const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
+    return __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
+}
+
 __global__ void k_iface_prep(PrepArgs a) {
     const int NI = a.C.n_iface;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the substep lengths of this block's rows: with NI >= blockDim a block spans at most two
+    // substeps, whose lengths (a dozen FP64 operations, on GB300's narrow FP64 pipe) are formed
+    // once per block; smaller interfaces form them per thread
+    const bool per_block = NI >= (int)blockDim.x;
+    __shared__ double s_dtp[2];
+    const int p_first = (int)(((int64_t)blockIdx.x * blockDim.x) / NI);
+    if (per_block && threadIdx.x < 2) {
+        const int pp = p_first + (int)threadIdx.x;
+        if (pp >= 1 && pp <= a.P) s_dtp[threadIdx.x] = prep_dtp(a, pp);
+    }
+    __syncthreads();
     if (gid >= (int64_t)NI * (a.P + 1)) return;
     const int p = (int)(gid / NI), i = (int)(gid % NI);
     if (a.base) {
@@ -1616,14 +1634,16 @@ __global__ void k_iface_prep(PrepArgs a) {
         a.base[(size_t)p * NI + i] = acc;
     }
     if (p == 0 || a.mode == RHS_PRED) return;  // Algorithm 1: c_p = dt_p f*_m (formed by the loop)
-    const double tn = __dadd_rn(a.st->t0, __dmul_rn((double)a.st->n_done, a.st->dt));
-    const double dtp = __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p])) - __dadd_rn(tn, __dmul_rn(a.dt, a.emb[p - 1]));
+    const double dtp = per_block ? s_dtp[p - p_first] : prep_dtp(a, p);
     const int row = a.C.dof[i];
     double I = 0.0;
     for (int j = 0; j < a.nFI; ++j) I = fma(a.Stil[(size_t)(p - 1) * a.nFI + j], a.FI[j][row], I);
+    // the embedded quadrature's row is windowed (M nonzero weights of P): zero weights are
+    // skipped by an integer test of their bits (a -0.0 weight adds -0.0 to a sum that starts at
+    // +0.0 and changes nothing), not by an FP64 compare
     for (int qq = 1; qq <= a.P; ++qq) {
         const double wq = a.Semb[(size_t)(p - 1) * a.P + (qq - 1)];
-        if (wq != 0.0) I = fma(wq, a.fe_old[(size_t)qq * NI + i], I);
+        if (((unsigned long long)__double_as_longlong(wq) << 1) != 0ull) I = fma(wq, a.fe_old[(size_t)qq * NI + i], I);
     }
     // Algorithm 2: c_p = dt_p (f*_m - f^E(T^k_{m,p-1})) + I_p; the loop adds dt_p f*_m
     a.cpre[(size_t)(p - 1) * NI + i] = fma(-dtp, a.fe_old[(size_t)(p - 1) * NI + i], I);
