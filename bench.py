@@ -1089,7 +1089,8 @@ def run_serving(args, rank, world):
     machines = machine_config(3)
     sched = serving_requests(args.lam, n_requests=args.requests, seed=0, pool=len(machines))
     out = {}
-    for prec in ("mixed", "fp64"):
+    precs = (args.precision,) if args.no_compare else ("mixed", "fp64")
+    for prec in precs:
         server = LookAheadServer(machines, device=local, precision=prec, max_active=args.max_active)
         reqs = [Request(r["arrival_s"], round(r["horizon_s"]), r["machine_index"]) for r in sched]
         if world > 1:
@@ -1112,24 +1113,27 @@ def run_serving(args, rank, world):
         server.close()
     if rank != 0:
         return
-    mx, f64 = out["mixed"], out["fp64"]
+    # the line's own figures are those of the first precision served (mixed unless only FP64 ran)
+    mx = out[precs[0]]
+    f64 = out.get("fp64") if len(precs) == 2 else None
     line = {
         "metric": METRIC, "value": mx["dof_substeps_per_s"], "unit": UNIT, "n_gpus": world,
         "steps": sum(round(r["horizon_s"]) for r in sched), "warmup": 0,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if precs[0] == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"serving: {args.requests} Poisson arrivals at {args.lam}/s of look-ahead requests "
                                f"(horizon ~ U(30,600) s rounded to whole macro steps) on a pool of 64 machines "
                                f"(12.9k-734k DOF), warm-start state kept on the device",
-                   "precision": "mixed vs fp64, same requests", "parallelism": f"continuous batching, up to "
+                   "precision": "mixed vs fp64, same requests" if f64 else precs[0],
+                   "parallelism": f"continuous batching, up to "
                    f"{args.max_active} requests in flight, replicas x{world}"},
         "latency_s": mx["latency_s"], "eta_per_request": mx["eta_per_request"],
         "offered_simulated_s_per_s": args.lam * world * sum(round(r["horizon_s"]) for r in sched) / len(sched),
         "served_simulated_s_per_s": mx["simulated_s_per_s"],
-        "mixed": mx, "fp64": f64,
+        **{p: out[p] for p in precs},
         "gain_vs_fp64": {"throughput": mx["dof_substeps_per_s"] / f64["dof_substeps_per_s"],
                          "p99_latency": f64["latency_s"]["p99"] / mx["latency_s"]["p99"],
-                         "p50_latency": f64["latency_s"]["p50"] / mx["latency_s"]["p50"]},
+                         "p50_latency": f64["latency_s"]["p50"] / mx["latency_s"]["p50"]} if f64 else None,
     }
     print(json.dumps(line), flush=True)
 
@@ -1141,7 +1145,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run of the mixed path")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 comparison run of the mixed path (config 4: serve the requests in "
+                         "--precision only)")
     ap.add_argument("--config", type=int, default=2,
                     help="0/1/2: one machine (2 = the headline workload, the largest single-GPU one); "
                          "3: the batch of 64 machines; "
