@@ -385,8 +385,9 @@ def _dominant_kernel(s, precision, kt, reps):
     """The CG SpMV of the timed path and its algorithmic bytes per launch that did work.
 
     Per SpMV: every nonzero's value and column (FP32 4 or FP64 8 bytes, and a 16-bit
-    offset from its 32-row slice's base, 2 bytes, or a 32-bit column, 4 bytes), the
-    slices' 4-byte bases, plus the row vectors it reads (u, r, m) and writes (w). The
+    offset from its 32-row slice's base, 2 bytes, or a 32-bit column, 4 bytes; none for
+    the FP32 copy with implied columns), the slices' 4-byte bases (or table positions),
+    plus the row vectors it reads (u, r, m) and writes (w). The
     SpMVs that did work in the timed steps are the CG updates plus one stopping
     SpMV per inner solve (from the steps' reports); the loop bodies' later
     launches after a stop return at once, and their time stays in the total. On large
@@ -397,6 +398,8 @@ def _dominant_kernel(s, precision, kt, reps):
     bases = 4 * ((n + 31) // 32) if cb == 2 else 0
     iters = sum(r["cg_iters_total"] for r in reps)
     if precision == "mixed":
+        if s.matrix_implied():  # the FP32 copy: values only, one 4-byte table position a slice
+            cb, bases = 0, 4 * ((n + 31) // 32)
         name = "k_mx_spmv"
         upd = "k_mx_update" if "k_mx_update" in kt else "k_mx_update_red"
         work = iters + sum(r["refinements_total"] for r in reps)
@@ -406,7 +409,7 @@ def _dominant_kernel(s, precision, kt, reps):
         return (name, upd, "FP32 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)"
                 + (" and its one-block dot sums (k_mx_dots)" if "k_mx_dots" in kt else ""),
                 (4 + cb) * nnz + 16 * n + bases, 48 * n, work, sp, kt.get(upd, (0, 0.0)),
-                f"{4 + cb} B/nnz + 16 B/row + 4 B per 32-row slice" if cb == 2 else f"{4 + cb} B/nnz + 16 B/row")
+                f"{4 + cb} B/nnz + 16 B/row + 4 B per 32-row slice" if cb != 4 else f"{4 + cb} B/nnz + 16 B/row")
     work = iters + sum(r["n_solves"] for r in reps)
     return ("k_cg_spmv", "k_cg_update", "FP64 sliced-ELL SpMV w = m u + dtau K u with (r,u), (w,u), (r,r)",
             (8 + cb) * nnz + 32 * n + bases, 96 * n, work, kt.get("k_cg_spmv", (0, 0.0)),

@@ -394,16 +394,29 @@ sdc_status sdc_scheme_weights(sdc_nodes nodes, int M, int P, int window, double*
                               double* Shat, double* Stil, double* Semb);
 
 /* Column form of the stored matrix K (Eq. coupledFEM; sliced ELL of 32-row slices, read by
- * every SpMV of the implicit solves, f^I and the bulk endpoints): 0 (default) = 16-bit offsets
- * from each slice's smallest column when every slice spans at most 65,535 columns (2 bytes an
- * entry instead of 4; a 27-point stencil numbered plane by plane spans about two node planes),
- * else 32-bit columns; 32 = 32-bit columns always. Takes effect at the next sdc_assemble.
- * Results are identical. SDC_ERR_ARG for other values. */
+ * every SpMV of the implicit solves, f^I and the bulk endpoints):
+ *   0 (default) = 16-bit offsets from each slice's smallest column when every slice spans at
+ *     most 65,535 columns (2 bytes an entry instead of 4; a 27-point stencil numbered plane by
+ *     plane spans about two node planes), else 32-bit columns; and the FP32 copy that the
+ *     mixed-precision solves stream has implied columns when the matrix allows them: each
+ *     slice's rows share one increasing table of relative columns (col - row), absent
+ *     neighbours hold 0, and no column is stored (4 bytes an entry instead of 6). Allowed when
+ *     every row's columns increase, a slice's table has at most 64 entries and the layout
+ *     holds at most 1.25 times the entries of the offsets form: a mesh numbered plane by
+ *     plane qualifies, a scrambled numbering does not;
+ *   16 = as 0 without implied columns;
+ *   32 = 32-bit columns always, no implied columns.
+ * Takes effect at the next sdc_assemble. Results are identical in every form: each row's
+ * products are summed in the same order. SDC_ERR_ARG for other values. */
 sdc_status sdc_set_matrix_columns(sdc_ctx* ctx, int bits);
 
 /* Bits of a column index in the assembled matrix: 16 or 32. SDC_ERR_STATE before
  * sdc_assemble. */
 sdc_status sdc_get_matrix_columns(const sdc_ctx* ctx, int32_t* bits);
+
+/* 1 when the assembled matrix's FP32 copy has implied columns (see sdc_set_matrix_columns),
+ * else 0. SDC_ERR_STATE before sdc_assemble, SDC_ERR_ARG for a null pointer. */
+sdc_status sdc_get_matrix_implied(const sdc_ctx* ctx, int32_t* implied);
 
 /* Sizes: total DOFs, stand DOFs, stored nonzeros of K, contact DOFs. */
 sdc_status sdc_get_sizes(const sdc_ctx* ctx, int64_t* n_dof, int64_t* n_stand, int64_t* nnz,

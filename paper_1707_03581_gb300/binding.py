@@ -100,6 +100,7 @@ _SIGS = {
     "sdc_get_sizes": (C.c_int, [_vp, _i64p, _i64p, _i64p, _i64p]),
     "sdc_set_matrix_columns": (C.c_int, [_vp, C.c_int]),
     "sdc_get_matrix_columns": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
+    "sdc_get_matrix_implied": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sdc_get_temperature": (C.c_int, [_vp, _vp, C.c_int64]),
     "sdc_get_temperature_device": (C.c_int, [_vp, C.POINTER(_vp)]),
     "sdc_get_heat_totals": (C.c_int, [_vp, C.POINTER(Heat)]),
@@ -322,7 +323,9 @@ class Solver:
 
     def set_matrix_columns(self, bits: int):
         """Column form of the stored matrix from the next assembly (set_machine): 0 automatic
-        (16-bit offsets from each slice's base when they reach), 32 = 32-bit columns."""
+        (16-bit offsets from each slice's base when they reach, and implied columns for the
+        FP32 copy when the matrix allows them), 16 = the same without implied columns,
+        32 = 32-bit columns."""
         self._call("sdc_set_matrix_columns", int(bits))
 
     def matrix_columns(self) -> int:
@@ -330,6 +333,12 @@ class Solver:
         b = C.c_int32()
         self._call("sdc_get_matrix_columns", C.byref(b))
         return b.value
+
+    def matrix_implied(self) -> bool:
+        """Whether the assembled matrix's FP32 copy has implied columns (no stored column)."""
+        b = C.c_int32()
+        self._call("sdc_get_matrix_implied", C.byref(b))
+        return bool(b.value)
 
     def set_graph_branches(self, on: bool):
         """Run solve-independent kernels beside the implicit solves (True) or in one chain."""

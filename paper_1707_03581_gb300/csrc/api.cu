@@ -108,8 +108,9 @@ struct sdc_ctx {
     int force_global = 0;           // sdc_set_contact_replicas
     int max_cluster = 0;            // sdc_set_contact_cluster (0: automatic)
     int branches = 1;               // sdc_set_graph_branches
-    int columns = 0;                // sdc_set_matrix_columns: 0 automatic, 32 = 32-bit columns
+    int columns = 0;                // sdc_set_matrix_columns: 0 automatic, 16 = no implied, 32 = 32-bit
     bool c32 = false;               // the assembled matrix has 32-bit columns (else 16-bit offsets)
+    bool implied = false;           // its FP32 copy has implied columns (ImpliedEll)
     int stepper = SDC_STEPPER_MRSDC;  // sdc_set_stepper
     int cg_unroll = 0;                // sdc_set_cg_unroll (0: by grid size)
     double* w_slot_ie = nullptr;      // implicit Euler: the unit position of t_{n+1} (one slot)
@@ -171,6 +172,9 @@ void* dalloc(sdc_ctx* c, std::vector<void*>& pool, size_t bytes) {
 
 // a kernel that reads the matrix, in the column form of the context's assembled matrix
 #define MK(c, k) k##_form((c)->c32)
+// the form of the FP32 copy: 2 = implied columns, else as the FP64 matrix
+inline int form32(const sdc_ctx* c) { return c->implied ? 2 : c->c32 ? 1 : 0; }
+#define MK32(c, k) k##_form32(form32(c))
 
 template <class T>
 T* dalloc_n(sdc_ctx* c, std::vector<void*>& pool, size_t count) {
@@ -524,7 +528,7 @@ int cg_unroll(sdc_ctx* c) {
 // the SpMV, one block that reduces its partials (k_mx_dots), and the update of four rows a thread (one a thread if a vector is not
 // 16-byte aligned, as a user allocator's blocks may be).
 void mx_spmv_launch(sdc_ctx* c, Chain& ch, const MixArgs& a) {
-    ch.kernel(MK(c, k_mx_spmv), row_grid(c, MK(c, k_mx_spmv)), RED_BLOCK, a);
+    ch.kernel(MK32(c, k_mx_spmv), row_grid(c, MK32(c, k_mx_spmv)), RED_BLOCK, a);
     if (!a.defer) ch.kernel(k_mx_dots, 1u, (unsigned)MX_DOTS_THREADS, a);
 }
 
@@ -558,7 +562,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
                     }
                 },
                 unroll, a.pair_kernels);
-            ch.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
+            ch.kernel(MK32(c, k_mx_refine), row_grid(c, MK32(c, k_mx_refine)), RED_BLOCK, a);
         }
         return;
     }
@@ -580,7 +584,7 @@ void add_solve_mixed(sdc_ctx* c, Chain& ch, MixArgs a, const RhsArgs& r) {
         mx_spmv_launch(c, inner, au);
         mx_update_launch(c, inner, au);
     }
-    outer.kernel(MK(c, k_mx_refine), row_grid(c, MK(c, k_mx_refine)), RED_BLOCK, a);
+    outer.kernel(MK32(c, k_mx_refine), row_grid(c, MK32(c, k_mx_refine)), RED_BLOCK, a);
 }
 
 // init kernel, then WHILE { spmv, update, p-update }
@@ -653,7 +657,7 @@ MixArgs mix_args(sdc_ctx* c, double dtau, int solve_idx, double rtol, int max_it
     a.refine_out = &c->st->refinements[solve_idx];
     a.true_res = &c->st->true_res[solve_idx];
     a.status = &c->st->status;
-    a.part_blocks = (int)row_grid(c, MK(c, k_mx_spmv));
+    a.part_blocks = (int)row_grid(c, MK32(c, k_mx_spmv));
     a.defer = a.part_blocks <= MIX_DEFER_MAX_BLOCKS ? 1 : 0;
     a.pair_kernels = a.defer ? 2 : 3;
     a.max_iter = std::min(max_iter, MIX_INNER_MAX);
@@ -738,8 +742,23 @@ void build_ell(sdc_ctx* c) {
         c->A.col = upload(c, c->pool_asm, col);
     }
     c->A.val = upload(c, c->pool_asm, val);
-    std::vector<float> v32(val.begin(), val.end());
-    c->A.val32 = upload(c, c->pool_asm, v32);
+    // the FP32 copy: implied columns when the matrix allows them (automatic form only), else
+    // the layout of the FP64 values
+    c->implied = false;
+    c->A.slice_ptr32 = nullptr;
+    c->A.stab = nullptr;
+    c->A.stoff = nullptr;
+    ImpliedEll ie;
+    if (c->columns == 0 && build_implied_ell(c->K, ie)) {
+        c->implied = true;
+        c->A.slice_ptr32 = upload(c, c->pool_asm, ie.slice_ptr);
+        c->A.stab = upload(c, c->pool_asm, ie.tab);
+        c->A.stoff = upload(c, c->pool_asm, ie.off);
+        c->A.val32 = upload(c, c->pool_asm, ie.val);
+    } else {
+        std::vector<float> v32(val.begin(), val.end());
+        c->A.val32 = upload(c, c->pool_asm, v32);
+    }
 }
 
 // One wave of the deferred FP32 update (rows strided): update_bps blocks a SM, or as many as
@@ -1181,7 +1200,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             fa.dT = c->dTv;
             fa.F = c->FI[set][m - 1];
             fa.n = c->n;
-            ch.kernel(MK(c, k_fi_mx), row_grid(c, MK(c, k_fi_mx)), (unsigned)RED_BLOCK, fa);
+            ch.kernel(MK32(c, k_fi_mx), row_grid(c, MK32(c, k_fi_mx)), (unsigned)RED_BLOCK, fa);
         } else {
             ch.kernel(MK(c, k_fi), row_grid(c, MK(c, k_fi)), (unsigned)RED_BLOCK, c->A, (const double*)c->d_genv,
                       (const double*)c->Tstd[m], c->FI[set][m - 1], (int*)nullptr);
@@ -1198,7 +1217,7 @@ void emit_step(sdc_ctx* c, Chain& ch) {
             b.Fx0 = Fx0;
             b.dT = c->dTv;
         }
-        auto kern = mixed ? MK(c, k_bulk_endpoint_mx) : MK(c, k_bulk_endpoint);
+        auto kern = mixed ? MK32(c, k_bulk_endpoint_mx) : MK(c, k_bulk_endpoint);
         b.rows = BULK_CONTACT;
         ch.kernel(kern, blocks_for(std::max(NI, 1), 256), 256u, b);
         b.rows = BULK_OFF_CONTACT;
@@ -1628,13 +1647,17 @@ const char* kernel_name(const void* f) {
         {(const void*)k_ie_spmv_form(false), "k_ie_spmv"}, {(const void*)k_ie_spmv_form(true), "k_ie_spmv"},
         {(const void*)k_fi_form(false), "k_fi"}, {(const void*)k_fi_form(true), "k_fi"},
         {(const void*)k_mx_init_form(false), "k_mx_init"}, {(const void*)k_mx_init_form(true), "k_mx_init"},
-        {(const void*)k_mx_spmv_form(false), "k_mx_spmv"}, {(const void*)k_mx_spmv_form(true), "k_mx_spmv"},
-        {(const void*)k_mx_refine_form(false), "k_mx_refine"}, {(const void*)k_mx_refine_form(true), "k_mx_refine"},
+        {(const void*)k_mx_spmv_form32(0), "k_mx_spmv"}, {(const void*)k_mx_spmv_form32(1), "k_mx_spmv"},
+        {(const void*)k_mx_spmv_form32(2), "k_mx_spmv"},
+        {(const void*)k_mx_refine_form32(0), "k_mx_refine"}, {(const void*)k_mx_refine_form32(1), "k_mx_refine"},
+        {(const void*)k_mx_refine_form32(2), "k_mx_refine"},
         {(const void*)k_mx_true_residual_form(false), "k_mx_true_residual"},
         {(const void*)k_mx_true_residual_form(true), "k_mx_true_residual"},
-        {(const void*)k_bulk_endpoint_mx_form(false), "k_bulk_endpoint_mx"},
-        {(const void*)k_bulk_endpoint_mx_form(true), "k_bulk_endpoint_mx"},
-        {(const void*)k_fi_mx_form(false), "k_fi_mx"}, {(const void*)k_fi_mx_form(true), "k_fi_mx"},
+        {(const void*)k_bulk_endpoint_mx_form32(0), "k_bulk_endpoint_mx"},
+        {(const void*)k_bulk_endpoint_mx_form32(1), "k_bulk_endpoint_mx"},
+        {(const void*)k_bulk_endpoint_mx_form32(2), "k_bulk_endpoint_mx"},
+        {(const void*)k_fi_mx_form32(0), "k_fi_mx"}, {(const void*)k_fi_mx_form32(1), "k_fi_mx"},
+        {(const void*)k_fi_mx_form32(2), "k_fi_mx"},
     };
     for (const auto& n : names)
         if (n.first == f) return n.second;
@@ -2089,7 +2112,7 @@ sdc_status sdc_synchronize(sdc_ctx* c) {
 
 sdc_status sdc_set_matrix_columns(sdc_ctx* c, int bits) {
     return guarded(c, [&] {
-        require(bits == 0 || bits == 32, SDC_ERR_ARG, "bits must be 0 (automatic) or 32");
+        require(bits == 0 || bits == 16 || bits == 32, SDC_ERR_ARG, "bits must be 0 (automatic), 16 or 32");
         c->columns = bits;
     });
 }
@@ -2100,6 +2123,15 @@ sdc_status sdc_get_matrix_columns(const sdc_ctx* cc, int32_t* bits) {
         require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
         require(bits != nullptr, SDC_ERR_ARG, "bits is null");
         *bits = c->c32 ? 32 : 16;
+    });
+}
+
+sdc_status sdc_get_matrix_implied(const sdc_ctx* cc, int32_t* implied) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    return guarded(c, [&] {
+        require(c->assembled, SDC_ERR_STATE, "call sdc_assemble first");
+        require(implied != nullptr, SDC_ERR_ARG, "implied is null");
+        *implied = c->implied ? 1 : 0;
     });
 }
 
@@ -2546,14 +2578,15 @@ void member_check(sdc_ctx* c, sdc_status st, int i) {
 // launches, and the loops end when the last member stops. Every member's chain waits for
 // the group solve before it goes on. Eligible: mixed precision, MRSDC, grids of at most
 // MIX_DEFER_MAX_BLOCKS blocks (deferred dots), no diagnostics, graph execution, and the
-// same scheme (the same sequence of solves) as the group's first member.
+// same scheme (the same sequence of solves) and matrix form as the group's first member.
 bool fusable(const sdc_ctx* c, const sdc_ctx* ref) {
     const bool ok = c->precision == SDC_MIXED_FP32 && c->stepper == SDC_STEPPER_MRSDC && !c->residuals &&
                     !c->true_res && !c->eager &&
                     blocks_for(std::max<int64_t>(c->n, 1), RED_BLOCK) <= (unsigned)MIX_DEFER_MAX_BLOCKS;
     if (!ok || !ref) return ok;
     return c->W.kind == ref->W.kind && c->W.M == ref->W.M && c->W.P == ref->W.P && c->W.w == ref->W.w &&
-           c->K_sweeps == ref->K_sweeps && c->dt == ref->dt && c->nondeg == ref->nondeg && c->c32 == ref->c32;
+           c->K_sweeps == ref->K_sweeps && c->dt == ref->dt && c->nondeg == ref->nondeg && c->c32 == ref->c32 &&
+           c->implied == ref->implied;
 }
 
 void group_release(sdc_batch* b) {
@@ -2641,7 +2674,7 @@ void build_group(sdc_batch* b) {
     }
     std::vector<int> n_spmv(nm), n_upd(nm);
     for (size_t i = 0; i < nm; ++i) {
-        n_spmv[i] = (int)row_grid(b->group[i], MK(b->group[i], k_mx_spmv));
+        n_spmv[i] = (int)row_grid(b->group[i], MK32(b->group[i], k_mx_spmv));
         n_upd[i] = (int)b->group[i]->update_grid;
     }
     unsigned t_spmv = 0, t_upd = 0, t_ref = 0;
@@ -2673,10 +2706,10 @@ void build_group(sdc_batch* b) {
         for (int u = 0; u < unroll; ++u) {
             GroupArgs gu = g;
             gu.tail_pairs = unroll - 1 - u;
-            inner.kernel(MK(b->group[0], k_mx_spmv_g), t_spmv, (unsigned)RED_BLOCK, gu);
+            inner.kernel(MK32(b->group[0], k_mx_spmv_g), t_spmv, (unsigned)RED_BLOCK, gu);
             inner.kernel(k_mx_update_g, t_upd, (unsigned)RED_BLOCK, gu);
         }
-        outer.kernel(MK(b->group[0], k_mx_refine_g), t_ref, (unsigned)RED_BLOCK, g);
+        outer.kernel(MK32(b->group[0], k_mx_refine_g), t_ref, (unsigned)RED_BLOCK, g);
         gc.kernel(k_group_end, 1u, 32u, g);
         for (size_t i = 0; i < nm; ++i) SDC_CUDA_TRY(cudaGraphAddDependencies(G, &gc.last, &out[i][k], nullptr, 1));
     }

@@ -58,6 +58,26 @@ int window_start(int p, int P, int w);
 // Assemble K = -(A + B_env) (CSR, sorted columns), lumped mass and b_env of one body.
 void assemble_body(const BodyInput& b, HostCSR& K, std::vector<double>& mass, std::vector<double>& genv);
 
+// FP32 copy of K with implied columns. Entry k of every row of slice s sits at
+// slice_ptr[s] + 32 k + lane and belongs to column row + off[t_s + k], where the table
+// off[t_s ..] is the increasing union of the relative columns (col - row) of the slice's
+// rows; a row that lacks one of them holds 0 there. No column is stored: a 27-point stencil
+// numbered plane by plane has a handful of distinct tables, shared by most slices.
+// tab[s] = t_s, or ~t_s when some row of the slice would reach outside [0, n) with some
+// offset of its table (the kernels clamp those columns; their entries are 0).
+struct ImpliedEll {
+    std::vector<int64_t> slice_ptr;  // n_slices + 1
+    std::vector<int32_t> tab;        // n_slices
+    std::vector<int32_t> off;        // the distinct tables, concatenated
+    std::vector<float> val;          // slice_ptr[n_slices]
+};
+constexpr int IMPLIED_MAX_WIDTH = 64;  // entries a row of the implied layout at most
+
+// Build the implied-column layout of K. Returns false (and leaves the other forms in use) when
+// a row's columns are not increasing, n >= 2^30, a slice's union exceeds IMPLIED_MAX_WIDTH, or
+// the layout stores more than 1.25 times the entries of the offsets form.
+bool build_implied_ell(const HostCSR& K, ImpliedEll& out);
+
 struct BinsHost {
     double ou = 0, ov = 0, bu = 1, bv = 1;
     int nu = 0, nv = 0;
@@ -97,6 +117,12 @@ struct EllDev {
     const int32_t* col = nullptr;
     const double* val = nullptr;
     const float* val32 = nullptr;
+    // Set when val32 holds the FP32 copy in the implied-column layout (ImpliedEll): its own
+    // slice pointers, the per-slice table starts and the tables. NULL otherwise, and val32 is
+    // then laid out like val.
+    const int64_t* slice_ptr32 = nullptr;
+    const int32_t* stab = nullptr;
+    const int32_t* stoff = nullptr;
 };
 
 // Axis-aligned rectangle in the contact plane: x = lo_u, y = lo_v, z = hi_u, w = hi_v.

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 
 #include "common.h"
@@ -211,6 +212,70 @@ void assemble_body(const BodyInput& B, HostCSR& K, std::vector<double>& mass, st
             }
         }
     }
+}
+
+// The implied-column layout of K's FP32 copy (see ImpliedEll). Entries of a row run over its
+// slice's table in increasing offset, that is in increasing column, as the CSR row does, so
+// an SpMV that sums a row's entries in storage order adds the same products in the same order
+// as the offsets form, with zeros between them.
+bool build_implied_ell(const HostCSR& K, ImpliedEll& out) {
+    const int64_t n = K.n;
+    if (n <= 0 || n >= (int64_t(1) << 30)) return false;
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t k = K.row_ptr[r] + 1; k < K.row_ptr[r + 1]; ++k)
+            if (K.col[k] <= K.col[k - 1]) return false;
+    const int64_t ns = (n + SLICE - 1) / SLICE;
+    out.slice_ptr.assign(ns + 1, 0);
+    out.tab.assign(ns, 0);
+    out.off.clear();
+    std::map<std::vector<int32_t>, int32_t> seen;
+    std::vector<int32_t> u;
+    int64_t stored_offsets_form = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t r0 = s * SLICE, r1 = std::min(n, r0 + SLICE);
+        u.clear();
+        int64_t w = 0;
+        for (int64_t r = r0; r < r1; ++r) {
+            w = std::max(w, K.row_ptr[r + 1] - K.row_ptr[r]);
+            for (int64_t k = K.row_ptr[r]; k < K.row_ptr[r + 1]; ++k) u.push_back(K.col[k] - (int32_t)r);
+        }
+        stored_offsets_form += w * SLICE;
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        if (u.empty() || (int64_t)u.size() > IMPLIED_MAX_WIDTH) return false;
+        // offsets increase, so the first row with the smallest and the last row with the
+        // largest are the only ones that can leave [0, n)
+        const bool clamp = r0 + u.front() < 0 || (r1 - 1) + u.back() >= n;
+        int32_t t;
+        const auto it = seen.find(u);
+        if (it == seen.end()) {
+            t = (int32_t)out.off.size();
+            out.off.insert(out.off.end(), u.begin(), u.end());
+            seen.emplace(u, t);
+        } else {
+            t = it->second;
+        }
+        out.tab[s] = clamp ? ~t : t;
+        out.slice_ptr[s + 1] = out.slice_ptr[s] + (int64_t)u.size() * SLICE;
+    }
+    if (out.slice_ptr[ns] * 4 > stored_offsets_form * 5) return false;
+    out.val.assign(out.slice_ptr[ns], 0.0f);
+    for (int64_t s = 0; s < ns; ++s) {
+        const int32_t t = out.tab[s] < 0 ? ~out.tab[s] : out.tab[s];
+        const int64_t w = (out.slice_ptr[s + 1] - out.slice_ptr[s]) / SLICE;
+        for (int lane = 0; lane < SLICE; ++lane) {
+            const int64_t r = s * SLICE + lane;
+            if (r >= n) break;
+            int64_t k = K.row_ptr[r];
+            for (int64_t q = 0; q < w && k < K.row_ptr[r + 1]; ++q)
+                if ((int64_t)K.col[k] - r == out.off[t + q]) {
+                    out.val[out.slice_ptr[s] + q * SLICE + lane] = (float)K.val[k];
+                    ++k;
+                }
+            if (k != K.row_ptr[r + 1]) return false;  // cannot happen: the table holds every offset
+        }
+    }
+    return true;
 }
 
 }  // namespace sdc

@@ -178,11 +178,54 @@ __device__ bool reduce_last(W (&v)[NQ], double* partials, unsigned int* counter,
     return true;
 }
 
+// FP32 row of the implied-column layout (A.stab set): entry k of the row is column
+// row + stoff[t + k] of the slice's table t, so only values stream from memory (4 bytes an
+// entry) and the table, one per slice shape, comes from L1 with one broadcast load per entry
+// for the warp. A slice flagged by ~t clamps its columns to [0, n); the clamped entries hold 0.
+// The entries run in increasing column, so the products and their order are those of the
+// offsets form (the zeros of absent neighbours add nothing).
+template <int CH>
+__device__ __forceinline__ float ell_row_implied(const EllDev& A, int64_t row, const float* __restrict__ x) {
+    const int64_t s = row >> 5;
+    const int lane = (int)(row & 31);
+    const int64_t b = A.slice_ptr32[s], e = A.slice_ptr32[s + 1];
+    if (lane == 0) {
+        const unsigned vb = (unsigned)((e - b) * sizeof(float));
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.val32 + b), "r"(vb) : "memory");
+    }
+    int32_t q = __ldg(A.stab + s);  // table position of the chunk's first entry
+    const bool clamp = q < 0;
+    if (clamp) q = ~q;
+    const int32_t r = (int32_t)row;
+    float acc = 0.0f;
+    for (int64_t k0 = b + lane; k0 < e; k0 += (int64_t)CH * SLICE, q += CH) {
+        float v[CH];
+        int32_t c[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int64_t k = k0 + (int64_t)j * SLICE;
+            const bool in = k < e;  // entry (k - b) / 32 of a table of (e - b) / 32 entries
+            v[j] = in ? __ldg(A.val32 + k) : 0.0f;
+            int32_t cc = in ? r + __ldg(A.stoff + (q + j)) : r;
+            if (clamp) cc = min(max(cc, 0), (int32_t)A.n - 1);
+            c[j] = cc;
+        }
+        float xv[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) xv[j] = __ldg(x + c[j]);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) acc = fmaf(v[j], xv[j], acc);
+    }
+    return acc;
+}
+
 // FP32 row of the sliced ELL: sum_k K32[row, k] x[k], CH entries a chunk (6; the fused batch
-// group's kernels, which hold their member's tables too, take 4 to keep within 32 registers)
-template <bool C32, int CH = 6>
+// group's kernels, which hold their member's tables too, take 4 to keep within 32 registers).
+// F is the FP32 copy's form: 0 = 16-bit offsets, 1 = 32-bit columns, 2 = implied columns.
+template <int F, int CH = 6>
 __device__ __forceinline__ float ell_row32(const EllDev& A, int64_t row, const float* __restrict__ x) {
-    return ell_row_t<C32, CH, float, float>(A, A.val32, row, x);
+    if constexpr (F == 2) return ell_row_implied<CH>(A, row, x);
+    else return ell_row_t<F == 1, CH, float, float>(A, A.val32, row, x);
 }
 
 // Two-level form of reduce_last for the CG kernels. Block totals go to
@@ -656,10 +699,10 @@ __device__ __forceinline__ void all_blocks_sum_f32(const float* partials, int G,
 //    decides and commits, and k_mx_update_red4 reads the step lengths.
 
 // FP32 SpMV row i: w = m u + dtau K32 u, and its terms of (r,u), (w,u), (r,r).
-template <bool C32, int CH = 6>
+template <int F, int CH = 6>
 __device__ __forceinline__ void mx_spmv_row(const MixArgs& a, int64_t i, float (&v)[3]) {
     const float u = a.Ul[i];
-    const float w = fmaf((float)a.dtau, ell_row32<C32, CH>(a.A, i, a.Ul), a.mass32[i] * u);
+    const float w = fmaf((float)a.dtau, ell_row32<F, CH>(a.A, i, a.Ul), a.mass32[i] * u);
     const float res = a.Rl[i];
     a.Wl[i] = w;
     v[0] = res * u;
@@ -685,7 +728,7 @@ __device__ __forceinline__ void mx_update_row(const MixArgs& a, int64_t i, float
 // 5.75M rows a probe of this SpMV took 218 us at 8 blocks a SM against 244 us at 6.
 // One block of the deferred-dot FP32 SpMV: block blk of a launch of nblk blocks for the
 // machine of `a` (its own launch, or its range of a fused group launch).
-template <bool C32, bool GROUP>
+template <int F, bool GROUP>
 __device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, unsigned nblk) {
     CgState* s = a.cg;
     if (s->done) {  // an iteration after the stop (rest of the loop body, host-driven lookahead)
@@ -700,13 +743,13 @@ __device__ __forceinline__ void mx_spmv_block(const MixArgs& a, unsigned blk, un
     }
     float v[3] = {0.0f, 0.0f, 0.0f};
     const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i < a.n) mx_spmv_row<C32, GROUP ? 4 : 6>(a, i, v);
+    if (i < a.n) mx_spmv_row<F, GROUP ? 4 : 6>(a, i, v);
     block_partials_f32<3>(v, reinterpret_cast<float*>(a.partials), blk, nblk);
 }
 
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv(MixArgs a) {
-    mx_spmv_block<C32, false>(a, blockIdx.x, gridDim.x);
+    mx_spmv_block<F, false>(a, blockIdx.x, gridDim.x);
 }
 
 // One block of the FP32 CG update (deferred dots), block blk of nblk for the machine of
@@ -963,7 +1006,7 @@ __global__ void k_mx_update_red4(MixArgs a) {
 // rounding is relative to the correction, not to b. Outer stop test.
 // One block of the end of a refinement pass (see k_mx_refine), block blk of nblk for the
 // machine of `a`; in a fused group the outer loop stops with the last member's convergence.
-template <bool C32, bool GROUP>
+template <int F, bool GROUP>
 __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, unsigned nblk, const GroupArgs& g) {
     if (GROUP && a.ms->done) return;  // a member whose refinement converged in an earlier pass
     double v[1] = {0.0};
@@ -972,7 +1015,7 @@ __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, 
         const float d = a.Dl[i];
         a.X[i] += (double)d;
         a.Dsum[i] += d;
-        const float Ad = fmaf((float)a.dtau, ell_row32<C32, GROUP ? 4 : 6>(a.A, i, a.Dl), a.mass32[i] * d);
+        const float Ad = fmaf((float)a.dtau, ell_row32<F, GROUP ? 4 : 6>(a.A, i, a.Dl), a.mass32[i] * d);
         const double res = a.R[i] - (double)Ad;
         a.R[i] = res;
         a.Rl[i] = (float)res;  // the next pass's FP32 residual and u (unread if none follows)
@@ -1003,9 +1046,9 @@ __device__ __forceinline__ void mx_refine_block(const MixArgs& a, unsigned blk, 
     }
 }
 
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine(MixArgs a) {
-    mx_refine_block<C32, false>(a, blockIdx.x, gridDim.x, GroupArgs{});
+    mx_refine_block<F, false>(a, blockIdx.x, gridDim.x, GroupArgs{});
 }
 
 // Fused group launches: the member of each block and its block within the member's range.
@@ -1043,7 +1086,7 @@ __device__ __forceinline__ void group_cap_failed(const GroupArgs& g) {
     for (int m = 0; m < g.n_members; ++m) report_status(g.args[m].status, SDC_ERR_NOT_CONVERGED);
 }
 
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_g(GroupArgs g) {
     // the inner loop ends after this body when no member's CG runs (the counter changes only
     // in the updates, outside this launch) or after launch_cap SpMV launches in the pass
@@ -1056,7 +1099,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_spmv_g(GroupArgs g) {
     }
     unsigned blk, nblk;
     const MixArgs& a = group_member(g, g.spmv, blk, nblk);
-    mx_spmv_block<C32, true>(a, blk, nblk);
+    mx_spmv_block<F, true>(a, blk, nblk);
 }
 
 __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update_g(GroupArgs g) {
@@ -1065,7 +1108,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 5) k_mx_update_g(GroupArgs g) {
     mx_update_block<true>(a, blk, nblk, g);
 }
 
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine_g(GroupArgs g) {
     // the outer loop ends after this pass when no member is refining or after pass_cap passes
     // (members that go on set the inner loop's condition again for their next pass)
@@ -1079,7 +1122,7 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_mx_refine_g(GroupArgs g) {
     }
     unsigned blk, nblk;
     const MixArgs& a = group_member(g, g.refine, blk, nblk);
-    mx_refine_block<C32, true>(a, blk, nblk, g);
+    mx_refine_block<F, true>(a, blk, nblk, g);
 }
 
 // Diagnostics of a mixed solve: the true residual ||b - (m x + dtau K x)|| / ||b|| with the
@@ -1140,11 +1183,11 @@ __global__ void k_bulk_endpoint(BulkArgs a) {
 //   predictor: f*_m = F^I(T*) + g = F(x0) - K dX
 //   sweep:     f*_m = f^I(T*) - f^I(T^k_m) = -K dX          (x0 = T^k_m)
 // K dX as an FP32 SpMV; the increment of every row goes to dT for k_fi_mx.
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_bulk_endpoint_mx(BulkArgs a) {
     const int64_t i = bulk_row(a);
     if (i >= 0) {
-        const double KdX = (double)ell_row32<C32>(a.A, i, a.dX);
+        const double KdX = (double)ell_row32<F>(a.A, i, a.dX);
         double incr, fstar;
         if (a.mode == RHS_PRED) {
             fstar = a.Fx0[i] - KdX;
@@ -1167,10 +1210,10 @@ __global__ void __launch_bounds__(RED_BLOCK, 8) k_bulk_endpoint_mx(BulkArgs a) {
 }
 
 // F^I(T_m) + g = F^I(T_prev) + g - K dT (mixed precision; FP32 SpMV of the increment)
-template <bool C32>
+template <int F>
 __global__ void __launch_bounds__(RED_BLOCK, 8) k_fi_mx(FiDevArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) a.F[i] = a.Fprev[i] - (double)ell_row32<C32>(a.A, i, a.dT);
+    if (i < a.n) a.F[i] = a.Fprev[i] - (double)ell_row32<F>(a.A, i, a.dT);
 }
 
 // Both column forms of every kernel that reads the matrix (EllDev), for the host code of
@@ -1184,15 +1227,20 @@ SDC_MATRIX_KERNEL(k_ie_init, KCgInit)
 SDC_MATRIX_KERNEL(k_cg_spmv, KCg)
 SDC_MATRIX_KERNEL(k_ie_spmv, KCg)
 SDC_MATRIX_KERNEL(k_mx_init, KMxInit)
-SDC_MATRIX_KERNEL(k_mx_spmv, KMx)
-SDC_MATRIX_KERNEL(k_mx_refine, KMx)
 SDC_MATRIX_KERNEL(k_mx_true_residual, KMx)
-SDC_MATRIX_KERNEL(k_mx_spmv_g, KGroup)
-SDC_MATRIX_KERNEL(k_mx_refine_g, KGroup)
 SDC_MATRIX_KERNEL(k_bulk_endpoint, KBulk)
-SDC_MATRIX_KERNEL(k_bulk_endpoint_mx, KBulk)
-SDC_MATRIX_KERNEL(k_fi_mx, KFi)
 #undef SDC_MATRIX_KERNEL
+// The kernels that read only the FP32 copy, in its three forms (0 = 16-bit offsets,
+// 1 = 32-bit columns, 2 = implied columns)
+#define SDC_MATRIX32_KERNEL(name, type) \
+    type name##_form32(int f) { return f == 2 ? name<2> : f == 1 ? name<1> : name<0>; }
+SDC_MATRIX32_KERNEL(k_mx_spmv, KMx)
+SDC_MATRIX32_KERNEL(k_mx_refine, KMx)
+SDC_MATRIX32_KERNEL(k_mx_spmv_g, KGroup)
+SDC_MATRIX32_KERNEL(k_mx_refine_g, KGroup)
+SDC_MATRIX32_KERNEL(k_bulk_endpoint_mx, KBulk)
+SDC_MATRIX32_KERNEL(k_fi_mx, KFi)
+#undef SDC_MATRIX32_KERNEL
 
 // ------------------------------------------------------------------ contact geometry
 

@@ -320,14 +320,16 @@ KCg k_cg_spmv_form(bool c32);
 KCgInit k_ie_init_form(bool c32);
 KCg k_ie_spmv_form(bool c32);
 KMxInit k_mx_init_form(bool c32);
-KMx k_mx_spmv_form(bool c32);
-KMx k_mx_refine_form(bool c32);
 KMx k_mx_true_residual_form(bool c32);
-KGroup k_mx_spmv_g_form(bool c32);
-KGroup k_mx_refine_g_form(bool c32);
 KBulk k_bulk_endpoint_form(bool c32);
-KBulk k_bulk_endpoint_mx_form(bool c32);
-KFi k_fi_mx_form(bool c32);
+// The kernels that read only the FP32 copy of K: f = 0 (16-bit offsets), 1 (32-bit
+// columns) or 2 (implied columns, EllDev::stab set).
+KMx k_mx_spmv_form32(int f);
+KMx k_mx_refine_form32(int f);
+KGroup k_mx_spmv_g_form32(int f);
+KGroup k_mx_refine_g_form32(int f);
+KBulk k_bulk_endpoint_mx_form32(int f);
+KFi k_fi_mx_form32(int f);
 __global__ void k_sisdc_fe(SisdcArgs a);
 __global__ void k_sisdc_rhs(SisdcArgs a);
 __global__ void k_sisdc_endpoint(const double* X, const double* Tprev, double* Tout, float* dT, int64_t n);

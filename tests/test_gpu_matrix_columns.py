@@ -2,12 +2,16 @@
 
 Every SpMV of the path (CG, f^I, bulk endpoints, refinement) reads K through the sliced
 ELL. Its columns are stored as 16-bit offsets from each 32-row slice's smallest column
-when every slice spans at most 65,535 columns, else as 32-bit columns. Either way the
-kernels read the same values and columns in the same order, so:
-  * the two forms give bitwise equal steps, in both precisions;
+when every slice spans at most 65,535 columns, else as 32-bit columns; and the FP32 copy
+of the mixed-precision solves has implied columns when the matrix allows them (each
+slice's rows share one increasing table of relative columns, absent neighbours hold 0).
+Every form sums the same products of a row in the same order, so:
+  * the forms give bitwise equal steps, in both precisions, also on the 733,586-DOF machine
+    whose FP32 CG runs three launches an iteration;
   * a node numbering whose slices span more columns (a random renumbering of the stand)
-    takes 32-bit columns by itself and gives the steps of the natural numbering, permuted,
-    to rounding (the rows' entries are then summed in another order).
+    takes 32-bit columns and no implied columns by itself, and gives the steps of the
+    natural numbering, permuted, to rounding (the rows' entries are then summed in another
+    order).
 """
 
 from dataclasses import replace
@@ -42,13 +46,33 @@ def _solver(mach, precision, bits):
 def test_column_forms_are_bitwise_equal(torch, precision, idx):
     mach = machine_config(idx)
     a = _solver(mach, precision, 0)
-    b = _solver(mach, precision, 32)
-    assert a.matrix_columns() == 16 and b.matrix_columns() == 32
+    b = _solver(mach, precision, 16)
+    c = _solver(mach, precision, 32)
+    assert a.matrix_columns() == 16 and b.matrix_columns() == 16 and c.matrix_columns() == 32
+    assert a.matrix_implied() and not b.matrix_implied() and not c.matrix_implied()
     for _ in range(3):
         ra = a.step(report=True)
         rb = b.step(report=True)
+        rc = c.step(report=True)
     assert np.array_equal(a.temperature(), b.temperature())
-    assert ra["cg_iters_total"] == rb["cg_iters_total"]
+    assert np.array_equal(a.temperature(), c.temperature())
+    assert ra["cg_iters_total"] == rb["cg_iters_total"] == rc["cg_iters_total"]
+    assert ra["refinements_total"] == rb["refinements_total"] == rc["refinements_total"]
+    for s in (a, b, c):
+        s.close()
+
+
+def test_implied_columns_bitwise_on_the_large_grid_machine(torch):
+    # the first machine of the 64-machine batch: 733,586 DOF, 2,866 blocks, so its FP32 CG
+    # runs the three-launch form (k_mx_spmv, k_mx_dots, k_mx_update_red4)
+    mach = machine_config(3)[0]
+    a = _solver(mach, "mixed", 0)
+    b = _solver(mach, "mixed", 16)
+    assert a.n == 733586 and a.matrix_implied() and not b.matrix_implied()
+    ra = a.step(report=True)
+    rb = b.step(report=True)
+    assert np.array_equal(a.temperature(), b.temperature())
+    assert ra["cg_iters_total"] == rb["cg_iters_total"] and ra["refinements_total"] == rb["refinements_total"]
     a.close()
     b.close()
 
@@ -73,6 +97,7 @@ def test_scrambled_numbering_takes_32_bit_columns(torch, precision):
     a = _solver(mach, precision, 0)
     b = _solver(scr, precision, 0)
     assert a.matrix_columns() == 16 and b.matrix_columns() == 32
+    assert a.matrix_implied() and not b.matrix_implied()
     for _ in range(2):
         a.step(report=True)
         b.step(report=True)
@@ -93,5 +118,10 @@ def test_matrix_columns_argument_checks(torch):
     with pytest.raises(SdcError):
         s.matrix_columns()  # before assembly
     with pytest.raises(SdcError):
-        s.set_matrix_columns(16)
+        s.matrix_implied()
+    for bad in (8, 24, -1):
+        with pytest.raises(SdcError):
+            s.set_matrix_columns(bad)
+    for ok in (0, 16, 32):
+        s.set_matrix_columns(ok)
     s.close()
