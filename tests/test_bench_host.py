@@ -74,3 +74,35 @@ def test_traffic_comes_from_a_profile_of_the_current_kernel(tmp_path, monkeypatc
     assert bench._profile_traffic("k_a", 101)[0] is None
     t, note = bench._profile_traffic("k_b", 100)
     assert t is None and "changed" in note
+
+
+class _FakeSolver:
+    def __init__(self, n, nnz, bits, implied):
+        self.n, self.nnz, self._bits, self._implied = n, nnz, bits, implied
+
+    def matrix_columns(self):
+        return self._bits
+
+    def matrix_implied(self):
+        return self._implied
+
+
+@pytest.mark.parametrize("bits,implied,per_nnz,slices", [(16, True, 4, True), (16, False, 6, True),
+                                                          (32, False, 8, False)])
+def test_spmv_bytes_follow_the_matrix_form(bits, implied, per_nnz, slices):
+    # the FP32 SpMV's algorithmic bytes: the value (4 B) and the stored column of every nonzero
+    # (none when implied, 2 B offset, 4 B column), 16 B a row, 4 B a 32-row slice (its base
+    # or its table position; none with 32-bit columns)
+    n, nnz = 1000, 27000
+    s = _FakeSolver(n, nnz, bits, implied)
+    kt = {"k_mx_spmv": (10, 1.0), "k_mx_update": (10, 0.5)}
+    reps = [{"cg_iters_total": 8, "refinements_total": 2, "n_solves": 2}]
+    name, upd, _, sp_bytes, up_bytes, work, _, _, note = bench._dominant_kernel(s, "mixed", kt, reps)
+    assert name == "k_mx_spmv" and upd == "k_mx_update"
+    assert sp_bytes == per_nnz * nnz + 16 * n + (4 * 32 if slices else 0)  # 32 slices of 32 rows
+    assert up_bytes == 48 * n and work == 10
+    assert note.startswith(f"{per_nnz} B/nnz")
+    # the FP64 path reads the FP64 values with the stored columns whatever the FP32 copy's form
+    name, _, _, sp64, _, work64, _, _, _ = bench._dominant_kernel(s, "fp64", {}, reps)
+    assert name == "k_cg_spmv" and work64 == 10
+    assert sp64 == (8 + bits // 8) * nnz + 32 * n + (4 * 32 if bits == 16 else 0)
