@@ -217,65 +217,110 @@ void assemble_body(const BodyInput& B, HostCSR& K, std::vector<double>& mass, st
 // The implied-column layout of K's FP32 copy (see ImpliedEll). Entries of a row run over its
 // slice's table in increasing offset, that is in increasing column, as the CSR row does, so
 // an SpMV that sums a row's entries in storage order adds the same products in the same order
-// as the offsets form, with zeros between them.
+// as the offsets form, with zeros between them. Slices are independent (OpenMP); the tables
+// are deduplicated in slice order.
 bool build_implied_ell(const HostCSR& K, ImpliedEll& out) {
     const int64_t n = K.n;
     if (n <= 0 || n >= (int64_t(1) << 30)) return false;
+    int unsorted = 0;
+#pragma omp parallel for schedule(static) reduction(| : unsorted)
     for (int64_t r = 0; r < n; ++r)
         for (int64_t k = K.row_ptr[r] + 1; k < K.row_ptr[r + 1]; ++k)
-            if (K.col[k] <= K.col[k - 1]) return false;
+            if (K.col[k] <= K.col[k - 1]) unsorted = 1;
+    if (unsorted) return false;
     const int64_t ns = (n + SLICE - 1) / SLICE;
+    constexpr int W = IMPLIED_MAX_WIDTH;
+    std::vector<int32_t> uni((size_t)ns * W);  // each slice's union, increasing
+    std::vector<int32_t> width(ns, 0);
+    std::vector<int64_t> wmax(ns, 0);          // longest row of the slice (offsets form)
+    int too_wide = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : too_wide)
+    for (int64_t s = 0; s < ns; ++s) {
+        int32_t* u = uni.data() + (size_t)s * W;
+        int w = 0;
+        int32_t merged[2 * W];
+        const int32_t* prev = nullptr;
+        int64_t prev_len = -1;
+        for (int64_t r = s * SLICE; r < std::min(n, (s + 1) * SLICE); ++r) {
+            const int32_t* c = K.col.data() + K.row_ptr[r];
+            const int64_t len = K.row_ptr[r + 1] - K.row_ptr[r];
+            wmax[s] = std::max(wmax[s], len);
+            // a row whose columns are its predecessor's shifted by one has the same offsets
+            bool same = prev && len == prev_len;
+            for (int64_t k = 0; same && k < len; ++k) same = c[k] == prev[k] + 1;
+            prev = c;
+            prev_len = len;
+            if (same || too_wide) continue;
+            // merge the row's offsets (increasing, since its columns are) into the union
+            int a = 0, m = 0;
+            int64_t k = 0;
+            while ((a < w || k < len) && m <= W) {
+                const int64_t o = k < len ? (int64_t)c[k] - r : INT64_MAX;
+                if (a < w && (int64_t)u[a] < o) {
+                    merged[m++] = u[a++];
+                } else {
+                    if (a < w && (int64_t)u[a] == o) ++a;
+                    merged[m++] = (int32_t)o;
+                    ++k;
+                }
+            }
+            if (m > W) {
+                too_wide = 1;
+                continue;
+            }
+            std::copy(merged, merged + m, u);
+            w = m;
+        }
+        width[s] = w;
+    }
+    if (too_wide) return false;
     out.slice_ptr.assign(ns + 1, 0);
     out.tab.assign(ns, 0);
     out.off.clear();
     std::map<std::vector<int32_t>, int32_t> seen;
-    std::vector<int32_t> u;
     int64_t stored_offsets_form = 0;
     for (int64_t s = 0; s < ns; ++s) {
-        const int64_t r0 = s * SLICE, r1 = std::min(n, r0 + SLICE);
-        u.clear();
-        int64_t w = 0;
-        for (int64_t r = r0; r < r1; ++r) {
-            w = std::max(w, K.row_ptr[r + 1] - K.row_ptr[r]);
-            for (int64_t k = K.row_ptr[r]; k < K.row_ptr[r + 1]; ++k) u.push_back(K.col[k] - (int32_t)r);
-        }
-        stored_offsets_form += w * SLICE;
-        std::sort(u.begin(), u.end());
-        u.erase(std::unique(u.begin(), u.end()), u.end());
-        if (u.empty() || (int64_t)u.size() > IMPLIED_MAX_WIDTH) return false;
+        const int32_t* u = uni.data() + (size_t)s * W;
+        const int w = width[s];
+        if (w == 0) return false;
+        stored_offsets_form += wmax[s] * SLICE;
         // offsets increase, so the first row with the smallest and the last row with the
         // largest are the only ones that can leave [0, n)
-        const bool clamp = r0 + u.front() < 0 || (r1 - 1) + u.back() >= n;
+        const int64_t r0 = s * SLICE, r1 = std::min(n, r0 + SLICE);
+        const bool clamp = r0 + u[0] < 0 || (r1 - 1) + u[w - 1] >= n;
+        std::vector<int32_t> key(u, u + w);
         int32_t t;
-        const auto it = seen.find(u);
+        const auto it = seen.find(key);
         if (it == seen.end()) {
             t = (int32_t)out.off.size();
-            out.off.insert(out.off.end(), u.begin(), u.end());
-            seen.emplace(u, t);
+            out.off.insert(out.off.end(), key.begin(), key.end());
+            seen.emplace(std::move(key), t);
         } else {
             t = it->second;
         }
         out.tab[s] = clamp ? ~t : t;
-        out.slice_ptr[s + 1] = out.slice_ptr[s] + (int64_t)u.size() * SLICE;
+        out.slice_ptr[s + 1] = out.slice_ptr[s] + (int64_t)w * SLICE;
     }
     if (out.slice_ptr[ns] * 4 > stored_offsets_form * 5) return false;
     out.val.assign(out.slice_ptr[ns], 0.0f);
+    int missed = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : missed)
     for (int64_t s = 0; s < ns; ++s) {
-        const int32_t t = out.tab[s] < 0 ? ~out.tab[s] : out.tab[s];
+        const int32_t* tab = out.off.data() + (out.tab[s] < 0 ? ~out.tab[s] : out.tab[s]);
         const int64_t w = (out.slice_ptr[s + 1] - out.slice_ptr[s]) / SLICE;
         for (int lane = 0; lane < SLICE; ++lane) {
             const int64_t r = s * SLICE + lane;
             if (r >= n) break;
             int64_t k = K.row_ptr[r];
             for (int64_t q = 0; q < w && k < K.row_ptr[r + 1]; ++q)
-                if ((int64_t)K.col[k] - r == out.off[t + q]) {
+                if ((int64_t)K.col[k] - r == tab[q]) {
                     out.val[out.slice_ptr[s] + q * SLICE + lane] = (float)K.val[k];
                     ++k;
                 }
-            if (k != K.row_ptr[r + 1]) return false;  // cannot happen: the table holds every offset
+            if (k != K.row_ptr[r + 1]) missed = 1;  // cannot happen: the table holds every offset
         }
     }
-    return true;
+    return !missed;
 }
 
 }  // namespace sdc
