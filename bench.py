@@ -271,6 +271,83 @@ def _reduced_baseline(proc, m, n_int, config_idx, units_per_step):
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle, interface-only substeps", "sample": sample}
 
 
+def _pool_worker(cfg, member, reduced, barrier, queue):
+    """One oracle process of the multi-machine CPU baseline (spawned; BLAS threads = 1 from the
+    environment the parent set): assemble machine `member` of workload `cfg`, wait for the
+    others, run one macro step, report its DOF-substeps and monotonic start and end."""
+    import threading
+
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    from oracle.machine import MachineProblem
+    from oracle.mrsdc import mrsdc_step, mrsdc_step_reduced
+    from oracle.weights import mrsdc_weights
+    from synth import machine_config
+
+    try:
+        m = machine_config(cfg, select=[member])[0]
+        sc = m.scheme
+        prob = MachineProblem(m)
+        W = mrsdc_weights(sc.nodes, sc.M, sc.P, sc.window)
+        T = np.full(prob.n, m.T0)
+        n_int = sum(1 for j in range(sc.M) if W["c"][j + 1] > W["c"][j])
+        barrier.wait(timeout=1800)
+        t0 = time.monotonic()
+        if reduced:
+            mrsdc_step_reduced(prob, T, m.t0, sc.dt, W, sc.sweeps)
+        else:
+            mrsdc_step(prob, T, m.t0, sc.dt, W, sc.sweeps)
+        t1 = time.monotonic()
+        queue.put({"member": member, "n": int(prob.n), "units": int(prob.n) * n_int * sc.P, "t0": t0, "t1": t1})
+    except (Exception, threading.BrokenBarrierError) as e:  # reported, not raised: the parent waits on the queue
+        barrier.abort()
+        queue.put({"member": member, "error": repr(e)[:300]})
+
+
+def _oracle_pool(cfg, members, reduced=False, timeout=1800):
+    """The oracle across the host cores for a workload of many machines: one spawned process
+    per machine (single-threaded numpy/scipy each), all assembled first, then one macro step
+    each started together; value = their DOF-substeps / (last end - first start)."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    names = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {v: os.environ.get(v) for v in names}
+    for v in names:
+        os.environ[v] = "1"
+    procs = []
+    try:
+        barrier, queue = ctx.Barrier(len(members)), ctx.Queue()
+        procs = [ctx.Process(target=_pool_worker, args=(cfg, i, reduced, barrier, queue)) for i in members]
+        for pr in procs:
+            pr.start()
+        res = [queue.get(timeout=timeout) for _ in procs]
+        for pr in procs:
+            pr.join(timeout=60)
+    finally:
+        for pr in procs:
+            if pr.is_alive():
+                pr.terminate()
+        for v, x in saved.items():
+            if x is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = x
+    bad = [r for r in res if "error" in r]
+    if bad:
+        raise RuntimeError(f"oracle process failed: {bad[0]}")
+    units = sum(r["units"] for r in res)
+    secs = max(r["t1"] for r in res) - min(r["t0"] for r in res)
+    dofs = sorted(r["n"] for r in res)
+    return {"value": units / secs, "unit": UNIT, "cores": len(members), "kind": "oracle",
+            "sample": (f"one macro step of each of {len(members)} machines of the workload ({dofs[0]}-{dofs[-1]} "
+                       f"DOF, {sum(dofs)} in total){' with interface-only substeps' if reduced else ''}, one "
+                       f"process per machine (single-threaded numpy/scipy), assembled first (not timed) and "
+                       f"started together; {secs:.1f} s from the first start to the last end"),
+            "host_cpu": _host_cpu()}
+
+
 def _cpu_baseline_line(value, cores_note, sample, host):
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
             "threads": cores_note, "host_cpu": host}
@@ -996,8 +1073,14 @@ def run_batch(args, rank, world):
         "autotune": tuned or "off (--no-tune)",
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
     b.close()
+    if not args.no_cpu_baseline and world == 1:
+        # as many machines as the host has cores, one oracle process each
+        try:
+            line["cpu_baseline"] = _oracle_pool(3, list(range(min(len(machines), os.cpu_count() or 1))))
+        except Exception as e:
+            line["cpu_baseline"] = {"error": str(e)[:300]}
+    print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()
 
@@ -1138,6 +1221,12 @@ def run_serving(args, rank, world):
                          "p99_latency": f64["latency_s"]["p99"] / mx["latency_s"]["p99"],
                          "p50_latency": f64["latency_s"]["p50"] / mx["latency_s"]["p50"]} if f64 else None,
     }
+    if not args.no_cpu_baseline and world == 1:
+        # the serving pool's machines on the host cores, one oracle process each
+        try:
+            line["cpu_baseline"] = _oracle_pool(3, list(range(min(len(machines), os.cpu_count() or 1))))
+        except Exception as e:
+            line["cpu_baseline"] = {"error": str(e)[:300]}
     print(json.dumps(line), flush=True)
 
 

@@ -106,3 +106,12 @@ def test_spmv_bytes_follow_the_matrix_form(bits, implied, per_nnz, slices):
     name, _, _, sp64, _, work64, _, _, _ = bench._dominant_kernel(s, "fp64", {}, reps)
     assert name == "k_cg_spmv" and work64 == 10
     assert sp64 == (8 + bits // 8) * nnz + 32 * n + (4 * 32 if bits == 16 else 0)
+
+
+def test_oracle_pool_runs_one_process_per_machine():
+    # the CPU baseline of the batch and serving workloads: one spawned oracle process per
+    # machine, one macro step each, started together (two small machines of the batch here)
+    cb = bench._oracle_pool(3, [6, 8])
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["unit"] == bench.UNIT
+    assert cb["value"] > 0 and "12902-41336 DOF" in cb["sample"]
+    assert cb["host_cpu"]["logical_cores"] == os.cpu_count()
