@@ -125,3 +125,29 @@ def test_matrix_columns_argument_checks(torch):
     for ok in (0, 16, 32):
         s.set_matrix_columns(ok)
     s.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "slab"])
+def test_implied_columns_bitwise_on_small_machines(torch, case):
+    # machines of a few hundred DOF, where a larger share of the slices meet the ends of the
+    # numbering and clamp their columns
+    from paper_1707_03581_gb300 import Solver
+    from synth import tiny_machine
+    from synth.machines import slab_machine
+
+    if case == "tiny":
+        mach, T0 = tiny_machine(z0=0.37, amp=0.2, period=2.5), None
+    else:
+        mach, T0 = slab_machine()
+    out = []
+    for bits in (0, 16):
+        s = Solver(0)
+        s.set_matrix_columns(bits)
+        s.set_machine(mach, precision="mixed", T0=T0)
+        assert s.matrix_implied() == (bits == 0)
+        reps = [s.step(report=True) for _ in range(3)]
+        assert all(r["status"] == 0 for r in reps)
+        out.append((s.temperature(), [r["cg_iters_total"] for r in reps]))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
